@@ -1,0 +1,248 @@
+"""RotorMap FP64 CPU oracle — TEST INFRASTRUCTURE ONLY.
+
+A plain, slow, obviously correct CPU implementation of what the GPU path
+computes, written from the paper (see ``rotormap_oracle.c`` for the passage each
+function follows). It shares no code with the CUDA library and neither imports
+the other. Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline
+leg of ``bench.py`` may import it.
+
+Parity status: every function here is pinned by ``tests/test_oracle_pins.py``
+against closed forms, invariants, values the paper prints, or brute force,
+except the reranker network (``mlp``), which is pinned by finite differences
+only; it is marked there.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "rotormap_oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile liboracle.so with gcc + OpenMP (portable flags)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-shared", "-fPIC", "-std=c11", "-fopenmp", "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        build()
+        lib = ctypes.CDLL(_LIB)
+        i64, i32, f64, p = ctypes.c_int64, ctypes.c_int, ctypes.c_double, ctypes.c_void_p
+        sig = {
+            "oracle_base": ([i32], i32),
+            "oracle_pack_2bit": ([p, i64, p], i64),
+            "oracle_default_bin_map": ([i32, i32, p], None),
+            "oracle_mer_bins": ([p, i64, i32, p, p], i32),
+            "oracle_factor": ([i32, i32, i32, p, p], None),
+            "oracle_embed": ([p, i32, i32, i32, i32, i32, p, p, p], i32),
+            "oracle_embed_matrix_form": ([p, i32, i32, i32, i32, i32, p, p, p], i32),
+            "oracle_fidelity": ([p, p, p, p, i32], f64),
+            "oracle_fidelity_per_band": ([p, p, p, p, i32, i32], f64),
+            "oracle_hamming_fingerprint_fidelity": ([p, p, i32], f64),
+            "oracle_n_windows": ([i64, i32, i32], i64),
+            "oracle_windows_direct": ([p, i64, i32, i32, i64, i64, i32, i32, i32, i32, p, p, p], i32),
+            "oracle_windows_recurrence": ([p, i64, i32, i64, i64, i32, i32, i32, i32, p, p, p], i32),
+            "oracle_ip_recurrence": ([p, i64, i32, i64, i64, i32, i32, i32, i32, p, p, p, p, p], i32),
+            "oracle_score_topk": ([p, i64, p, p, i64, i32, i32, i64, i64, i32, i32, i32, i32, p, i32, i32, i32, i32,
+                                   p, p], i32),
+            "oracle_score_pairs": ([p, i64, p, p, p, p, i64, i32, i32, i32, i32, i32, p, i32, i32, p], i32),
+            "oracle_levenshtein": ([p, i32, p, i32], i32),
+            "oracle_levenshtein_pairs": ([p, i64, p, p, p, p, i64, i32, i32, p], i32),
+            "oracle_max_threads": ([], i32),
+        }
+        for name, (args, res) in sig.items():
+            fn = getattr(lib, name)
+            fn.argtypes = args
+            fn.restype = res
+        _lib = lib
+    return _lib
+
+
+def _u8(x) -> np.ndarray:
+    if isinstance(x, (bytes, bytearray)):
+        return np.frombuffer(bytes(x), dtype=np.uint8).copy()
+    if isinstance(x, str):
+        return np.frombuffer(x.encode(), dtype=np.uint8).copy()
+    return np.ascontiguousarray(x, dtype=np.uint8)
+
+
+def _p(a: np.ndarray) -> int:
+    return a.ctypes.data
+
+
+class Params:
+    """(s, m, t, variant) of the encoding, window length N and stride."""
+
+    def __init__(self, s=4, m=2, t=2, variant=1, N=150, stride=1, score_mode=0, bin_map=None):
+        self.s, self.m, self.t, self.variant = s, m, t, variant
+        self.N, self.stride, self.score_mode = N, stride, score_mode
+        self.bin_map = default_bin_map(s, t) if bin_map is None else np.ascontiguousarray(bin_map, np.uint16)
+
+    @property
+    def dim(self) -> int:
+        """complex dimension m * 4^t"""
+        return self.m << (2 * self.t)
+
+
+# ---------------------------------------------------------------- primitives
+
+def base(c: str) -> int:
+    return _load().oracle_base(ord(c))
+
+
+def pack_2bit(seq) -> np.ndarray:
+    seq = _u8(seq)
+    out = np.zeros((len(seq) + 15) // 16, dtype=np.uint32)
+    bad = _load().oracle_pack_2bit(_p(seq), len(seq), _p(out))
+    if bad >= 0:
+        raise ValueError(f"invalid letter at {bad}")
+    return out
+
+
+def default_bin_map(s: int, t: int) -> np.ndarray:
+    out = np.empty(1 << (2 * s), dtype=np.uint16)
+    _load().oracle_default_bin_map(s, t, _p(out))
+    return out
+
+
+def mer_bins(seq, s: int, bin_map: np.ndarray) -> np.ndarray:
+    seq = _u8(seq)
+    out = np.empty(max(len(seq) - s + 1, 0), dtype=np.int32)
+    if _load().oracle_mer_bins(_p(seq), len(seq), s, _p(np.ascontiguousarray(bin_map, np.uint16)), _p(out)) != 0:
+        raise ValueError("invalid letter")
+    return out
+
+
+def factor(m: int, variant: int, k: int) -> tuple[int, int]:
+    a, q = ctypes.c_int64(), ctypes.c_int64()
+    _load().oracle_factor(m, variant, k, ctypes.byref(a), ctypes.byref(q))
+    return a.value, q.value
+
+
+def embed(seq, p: Params, N: int | None = None, matrix_form: bool = False) -> np.ndarray:
+    """Unnormalised RoPE vector of the first N letters (complex128, band-major)."""
+    seq = _u8(seq)
+    N = p.N if N is None else N
+    if len(seq) < N:
+        raise ValueError("sequence shorter than N")
+    re = np.empty(p.dim)
+    im = np.empty(p.dim)
+    fn = _load().oracle_embed_matrix_form if matrix_form else _load().oracle_embed
+    if fn(_p(seq), N, p.s, p.m, p.t, p.variant, _p(p.bin_map), _p(re), _p(im)) != 0:
+        raise ValueError("invalid letter")
+    return re + 1j * im
+
+
+def fidelity(x: np.ndarray, y: np.ndarray) -> float:
+    xr, xi = np.ascontiguousarray(x.real), np.ascontiguousarray(x.imag)
+    yr, yi = np.ascontiguousarray(y.real), np.ascontiguousarray(y.imag)
+    return _load().oracle_fidelity(_p(xr), _p(xi), _p(yr), _p(yi), len(x))
+
+
+def fidelity_per_band(x: np.ndarray, y: np.ndarray, m: int) -> float:
+    xr, xi = np.ascontiguousarray(x.real), np.ascontiguousarray(x.imag)
+    yr, yi = np.ascontiguousarray(y.real), np.ascontiguousarray(y.imag)
+    return _load().oracle_fidelity_per_band(_p(xr), _p(xi), _p(yr), _p(yi), m, len(x) // m)
+
+
+def hamming_fingerprint_fidelity(S, T) -> float:
+    S, T = _u8(S), _u8(T)
+    assert len(S) == len(T)
+    return _load().oracle_hamming_fingerprint_fidelity(_p(S), _p(T), len(S))
+
+
+def n_windows(L: int, N: int, stride: int) -> int:
+    return _load().oracle_n_windows(L, N, stride)
+
+
+def windows_direct(ref, p: Params, j0: int, count: int) -> np.ndarray:
+    ref = _u8(ref)
+    re = np.empty((count, p.dim))
+    im = np.empty((count, p.dim))
+    if _load().oracle_windows_direct(_p(ref), len(ref), p.N, p.stride, j0, count, p.s, p.m, p.t, p.variant,
+                                     _p(p.bin_map), _p(re), _p(im)) != 0:
+        raise ValueError("window out of range or invalid letter")
+    return re + 1j * im
+
+
+def windows_recurrence(ref, p: Params, w0: int, count: int) -> np.ndarray:
+    ref = _u8(ref)
+    re = np.empty((count, p.dim))
+    im = np.empty((count, p.dim))
+    if _load().oracle_windows_recurrence(_p(ref), len(ref), p.N, w0, count, p.s, p.m, p.t, p.variant,
+                                         _p(p.bin_map), _p(re), _p(im)) != 0:
+        raise ValueError("window out of range or invalid letter")
+    return re + 1j * im
+
+
+def ip_recurrence(ref, p: Params, x: np.ndarray, w0: int, count: int) -> np.ndarray:
+    ref = _u8(ref)
+    xr, xi = np.ascontiguousarray(x.real), np.ascontiguousarray(x.imag)
+    outr, outi = np.empty(count), np.empty(count)
+    if _load().oracle_ip_recurrence(_p(ref), len(ref), p.N, w0, count, p.s, p.m, p.t, p.variant, _p(p.bin_map),
+                                    _p(xr), _p(xi), _p(outr), _p(outi)) != 0:
+        raise ValueError("window out of range or invalid letter")
+    return outr + 1j * outi
+
+
+def score_topk(ref, seqs, offsets, p: Params, k: int = 8, sep: int = 0, j_begin: int = 0, j_end: int | None = None,
+               n_threads: int = 0) -> tuple[np.ndarray, np.ndarray]:
+    """Exhaustive FP64 top-k: (window starts int64 [n,k], scores float64 [n,k])."""
+    ref, seqs = _u8(ref), _u8(seqs)
+    offsets = np.ascontiguousarray(offsets, dtype=np.int64)
+    n = len(offsets) - 1
+    if j_end is None:
+        j_end = n_windows(len(ref), p.N, p.stride)
+    out_w = np.empty((n, k), dtype=np.int64)
+    out_s = np.empty((n, k), dtype=np.float64)
+    rc = _load().oracle_score_topk(_p(ref), len(ref), _p(seqs), _p(offsets), n, p.N, p.stride, j_begin, j_end, p.s,
+                                   p.m, p.t, p.variant, _p(p.bin_map), p.score_mode, k, sep, n_threads, _p(out_w),
+                                   _p(out_s))
+    if rc != 0:
+        raise ValueError(f"oracle_score_topk failed ({rc})")
+    return out_w, out_s
+
+
+def score_pairs(ref, seqs, offsets, read_idx, win_start, p: Params, n_threads: int = 0) -> np.ndarray:
+    ref, seqs = _u8(ref), _u8(seqs)
+    offsets = np.ascontiguousarray(offsets, dtype=np.int64)
+    ri = np.ascontiguousarray(read_idx, dtype=np.int64)
+    ws = np.ascontiguousarray(win_start, dtype=np.int64)
+    out = np.empty(len(ri))
+    if _load().oracle_score_pairs(_p(ref), len(ref), _p(seqs), _p(offsets), _p(ri), _p(ws), len(ri), p.N, p.s, p.m,
+                                  p.t, p.variant, _p(p.bin_map), p.score_mode, n_threads, _p(out)) != 0:
+        raise ValueError("oracle_score_pairs failed")
+    return out
+
+
+def levenshtein(a, b) -> int:
+    a, b = _u8(a), _u8(b)
+    return _load().oracle_levenshtein(_p(a), len(a), _p(b), len(b))
+
+
+def levenshtein_pairs(ref, seqs, offsets, read_idx, win_start, N: int, n_threads: int = 0) -> np.ndarray:
+    ref, seqs = _u8(ref), _u8(seqs)
+    offsets = np.ascontiguousarray(offsets, dtype=np.int64)
+    ri = np.ascontiguousarray(read_idx, dtype=np.int64)
+    ws = np.ascontiguousarray(win_start, dtype=np.int64)
+    out = np.empty(len(ri), dtype=np.int32)
+    if _load().oracle_levenshtein_pairs(_p(ref), len(ref), _p(seqs), _p(offsets), _p(ri), _p(ws), len(ri), N,
+                                        n_threads, _p(out)) != 0:
+        raise ValueError("oracle_levenshtein_pairs failed")
+    return out
+
+
+def max_threads() -> int:
+    return _load().oracle_max_threads()

@@ -1,0 +1,436 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+Each test names the passage it checks. These run on CPU only.
+"""
+import itertools
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "paper_facts.json")
+LETTERS = b"ACGT"
+
+
+def rand_seq(n, seed):
+    return synth.uniform_ref(n, seed)
+
+
+def de_bruijn(k, n):
+    """de Bruijn sequence B(k, n) (every length-n word over k letters exactly
+    once, cyclically), by the Lyndon-word construction; linearised by
+    appending its first n-1 letters."""
+    a = [0] * k * n
+    seq = []
+
+    def db(t, p):
+        if t > n:
+            if n % p == 0:
+                seq.extend(a[1:p + 1])
+        else:
+            a[t] = a[t - p]
+            db(t + 1, p)
+            for j in range(a[t - p] + 1, k):
+                a[t] = j
+                db(t + 1, t)
+
+    db(1, 1)
+    seq = seq + seq[: n - 1]
+    return bytes(LETTERS[i] for i in seq)
+
+
+PARAMS = [
+    dict(s=4, m=2, t=2, variant=1),   # d=64 reading
+    dict(s=4, m=4, t=2, variant=1),   # d=128 reading
+    dict(s=2, m=2, t=2, variant=0),   # paper-pure default, no compaction
+    dict(s=3, m=1, t=3, variant=0),
+    dict(s=5, m=3, t=3, variant=1),
+]
+
+
+# ------------------------------------------------------------------ §1
+
+def test_hamming_fingerprint_golden():
+    facts = json.load(open(GOLDEN))["hamming_fingerprint"]
+    for f in facts:
+        assert oracle.hamming_fingerprint_fidelity(f["S"], f["T"]) == pytest.approx(f["fidelity"], abs=1e-15)
+
+
+def test_hamming_fingerprint_formula_random():
+    rng = np.random.default_rng(0)
+    for n in (1, 7, 64, 300):
+        S = rand_seq(n, 11 + n)
+        for d in sorted(set([0, 1, n // 3, n])):
+            T = S.copy()
+            for i in rng.choice(n, size=d, replace=False):
+                T[i] = LETTERS[(LETTERS.index(S[i]) + 1 + rng.integers(3)) % 4]
+            assert oracle.hamming_fingerprint_fidelity(S, T) == pytest.approx(((n - d) / n) ** 2, abs=1e-14)
+
+
+# ------------------------------------------------------------------ §2.1–2.3, §3.3 golden dimensions
+
+def test_dimensions_golden():
+    facts = json.load(open(GOLDEN))
+    for f in facts["dimensions"]:
+        p = oracle.Params(s=f["s"], m=f["m"], t=f["t"], variant=0, N=4 ** f["s"] + 8)
+        assert p.dim == f["complex_dim"]
+        assert 2 * f["t"] + int(math.log2(f["m"])) == f["qubits"]
+        if f["complex_dim"] <= 1024:
+            x = oracle.embed(rand_seq(p.N, 5), p)
+            assert x.shape == (f["complex_dim"],)
+    fr = facts["fine_tuned_factor_range"]
+    fs = [a / q for a, q in (oracle.factor(fr["m"], 1, k) for k in range(1, fr["m"] + 1))]
+    assert min(fs) == fr["min"] and max(fs) == fr["max"]
+    assert all(b > a for a, b in zip(fs, fs[1:]))
+    assert [a / q for a, q in (oracle.factor(4, 0, k) for k in range(1, 5))] == [1, 2, 3, 4]
+    assert oracle.factor(1, 1, 1) == (1, 1)
+    wc = facts["window_count"]
+    assert oracle.n_windows(wc["L"], wc["N"], wc["step"]) == pytest.approx(wc["approx_windows"], rel=wc["rel_tol"])
+    so = facts["scan_ops"]
+    assert 4 * so["windows"] * so["complex_dim"] == pytest.approx(so["approx_ops_per_read"], rel=so["rel_tol"])
+
+
+# ------------------------------------------------------------------ §2.1 letters, packing, s-mers
+
+def test_pack_bit_layout():
+    seq = rand_seq(1000, 3)
+    packed = oracle.pack_2bit(seq)
+    assert packed.shape == ((1000 + 15) // 16,)
+    for i in range(1000):
+        assert (int(packed[i // 16]) >> (2 * (i % 16))) & 3 == LETTERS.index(seq[i])
+    assert int(packed[-1]) >> (2 * (1000 % 16)) == 0
+    assert np.array_equal(oracle.pack_2bit(bytes(seq).lower()), packed)
+    with pytest.raises(ValueError):
+        oracle.pack_2bit(b"ACGTN")
+
+
+def test_mer_bins_brute_force():
+    seq = rand_seq(200, 4)
+    for s, t in ((1, 1), (3, 3), (4, 2), (6, 3)):
+        bm = oracle.default_bin_map(s, t)
+        bins = oracle.mer_bins(seq, s, bm)
+        for p in range(len(seq) - s + 1):
+            code = 0
+            for i in range(s):
+                code = code * 4 + LETTERS.index(seq[p + i])
+            assert bins[p] == bm[code]
+
+
+def test_default_bin_map_properties():
+    for s in range(1, 8):
+        assert np.array_equal(oracle.default_bin_map(s, s), np.arange(4 ** s))
+    for s, t in ((4, 2), (6, 3), (8, 4)):
+        bm = oracle.default_bin_map(s, t)
+        counts = np.bincount(bm, minlength=4 ** t)
+        assert len(counts) == 4 ** t and counts.min() > 0
+        assert counts.max() - counts.min() <= max(2, 4 ** (s - t) // 4)
+
+
+# ------------------------------------------------------------------ §2.1–2.3 embedding
+
+@pytest.mark.parametrize("pp", PARAMS)
+def test_matrix_form_equals_direct_sum(pp):
+    p = oracle.Params(N=180, **pp)
+    for seed in range(3):
+        seq = rand_seq(180, 20 + seed)
+        x = oracle.embed(seq, p)
+        y = oracle.embed(seq, p, matrix_form=True)
+        assert np.abs(x - y).max() < 1e-12 * max(1.0, np.abs(x).max())
+
+
+@pytest.mark.parametrize("pp", PARAMS)
+def test_band_sum_closed_form(pp):
+    """Summing a band over all bins gives sum_{l=0}^{N-s} w^{f l}: a geometric
+    series, independent of the letters."""
+    N = 151
+    p = oracle.Params(N=N, **pp)
+    nb = 4 ** p.t
+    x = oracle.embed(rand_seq(N, 7), p)
+    for k in range(1, p.m + 1):
+        a, q = oracle.factor(p.m, p.variant, k)
+        z = np.exp(2j * np.pi * a / (q * N))
+        closed = (1 - z ** (N - p.s + 1)) / (1 - z)
+        assert abs(x[(k - 1) * nb:k * nb].sum() - closed) < 1e-11
+
+
+@pytest.mark.parametrize("s", [1, 2, 3])
+def test_norm_of_distinct_smers(s):
+    """With every s-mer at most once and t = s, each bin holds one unit phase,
+    so ||c^(k)||^2 = N - s + 1 for every band."""
+    seq = de_bruijn(4, s)
+    N = len(seq)
+    for m, variant in ((1, 0), (3, 0), (4, 1)):
+        p = oracle.Params(s=s, m=m, t=s, variant=variant, N=N)
+        x = oracle.embed(seq, p)
+        nb = 4 ** s
+        for k in range(m):
+            band = x[k * nb:(k + 1) * nb]
+            assert np.sum(np.abs(band) ** 2) == pytest.approx(N - s + 1, abs=1e-10)
+            assert np.allclose(np.abs(band), 1.0, atol=1e-12)
+
+
+def test_all_A_and_periodic_give_zero_vector():
+    """§3.3: evenly spaced unit phases sum to zero; an all-A string, or a
+    periodic one whose period divides N, gives the zero vector (s = 1, default
+    factors)."""
+    N = 120
+    for m in (1, 2, 4):
+        p = oracle.Params(s=1, m=m, t=1, variant=0, N=N)
+        assert np.abs(oracle.embed(b"A" * N, p)).max() < 1e-12
+        assert np.abs(oracle.embed(b"ACGT" * (N // 4), p)).max() < 1e-12
+        assert np.abs(oracle.embed(b"GATTAC" * (N // 6), p)).max() < 1e-12
+    # the fine-tuned factors (§3.3) break the cancellation for k > 1
+    p = oracle.Params(s=1, m=4, t=1, variant=1, N=N)
+    x = oracle.embed(b"A" * N, p)
+    assert np.abs(x[:4]).max() < 1e-12
+    assert np.abs(x[4:]).max() > 0.1
+
+
+def test_random_walk_modulus():
+    """§3.3: the sum of n random unit phases has Rayleigh modulus, mean
+    sqrt(n pi)/2."""
+    facts = json.load(open(GOLDEN))["random_walk_modulus"]
+    N, s = 20000, 2
+    p = oracle.Params(s=s, m=1, t=s, variant=0, N=N)
+    ratios = []
+    for seed in range(12):
+        seq = rand_seq(N, 100 + seed)
+        x = oracle.embed(seq, p)
+        counts = np.bincount(oracle.mer_bins(seq, s, p.bin_map), minlength=16)
+        ratios.extend(np.abs(x) / np.sqrt(counts))
+    assert np.mean(ratios) == pytest.approx(facts["mean_factor"], rel=0.06)
+
+
+# ------------------------------------------------------------------ fidelity
+
+def test_fidelity_identity_bounds_phase():
+    for pp in PARAMS:
+        p = oracle.Params(N=150, **pp)
+        x = oracle.embed(rand_seq(150, 1), p)
+        y = oracle.embed(rand_seq(150, 2), p)
+        assert oracle.fidelity(x, x) == pytest.approx(1.0, abs=1e-14)
+        f = oracle.fidelity(x, y)
+        assert 0.0 <= f <= 1.0
+        assert oracle.fidelity(x, y * np.exp(0.7j)) == pytest.approx(f, abs=1e-14)
+        assert oracle.fidelity(3.5 * x, y) == pytest.approx(f, abs=1e-14)
+        assert oracle.fidelity(x, np.zeros_like(x)) == 0.0
+        # definition written out with numpy's complex inner product
+        assert f == pytest.approx(abs(np.vdot(x, y)) ** 2 / (np.vdot(x, x).real * np.vdot(y, y).real), rel=1e-12)
+
+
+def test_complex_real_identity():
+    """§4: |<z1|z2>|^2 = (<x1|x2> + <y1|y2>)^2 + (<x1|y2> - <y1|x2>)^2, the real
+    contraction the tensor cores evaluate."""
+    p = oracle.Params(N=150)
+    for seed in range(5):
+        z1 = oracle.embed(rand_seq(150, 30 + seed), p)
+        z2 = oracle.embed(rand_seq(150, 40 + seed), p)
+        x1, y1, x2, y2 = z1.real, z1.imag, z2.real, z2.imag
+        lhs = oracle.fidelity(z1, z2) * np.sum(np.abs(z1) ** 2) * np.sum(np.abs(z2) ** 2)
+        rhs = (x1 @ x2 + y1 @ y2) ** 2 + (x1 @ y2 - y1 @ x2) ** 2
+        assert lhs == pytest.approx(rhs, rel=1e-12)
+
+
+def test_fidelity_tracks_mutation():
+    """§1/§2.4: more edits, lower fidelity (monotone in expectation)."""
+    p = oracle.Params(s=4, m=4, t=4, variant=0, N=1000)
+    ref = rand_seq(5000, 77)
+    fids = []
+    for rate in (0.0, 0.02, 0.1, 0.3):
+        rd = synth.reads(ref, 40, seed=5, length=1000, sub_rate=rate / 2, indel_rate=rate / 2)
+        f = [oracle.fidelity(oracle.embed(rd.read(i), p), oracle.embed(ref[rd.true_pos[i]:rd.true_pos[i] + 1000], p))
+             for i in range(rd.n)]
+        fids.append(np.mean(f))
+    assert fids[0] == pytest.approx(1.0, abs=1e-12)
+    assert fids[0] > fids[1] > fids[2] > fids[3]
+
+
+def test_per_band_mean_and_shift_invariance():
+    """§2.5: for m = 1 a cyclic shift changes c only by a global phase (up to
+    the wrapped s-mers), so the fidelity stays near 1; for m > 1 the bands
+    rotate by different phases and the concatenated fidelity drops, while the
+    per-band mean stays near 1."""
+    N, l = 2000, 150
+    seq = rand_seq(N, 9)
+    shifted = np.concatenate([seq[-l:], seq[:-l]])
+    p1 = oracle.Params(s=4, m=1, t=4, variant=0, N=N)
+    assert oracle.fidelity(oracle.embed(seq, p1), oracle.embed(shifted, p1)) > 0.97
+    p4 = oracle.Params(s=4, m=4, t=4, variant=0, N=N)
+    x, y = oracle.embed(seq, p4), oracle.embed(shifted, p4)
+    assert oracle.fidelity(x, y) < 0.8
+    assert oracle.fidelity_per_band(x, y, 4) > 0.97
+    # per-band mean written out band by band
+    nb = 4 ** 4
+    manual = np.mean([oracle.fidelity(x[k * nb:(k + 1) * nb], y[k * nb:(k + 1) * nb]) for k in range(4)])
+    assert oracle.fidelity_per_band(x, y, 4) == pytest.approx(manual, abs=1e-15)
+
+
+def test_bin_permutation_invariance():
+    """With s = t a relabelling of the bins permutes both vectors alike and
+    leaves fidelities unchanged."""
+    rng = np.random.default_rng(3)
+    a, b = rand_seq(150, 50), rand_seq(150, 51)
+    p = oracle.Params(s=3, m=2, t=3, variant=1, N=150)
+    q = oracle.Params(s=3, m=2, t=3, variant=1, N=150, bin_map=rng.permutation(64).astype(np.uint16))
+    assert oracle.fidelity(oracle.embed(a, p), oracle.embed(b, p)) == pytest.approx(
+        oracle.fidelity(oracle.embed(a, q), oracle.embed(b, q)), abs=1e-14)
+
+
+# ------------------------------------------------------------------ §3.4 recurrences
+
+@pytest.mark.parametrize("pp", PARAMS)
+def test_window_recurrence_equals_direct(pp):
+    ref = rand_seq(3000, 60)
+    p = oracle.Params(N=150, **pp)
+    rec = oracle.windows_recurrence(ref, p, 17, 2000)
+    dirct = oracle.windows_direct(ref, p, 17, 2000)
+    assert np.abs(rec - dirct).max() < 1e-11
+
+
+def test_window_recurrence_on_repeats():
+    """The coinciding-exception case (same s-mer leaves and enters) occurs
+    constantly on a tandem repeat."""
+    ref = np.frombuffer(b"ACGTTGCA" * 100, dtype=np.uint8)
+    p = oracle.Params(s=4, m=2, t=2, variant=1, N=64)
+    assert np.abs(oracle.windows_recurrence(ref, p, 0, 700) - oracle.windows_direct(ref, p, 0, 700)).max() < 1e-11
+
+
+@pytest.mark.parametrize("pp", PARAMS[:3])
+def test_ip_recurrence_equals_direct(pp):
+    ref = rand_seq(2000, 61)
+    p = oracle.Params(N=150, **pp)
+    x = oracle.embed(rand_seq(150, 62), p)
+    ip = oracle.ip_recurrence(ref, p, x, 5, 1500)
+    direct = oracle.windows_direct(ref, p, 5, 1500) @ np.conj(x)
+    assert np.abs(ip - direct).max() < 1e-10
+
+
+# ------------------------------------------------------------------ §3.1 / §3.5 exhaustive top-k
+
+def brute_topk(ref, heads, p, k, sep):
+    W = oracle.n_windows(len(ref), p.N, p.stride)
+    wins = oracle.windows_direct(ref, p, 0, W)
+    out_w, out_s = [], []
+    for h in heads:
+        x = oracle.embed(h, p)
+        sc = [(oracle.fidelity(x, wins[j]) if p.score_mode == 0 else oracle.fidelity_per_band(x, wins[j], p.m),
+               j * p.stride) for j in range(W)]
+        sc.sort(key=lambda t: (-t[0], t[1]))
+        got, taken = [], set()
+        for s_, w in sc:
+            if sep > 0:
+                if w // sep in taken:
+                    continue
+                taken.add(w // sep)
+            got.append((w, s_))
+            if len(got) == k:
+                break
+        got += [(-1, -np.inf)] * (k - len(got))
+        out_w.append([g[0] for g in got])
+        out_s.append([g[1] for g in got])
+    return np.array(out_w), np.array(out_s)
+
+
+@pytest.mark.parametrize("stride,sep,k,mode", [(1, 0, 5, 0), (3, 0, 4, 0), (1, 20, 4, 0), (2, 0, 300, 0),
+                                               (1, 0, 6, 1)])
+def test_score_topk_brute_force(stride, sep, k, mode):
+    ref = rand_seq(400, 70)
+    # tandem-repeat patch: exact score ties between distinct windows
+    ref[100:180] = np.frombuffer(b"ACGTA" * 16, dtype=np.uint8)
+    rd = synth.reads(ref, 6, seed=71, length=40)
+    p = oracle.Params(s=3, m=2, t=2, variant=1, N=40, stride=stride, score_mode=mode)
+    heads = [rd.read(i)[:40] for i in range(rd.n)]
+    bw, bs = brute_topk(ref, heads, p, k, sep)
+    ow, os_ = oracle.score_topk(ref, rd.seqs, rd.offsets, p, k=k, sep=sep)
+    assert np.array_equal(ow, bw)
+    assert np.allclose(os_, bs, rtol=1e-14, atol=0)
+
+
+def test_score_topk_finds_planted_reads():
+    ref = rand_seq(30000, 80)
+    rd = synth.reads(ref, 24, seed=81)
+    p = oracle.Params(N=150)
+    w, s = oracle.score_topk(ref, rd.seqs, rd.offsets, p, k=3)
+    hit = np.abs(w[:, 0] - rd.true_pos) <= 150
+    assert hit.mean() >= 0.9
+    assert np.all(s[:, 0] >= s[:, 1])
+
+
+def test_score_pairs_matches_topk():
+    ref = rand_seq(5000, 90)
+    rd = synth.reads(ref, 5, seed=91)
+    p = oracle.Params(N=150)
+    w, s = oracle.score_topk(ref, rd.seqs, rd.offsets, p, k=4)
+    ri = np.repeat(np.arange(5), 4)
+    sp = oracle.score_pairs(ref, rd.seqs, rd.offsets, ri, w.ravel(), p)
+    assert np.array_equal(sp, s.ravel())
+
+
+# ------------------------------------------------------------------ Levenshtein (§1)
+
+def brute_levenshtein(a, b):
+    """breadth-first search over single edits (tiny strings, alphabet of a+b)"""
+    alphabet = sorted(set(a + b)) or ["A"]
+    if a == b:
+        return 0
+    seen = {a}
+    frontier = [a]
+    d = 0
+    limit = len(a) + len(b) + 1
+    while frontier and d < limit:
+        d += 1
+        nxt = []
+        for u in frontier:
+            cands = set()
+            for i in range(len(u) + 1):
+                for c in alphabet:
+                    cands.add(u[:i] + c + u[i:])
+                if i < len(u):
+                    cands.add(u[:i] + u[i + 1:])
+                    for c in alphabet:
+                        cands.add(u[:i] + c + u[i + 1:])
+            for v in cands:
+                if len(v) > max(len(a), len(b)) + 1 or v in seen:
+                    continue
+                if v == b:
+                    return d
+                seen.add(v)
+                nxt.append(v)
+        frontier = nxt
+    raise AssertionError("unreachable")
+
+
+def test_levenshtein_brute_force():
+    words = ["".join(w) for n in range(0, 5) for w in itertools.product("AC", repeat=n)]
+    rng = np.random.default_rng(5)
+    for a in words:
+        for b in rng.choice(words, size=6):
+            assert oracle.levenshtein(a, b) == brute_levenshtein(a, str(b))
+
+
+def test_levenshtein_properties():
+    assert oracle.levenshtein("kitten", "sitting") == 3
+    rng = np.random.default_rng(6)
+    for _ in range(50):
+        a, b, c = (bytes(rng.choice(list(LETTERS), size=rng.integers(0, 30))) for _ in range(3))
+        dab = oracle.levenshtein(a, b)
+        assert dab == oracle.levenshtein(b, a)
+        assert oracle.levenshtein(a, a) == 0
+        assert oracle.levenshtein(a, b"") == len(a)
+        assert dab <= oracle.levenshtein(a, c) + oracle.levenshtein(c, b)
+        assert dab >= abs(len(a) - len(b))
+        if len(a) == len(b):
+            assert dab <= sum(x != y for x, y in zip(a, b))
+
+
+def test_levenshtein_of_planted_reads_bounded_by_edits():
+    ref = rand_seq(20000, 95)
+    rd = synth.reads(ref, 50, seed=96, sub_rate=0.03, indel_rate=0.03)
+    for i in range(rd.n):
+        span = ref[rd.true_pos[i]:rd.true_pos[i] + rd.true_span[i]].tobytes()
+        assert oracle.levenshtein(rd.read(i), span) <= rd.n_edits[i]
