@@ -1,0 +1,387 @@
+#!/usr/bin/env python
+"""RotorMap hot-path benchmark: prints one JSON line.
+
+Workload (default "markov100M"): a 100 Mbp order-2 Markov reference (GC 41%,
+planted tandem repeats and segmental duplicates) and 1,000,000 planted 150 bp
+reads (1% substitutions, 0.5% indels of geometric length), encoded with the
+fine-tuned compact RoPE s=4, m=2, t=2 (d = 64 reals), every window of length
+150 at stride 1 scored exhaustively, top-8 per read. A step maps one batch of
+reads (default 131,072; 8 steps = the whole read set) through rope_map: read
+encoding, the on-chip window recurrence fused with the BF16 tensor-core scan
+and top-k, and FP32 re-scoring. The reference index is built once before the
+timed region (the paper's "preloaded data").
+
+  value       BF16 tensor-core read x window scores/s over all ranks
+  fp32_plain  the FP32 CUDA-core scan on a read subset (same metric)
+  top1_acc    fraction of planted reads whose top-1 window overlaps the truth
+  e2e         the same metric through host buffers (H2D of the reads, D2H of
+              the top-k) around every step
+  roofline    the scan kernel (CUDA events around its launch) against the
+              measured sustained BF16 tensor peak
+  cpu_baseline the FP64 oracle on a bounded sample, on this host's cores
+
+--impl reference times the FP64 oracle (the only reference implementation
+of this path) on the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "read×window scores/s and reads/s, BF16-TC vs FP32 plain, at equal top-1 acc"
+UNIT = "scores/s"
+
+WORKLOADS = {
+    "markov100M": dict(
+        desc="100 Mbp order-2 Markov reference (GC 41%, 2.5% tandem repeats, 2.5% segmental duplicates), "
+             "1M x 150 bp planted reads (1% sub, 0.5% indel geom p=0.7), fine-tuned compact RoPE s=4 m=2 t=2 "
+             "(d=64), N=150, stride 1, exhaustive, top-8",
+        L=100_000_000, gc=0.41, tandem=0.025, segdup=0.025, inter=0.0, ref_seed=3,
+        n_reads=1_000_000, read_len=150, sub=0.01, indel=0.005, read_seed=4,
+        s=4, m=2, t=2, variant=1, N=150, stride=1, k=8),
+    "uniform100k": dict(
+        desc="100 kbp uniform reference, 256 x 150 bp planted reads (1% sub, 0.5% indel), d=64, stride 1, top-8",
+        L=100_000, gc=None, ref_seed=1, n_reads=256, read_len=150, sub=0.01, indel=0.005, read_seed=2,
+        s=4, m=2, t=2, variant=1, N=150, stride=1, k=8),
+}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=8)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="markov100M", choices=sorted(WORKLOADS))
+    ap.add_argument("--batch", type=int, default=131072)
+    ap.add_argument("--fp32-reads", type=int, default=4096)
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--cpu-reads", type=int, default=32)
+    ap.add_argument("--cpu-windows", type=int, default=1_000_000)
+    ap.add_argument("--no-cpu", action="store_true")
+    return ap.parse_args()
+
+
+def make_inputs(wl, rank):
+    import synth
+
+    if wl.get("gc") is None:
+        ref = synth.uniform_ref(wl["L"], wl["ref_seed"])
+    else:
+        ref = synth.markov_ref(wl["L"], wl["gc"], wl["ref_seed"], wl["tandem"], wl["segdup"], wl["inter"])
+    rd = synth.reads(ref, wl["n_reads"], seed=wl["read_seed"] + 1000 * rank, length=wl["read_len"],
+                     sub_rate=wl["sub"], indel_rate=wl["indel"])
+    return ref, rd
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+def traffic_record():
+    """DRAM bytes per scan launch from the committed ncu summary, if it was
+    taken on the current kernel source (else None)."""
+    path = os.path.join(ROOT, "profiles", "scan_tc_traffic.json")
+    src = os.path.join(ROOT, "paper_2603_22245_gb300", "csrc", "rope_scan_tc.cu")
+    if not os.path.exists(path):
+        return None
+    rec = json.load(open(path))
+    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    return rec if rec.get("kernel_sha") == h else None
+
+
+class Clocks:
+    """nvidia-smi samples (200 ms) during the timed region."""
+
+    def __init__(self, device_index: int):
+        self.proc = None
+        self.path = None
+        self.dev = device_index
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.dev), f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_setup(args):
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def cpu_baseline(ref, rd, wl, n_reads, n_windows):
+    """The FP64 oracle, as it stands, on a bounded sample of the workload."""
+    import oracle
+
+    op = oracle.Params(s=wl["s"], m=wl["m"], t=wl["t"], variant=wl["variant"], N=wl["N"], stride=wl["stride"])
+    W = oracle.n_windows(len(ref), wl["N"], wl["stride"])
+    n_windows = min(n_windows, W)
+    sub = rd.subset(np.arange(min(n_reads, rd.n)))
+    t0 = time.perf_counter()
+    oracle.score_topk(ref, sub.seqs, sub.offsets, op, k=wl["k"], j_begin=0, j_end=n_windows)
+    dt = time.perf_counter() - t0
+    return {"value": sub.n * n_windows / dt, "unit": UNIT, "cores": oracle.max_threads(), "kind": "oracle",
+            "sample": f"{sub.n} reads x the first {n_windows} windows, exhaustive FP64 scoring + full sort",
+            "seconds": dt}
+
+
+def run_reference(args, wl):
+    """--impl reference: the FP64 oracle on this host's cores, K steps of a bounded sample."""
+    ws, rank, _ = dist_setup(args)
+    if rank != 0:
+        return
+    import oracle
+
+    ref, rd = make_inputs(dict(wl, n_reads=min(wl["n_reads"], 4096)), 0)
+    op = oracle.Params(s=wl["s"], m=wl["m"], t=wl["t"], variant=wl["variant"], N=wl["N"], stride=wl["stride"])
+    W = oracle.n_windows(len(ref), wl["N"], wl["stride"])
+    nw = min(W, 200_000)
+    per_step = 8
+    times = []
+    for i in range(args.warmup + args.steps):
+        sub = rd.subset(np.arange(i * per_step, (i + 1) * per_step) % rd.n)
+        t0 = time.perf_counter()
+        oracle.score_topk(ref, sub.seqs, sub.offsets, op, k=wl["k"], j_begin=0, j_end=nw)
+        if i >= args.warmup:
+            times.append(time.perf_counter() - t0)
+    total = sum(times)
+    value = args.steps * per_step * nw / total
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload + ": " + wl["desc"],
+                       "sample_per_step": f"{per_step} reads x the first {nw} windows"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.max_threads(), "kind": "oracle",
+                             "sample": f"{per_step} reads x {nw} windows per step"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    wl = WORKLOADS[args.workload]
+    if args.impl == "reference":
+        run_reference(args, wl)
+        return
+
+    import torch
+
+    ws, rank, local = dist_setup(args)
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+    from paper_2603_22245_gb300 import rotormap as rm
+
+    rm.load()
+    ref, rd = make_inputs(wl, rank)
+    p = rm.Params(s=wl["s"], m=wl["m"], t=wl["t"], variant=wl["variant"], window_len=wl["N"], stride=wl["stride"])
+    dref = torch.from_numpy(ref).cuda()
+    t0 = time.perf_counter()
+    idx = rm.rope_encode_reference(p, dref)
+    torch.cuda.synchronize()
+    index_s = time.perf_counter() - t0
+    del dref
+    W = idx.n_windows
+    seqs = torch.from_numpy(rd.seqs).cuda()
+    offs = torch.from_numpy(rd.offsets).cuda()
+    B = min(args.batch, rd.n)
+    n_batches = max(1, rd.n // B)
+    k = wl["k"]
+
+    # read batches as views: seqs is shared, offsets are absolute into it
+    outs = (torch.empty((B, k), dtype=torch.int64, device="cuda"), torch.empty((B, k), dtype=torch.float32,
+                                                                              device="cuda"))
+    true_pos = rd.true_pos
+
+    def step(bi, precision="bf16", o=None):
+        b = bi % n_batches
+        return rm.rope_map(idx, seqs, offs[b * B:(b + 1) * B + 1], k=k, precision=precision, out=o or outs)
+
+    for i in range(args.warmup):
+        step(i)
+    rm.rope_sync_status()
+    rm.rope_profile_enable(args.steps)
+    step_outs = [(torch.empty((B, k), dtype=torch.int64, device="cuda"),
+                  torch.empty((B, k), dtype=torch.float32, device="cuda")) for _ in range(args.steps)]
+    hits = []
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clk = Clocks(local)
+    clk.start()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record()
+    tops = []
+    for i in range(args.steps):
+        w, _ = step(i, o=step_outs[i])
+        tops.append(w[:, 0])
+    ev1.record()
+    torch.cuda.synchronize()
+    clocks = clk.stop()
+    elapsed = ev0.elapsed_time(ev1) / 1000.0
+    if dist:
+        t = torch.tensor([elapsed], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed = float(t.item())
+        dist.barrier()
+    rm.rope_sync_status()
+    stage_ms = rm.rope_profile_read(args.steps)
+    rm.rope_profile_enable(0)
+    for i, top in enumerate(tops):
+        b = i % n_batches
+        hits.append(np.abs(top.cpu().numpy() - true_pos[b * B:(b + 1) * B]) < wl["N"])
+    acc_bf16 = float(np.concatenate(hits).mean())
+    scores_step = B * W
+    value = ws * args.steps * scores_step / elapsed
+    reads_s = ws * args.steps * B / elapsed
+
+    # roofline of the scan kernel (CUDA events around its launch, same stream)
+    scan_s = float(np.mean(stage_ms[:, 1])) / 1000.0
+    flops = scores_step * 8 * p.dim
+    peaks, peak_src = measured_peaks()
+    peak = peaks["bf16_tflops_sustained"]
+    achieved = flops / scan_s / 1e12
+    trec = traffic_record()
+    roofline = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": (trec["dram_bytes_per_launch_scaled"] * 1.0) if trec else None,
+                "kernel": "scan_tc_kernel (BF16 tcgen05)", "peak_source": f"{peak_src} bf16_tflops_sustained",
+                "flops_per_launch": flops, "ms_per_launch": scan_s * 1000.0,
+                "stage_ms": {"encode": float(np.mean(stage_ms[:, 0])), "scan": float(np.mean(stage_ms[:, 1])),
+                             "merge_rescore": float(np.mean(stage_ms[:, 2]))}}
+
+    # FP32 plain path and BF16 on the same read subset (equal-accuracy check)
+    F = min(args.fp32_reads, B)
+    fo = (torch.empty((F, k), dtype=torch.int64, device="cuda"), torch.empty((F, k), dtype=torch.float32,
+                                                                             device="cuda"))
+    osub = offs[:F + 1]
+    rm.rope_map(idx, seqs, osub, k=k, precision="fp32", out=fo)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    n32 = 2
+    for _ in range(n32):
+        rm.rope_map(idx, seqs, osub, k=k, precision="fp32", out=fo)
+    e1.record()
+    torch.cuda.synchronize()
+    t32 = e0.elapsed_time(e1) / 1000.0 / n32
+    acc32 = float(np.mean(np.abs(fo[0][:, 0].cpu().numpy() - true_pos[:F]) < wl["N"]))
+    bo = rm.rope_map(idx, seqs, osub, k=k, precision="bf16")
+    acc16_sub = float(np.mean(np.abs(bo[0][:, 0].cpu().numpy() - true_pos[:F]) < wl["N"]))
+    agree = float(torch.mean((bo[0][:, 0] == fo[0][:, 0]).float()).item())
+    rm.rope_sync_status()
+    fp32 = {"value": F * W / t32, "unit": UNIT, "reads_per_s": F / t32, "reads": F, "top1_acc": acc32,
+            "bf16_top1_acc_same_reads": acc16_sub, "top1_window_agreement": agree}
+
+    # end to end through host buffers: H2D reads, rope_map, D2H top-k, every step
+    e2e = None
+    if args.e2e_steps > 0:
+        b0 = 0
+        o_h = rd.offsets[b0 * B:(b0 + 1) * B + 1]
+        s_h = rd.seqs[o_h[0]:o_h[-1]]
+        seq_pin = torch.from_numpy(np.ascontiguousarray(s_h)).pin_memory()
+        off_pin = torch.from_numpy(np.ascontiguousarray(o_h - o_h[0])).pin_memory()
+        w_pin = torch.empty((B, k), dtype=torch.int64).pin_memory()
+        s_pin = torch.empty((B, k), dtype=torch.float32).pin_memory()
+        dseq = torch.empty(seq_pin.shape, dtype=torch.uint8, device="cuda")
+        doff = torch.empty(off_pin.shape, dtype=torch.int64, device="cuda")
+        for it in range(2 + args.e2e_steps):
+            if it == 2:
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+            dseq.copy_(seq_pin, non_blocking=True)
+            doff.copy_(off_pin, non_blocking=True)
+            w_, s_ = rm.rope_map(idx, dseq, doff, k=k, precision="bf16", out=outs)
+            w_pin.copy_(w_, non_blocking=True)
+            s_pin.copy_(s_, non_blocking=True)
+            torch.cuda.synchronize()
+        te = (time.perf_counter() - t0) / args.e2e_steps
+        if dist:
+            t = torch.tensor([te], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            te = float(t.item())
+        e2e = {"value": ws * scores_step / te, "unit": UNIT, "reads_per_s": ws * B / te,
+               "h2d_bytes_per_step": int(seq_pin.numel() + off_pin.numel() * 8),
+               "d2h_bytes_per_step": int(w_pin.numel() * 8 + s_pin.numel() * 4)}
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu:
+        cpu = cpu_baseline(ref, rd, wl, args.cpu_reads, args.cpu_windows)
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1000.0 * elapsed / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+        "config": {"workload": args.workload + ": " + wl["desc"], "reads_per_step_per_gpu": B, "n_windows": W,
+                   "scores_per_step_per_gpu": scores_step, "l2": "inputs larger than L2 (0.8 GB index streamed "
+                   "per scan pass; reads 20 MB/step)", "index_build_s": index_s, "parallelism": f"replicated index, "
+                   f"reads sharded over {ws} GPU(s)"},
+        "reads_per_s": reads_s, "top1_acc": acc_bf16, "fp32_plain": fp32,
+        "speedup_vs_fp32_plain": value / ws / fp32["value"],
+        "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": 3 * args.steps, "clocks": clocks,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    idx.free()
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

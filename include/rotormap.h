@@ -1,0 +1,215 @@
+/*
+ * rotormap.h — C ABI of the GB300 (sm_103a) RotorMap hot path.
+ *
+ * RotorMap (§3) maps a DNA read to a reference by encoding the read's head of
+ * length N with the RoPE encoding (§2) and scoring it against the encoding of
+ * every length-N window of the reference (§3.1), keeping the best loci
+ * (§3.5). This library computes, on one GPU:
+ *   - the 2-bit packing of letters and the s-mer bin codes (§2.1, §2.6),
+ *   - the RoPE encodings of read heads by direct summation (§2.1-§2.3, §3.3),
+ *   - the encodings of all reference windows, generated on chip by the
+ *     slide-by-one recurrence of §3.4 from periodic exact anchors (never stored),
+ *   - the read x window fidelity |<x|c>|^2/(|x|^2 |c|^2) (§2.4) as a real
+ *     contraction (§4 identity) on the tensor cores (BF16 in, FP32 accumulate)
+ *     or on the CUDA cores in FP32, fused with a per-read top-k (§3.5),
+ *   - an FP32 re-scoring of the best candidates by direct summation.
+ *
+ * Conventions
+ *   - Pointers are DEVICE pointers unless the name ends in _host.
+ *   - Outputs are allocated by the caller. The library owns only rope_index
+ *     objects and the per-call scratch it takes from its own stream-ordered
+ *     memory pool (released back to the pool on the same stream).
+ *   - Calls are asynchronous on `stream` unless stated otherwise. Errors found
+ *     on the host are returned at once; errors found by a kernel (a letter
+ *     outside {A,C,G,T}, a read shorter than N, a wait that ran out) are
+ *     recorded in a device status word and returned by rope_sync_status().
+ *   - Nothing is thrown across the ABI. rope_last_error() gives a per-thread
+ *     message for the last failing call.
+ *   - Letters: A,C,G,T in either case map to 0,1,2,3. Window j starts at
+ *     reference position j*stride; window starts and counts are int64.
+ *   - Vectors: an encoding has D = m*4^t complex entries, band-major (entry
+ *     (k-1)*4^t + b for factor k and bin b). As reals it is stored
+ *     [re_0..re_{D-1}, im_0..im_{D-1}] (2D floats).
+ */
+#ifndef ROTORMAP_H
+#define ROTORMAP_H
+
+#include <stdint.h>
+#include <cuda_runtime_api.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  ROPE_OK = 0,
+  ROPE_ERR_INVALID_ARG = 1,   /* bad parameter, size or pointer                  */
+  ROPE_ERR_INVALID_BASE = 2,  /* a letter outside {A,C,G,T,a,c,g,t}              */
+  ROPE_ERR_OOM = 3,           /* device allocation failed                        */
+  ROPE_ERR_CUDA = 4,          /* a CUDA runtime call failed                      */
+  ROPE_ERR_TIMEOUT = 5,       /* a bounded in-kernel wait ran out                */
+  ROPE_ERR_UNSUPPORTED = 6    /* parameters valid but not built for this path    */
+} rope_status;
+
+/* Encoding and window parameters.
+ *   s        s-mer length, 1 <= s <= 8 (§2.1)
+ *   m        number of multiplicity factors, 1 <= m <= 8 (§2.2, §2.3)
+ *   t        compact bin exponent, 1 <= t <= s: 4^s s-mers fold onto 4^t bins
+ *            (§2.6); m*4^t <= 4096
+ *   variant  0 = default factors f_k = k (§2.2 Eq. mult-factor),
+ *            1 = fine-tuned f_k = 2(k-1)/(m-1)+1 (§3.3 Eq. mult-factor-finetune;
+ *                f_1 = 1 when m = 1)
+ *   score_mode 0 = fidelity of the concatenated normalised vector (§2.3, §2.4);
+ *            1 = mean over k of per-band fidelities (§2.5)
+ *   window_len N, the window and read-head length (§3.1), s <= N <= 65536
+ *   stride   window step (§3.1), 1 <= stride <= 64
+ *   bin_of_mer_host  4^s entries in [0, 4^t) mapping s-mer code
+ *            sum_i base(p+i) 4^(s-1-i) to its bin; NULL selects the identity
+ *            when s == t and Knuth's multiplicative hash
+ *            (code * 0x9E3779B97F4A7C15 mod 2^64) >> (64-2t) otherwise. Copied
+ *            at the call; the caller keeps ownership. */
+typedef struct {
+  int32_t s, m, t;
+  int32_t variant;
+  int32_t score_mode;
+  int32_t window_len;
+  int32_t stride;
+  int32_t reserved0;
+  const uint16_t* bin_of_mer_host;
+} rope_params;
+
+/* Scoring precision */
+enum { ROPE_PREC_FP32 = 0, ROPE_PREC_BF16 = 1 };
+
+/* Options of rope_score_topk.
+ *   k          results per read, 1 <= k <= 32
+ *   sep        0: plain top-k. sep > 0: at most one window per bucket
+ *              floor(start/sep) (the best), then the best k buckets
+ *   precision  ROPE_PREC_FP32 (CUDA cores) or ROPE_PREC_BF16 (tensor cores)
+ *   rescore    1: re-score the kept candidates by direct FP32 summation before
+ *              the final ranking; 0: report the scan's own scores
+ *   cand_depth candidates kept per read per window range (0 = 16); k..32
+ *   rescore_depth candidates re-scored per read (0 = 2*k, capped at 32)
+ *   j_begin, j_end  window-number range [j_begin, j_end) scanned; j_end <= 0
+ *              means all windows
+ *   n_ranges   window ranges the scan is split into (0 = automatic) */
+typedef struct {
+  int32_t k;
+  int32_t sep;
+  int32_t precision;
+  int32_t rescore;
+  int32_t cand_depth;
+  int32_t rescore_depth;
+  int32_t n_ranges;
+  int32_t reserved0;
+  int64_t j_begin;
+  int64_t j_end;
+} rope_score_opts;
+
+typedef struct rope_index rope_index;
+
+/* Name of a status code (static string). */
+const char* rope_status_string(rope_status st);
+
+/* Message of the last failing call on this host thread (static storage). */
+const char* rope_last_error(void);
+
+/* Complex dimension m*4^t of valid params, else -1. */
+int32_t rope_dim(const rope_params* p);
+
+/* Synchronises `stream`, then returns and clears the device status word of
+ * the current device: ROPE_OK, ROPE_ERR_INVALID_BASE, ROPE_ERR_INVALID_ARG
+ * (a read shorter than N) or ROPE_ERR_TIMEOUT. */
+rope_status rope_sync_status(cudaStream_t stream);
+
+/* ---- step a1: 2-bit packing (§2.1 alphabet) ------------------------------
+ * seq: len letters (uint8). out_words: ceil(len/16) uint32; base i goes to
+ * bits 2*(i mod 16) of word i/16, unused high bits of the last word are 0.
+ * An invalid letter sets ROPE_ERR_INVALID_BASE in the status word. */
+rope_status rope_pack_2bit(const uint8_t* seq, int64_t len, uint32_t* out_words, cudaStream_t stream);
+
+/* ---- step a2: s-mer bins (§2.1 locations, §2.6 compact map) -------------
+ * packed: words from rope_pack_2bit for a sequence of `len` letters.
+ * out_bins: len-s+1 uint16, out_bins[p] = bin of the s-mer at location p. */
+rope_status rope_mer_bins(const rope_params* p, const uint32_t* packed, int64_t len, uint16_t* out_bins,
+                          cudaStream_t stream);
+
+/* ---- reference index (§3.1) ---------------------------------------------
+ * ref: len letters on the device. Packs the reference, and for every window
+ * j < W = floor((len-N)/stride)+1 computes its squared norm exactly enough
+ * (FP64 recurrence from FP64 anchors) to store 1/sqrt(C_j) in FP32 (0 for a
+ * zero vector, whose fidelity is 0), per-band norms when score_mode = 1, and
+ * the FP32 anchors c(j) every 64 windows that seed the on-chip recurrence.
+ * Requires 1 <= W < 2^32. Synchronous: returns after the index is built.
+ * *out receives a new index owned by the caller (free with rope_index_free). */
+rope_status rope_encode_reference(const rope_params* p, const uint8_t* ref, int64_t len, rope_index** out,
+                                  cudaStream_t stream);
+
+/* Frees an index (NULL is allowed). Synchronises the device first. */
+void rope_index_free(rope_index* idx);
+
+/* Index facts: number of windows, reference length, anchor period, and the
+ * device arrays (packed words, 1/sqrt(C_j)); any output pointer may be NULL. */
+rope_status rope_index_info(const rope_index* idx, int64_t* n_windows, int64_t* ref_len, int32_t* anchor_period,
+                            const uint32_t** packed, const float** inv_norm);
+
+/* ---- step a4: window encodings (§3.4 recurrence), for inspection --------
+ * Writes c(j) for j in [j_begin, j_begin+count) as count x 2D floats,
+ * unnormalised, generated by the same on-chip recurrence the scans use. */
+rope_status rope_window_embeddings(const rope_index* idx, int64_t j_begin, int64_t count, float* out,
+                                   cudaStream_t stream);
+
+/* ---- step a3: read encoding (§2.1-§2.3, §3.3) ---------------------------
+ * seqs: concatenated reads (uint8 letters); offsets: n_reads+1 int64 (read r
+ * is seqs[offsets[r], offsets[r+1])); only the head of length N is encoded
+ * and every read must have at least N letters.
+ *   emb_f32  n_reads x 2D floats, the unnormalised encoding (may be NULL)
+ *   emb_bf16 n_reads x 2D bf16 (uint16 bits), the encoding divided by its norm
+ *            (zero for a zero vector); the tensor-core operand (may be NULL)
+ *   norms    n_reads x (1+m) floats: |x|^2, then |x_k|^2 per band (required) */
+rope_status rope_encode_reads(const rope_params* p, const uint8_t* seqs, const int64_t* offsets, int64_t n_reads,
+                              float* emb_f32, uint16_t* emb_bf16, float* norms, cudaStream_t stream);
+
+/* ---- steps a4-a7: scan, fidelity, top-k, re-scoring (§3.1, §3.4, §3.5) --
+ * Scores every read against every window in the range and writes, per read,
+ * k window starts (int64, j*stride) and fidelities (float), best first
+ * (score descending, start ascending); missing entries are (-1, -inf).
+ * emb_f32/norms come from rope_encode_reads; emb_bf16 is required for
+ * ROPE_PREC_BF16. Uses scratch from the library's stream-ordered pool. */
+rope_status rope_score_topk(const rope_index* idx, const float* emb_f32, const uint16_t* emb_bf16,
+                            const float* norms, int64_t n_reads, const rope_score_opts* opts, int64_t* out_win,
+                            float* out_score, cudaStream_t stream);
+
+/* Every score of every read against windows [j_begin, j_begin+count), as
+ * n_reads x count floats, computed by the same scan kernel as rope_score_topk
+ * (FP32 or BF16 tensor-core path) with its top-k stage replaced by a store.
+ * For parity checks on small cases. */
+rope_status rope_score_dense(const rope_index* idx, const float* emb_f32, const uint16_t* emb_bf16,
+                             const float* norms, int64_t n_reads, int32_t precision, int64_t j_begin, int64_t count,
+                             float* out, cudaStream_t stream);
+
+/* ---- the whole path (§3.1, §3.5) ----------------------------------------
+ * Encodes the heads of the reads and scans them against the index; writes k
+ * window starts and fidelities per read as rope_score_topk does. `opts` as
+ * for rope_score_topk (j range ignored). Reads shorter than N are an error. */
+rope_status rope_map(const rope_index* idx, const uint8_t* seqs, const int64_t* offsets, int64_t n_reads,
+                     const rope_score_opts* opts, int64_t* out_win, float* out_score, cudaStream_t stream);
+
+/* ---- stage timing (tracing) ---------------------------------------------
+ * rope_profile_enable(max_calls) starts recording: every following
+ * rope_score_topk / rope_map call (up to max_calls) records CUDA events on its
+ * stream around its three stages (read encoding, scan, merge/re-score);
+ * max_calls = 0 stops recording and frees the events.
+ * rope_profile_read() synchronises those events and writes, per recorded
+ * call, the milliseconds of [encode, scan, merge] (encode is 0 for
+ * rope_score_topk) into ms[3*i .. 3*i+2]; *n_calls receives the number of
+ * calls recorded (at most `capacity`). Host-thread-safe; one recorder per
+ * process. */
+rope_status rope_profile_enable(int32_t max_calls);
+rope_status rope_profile_read(float* ms_host, int32_t capacity, int32_t* n_calls);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ROTORMAP_H */

@@ -1,0 +1,726 @@
+// C ABI of the RotorMap GB300 library (see include/rotormap.h).
+//
+// Host responsibilities: validation, the exact phase tables (factor f_k held as
+// the fraction a_k/q so that every exponent is reduced in integers before the
+// FP64 trigonometric call), the default 4^s -> 4^t map, index construction,
+// per-call scratch from a stream-ordered memory pool, and launch geometry.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "rope_internal.h"
+#include "rotormap.h"
+
+using namespace rope;
+
+// ---------------------------------------------------------------- errors
+
+static thread_local char g_last_error[512] = "";
+
+static rope_status fail(rope_status st, const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_last_error, sizeof(g_last_error), fmt, ap);
+  va_end(ap);
+  return st;
+}
+
+#define ROPE_CUDA(call)                                                                               \
+  do {                                                                                                \
+    cudaError_t e_ = (call);                                                                          \
+    if (e_ != cudaSuccess) return fail(ROPE_ERR_CUDA, "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), \
+                                       __FILE__, __LINE__);                                           \
+  } while (0)
+
+extern "C" const char* rope_status_string(rope_status st) {
+  switch (st) {
+    case ROPE_OK: return "ROPE_OK";
+    case ROPE_ERR_INVALID_ARG: return "ROPE_ERR_INVALID_ARG";
+    case ROPE_ERR_INVALID_BASE: return "ROPE_ERR_INVALID_BASE";
+    case ROPE_ERR_OOM: return "ROPE_ERR_OOM";
+    case ROPE_ERR_CUDA: return "ROPE_ERR_CUDA";
+    case ROPE_ERR_TIMEOUT: return "ROPE_ERR_TIMEOUT";
+    case ROPE_ERR_UNSUPPORTED: return "ROPE_ERR_UNSUPPORTED";
+  }
+  return "ROPE_ERR_UNKNOWN";
+}
+
+extern "C" const char* rope_last_error(void) { return g_last_error; }
+
+// ---------------------------------------------------------------- per-device context
+
+namespace {
+
+struct DeviceCtx {
+  int* status = nullptr;       // device status word
+  cudaMemPool_t pool = nullptr;
+  int num_sms = 0;
+};
+
+std::mutex g_mu;
+std::map<int, DeviceCtx> g_ctx;
+
+rope_status get_ctx(DeviceCtx** out) {
+  int dev = 0;
+  ROPE_CUDA(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lk(g_mu);
+  auto it = g_ctx.find(dev);
+  if (it != g_ctx.end()) {
+    *out = &it->second;
+    return ROPE_OK;
+  }
+  DeviceCtx c;
+  ROPE_CUDA(cudaDeviceGetAttribute(&c.num_sms, cudaDevAttrMultiProcessorCount, dev));
+  ROPE_CUDA(cudaMalloc(&c.status, sizeof(int)));
+  ROPE_CUDA(cudaMemset(c.status, 0, sizeof(int)));
+  cudaMemPoolProps props;
+  memset(&props, 0, sizeof(props));
+  props.allocType = cudaMemAllocationTypePinned;
+  props.location.type = cudaMemLocationTypeDevice;
+  props.location.id = dev;
+  ROPE_CUDA(cudaMemPoolCreate(&c.pool, &props));
+  uint64_t keep = ~0ull;  // keep freed blocks in the pool for reuse
+  ROPE_CUDA(cudaMemPoolSetAttribute(c.pool, cudaMemPoolAttrReleaseThreshold, &keep));
+  auto res = g_ctx.emplace(dev, c);
+  *out = &res.first->second;
+  return ROPE_OK;
+}
+
+rope_status pool_alloc(DeviceCtx* c, void** p, size_t bytes, cudaStream_t st) {
+  if (bytes == 0) bytes = 16;
+  cudaError_t e = cudaMallocFromPoolAsync(p, bytes, c->pool, st);
+  if (e == cudaErrorMemoryAllocation) return fail(ROPE_ERR_OOM, "scratch allocation of %zu bytes failed", bytes);
+  if (e != cudaSuccess) return fail(ROPE_ERR_CUDA, "cudaMallocFromPoolAsync: %s", cudaGetErrorString(e));
+  return ROPE_OK;
+}
+
+// ---------------------------------------------------------------- parameters and tables
+
+rope_status check_params(const rope_params* p) {
+  if (!p) return fail(ROPE_ERR_INVALID_ARG, "params is NULL");
+  if (p->s < 1 || p->s > 8) return fail(ROPE_ERR_INVALID_ARG, "s=%d outside [1,8]", p->s);
+  if (p->t < 1 || p->t > p->s) return fail(ROPE_ERR_INVALID_ARG, "t=%d outside [1,s]", p->t);
+  if (p->m < 1 || p->m > 8) return fail(ROPE_ERR_INVALID_ARG, "m=%d outside [1,8]", p->m);
+  if ((int64_t)p->m << (2 * p->t) > 4096) return fail(ROPE_ERR_INVALID_ARG, "m*4^t > 4096");
+  if (p->variant != 0 && p->variant != 1) return fail(ROPE_ERR_INVALID_ARG, "variant=%d", p->variant);
+  if (p->score_mode != 0 && p->score_mode != 1) return fail(ROPE_ERR_INVALID_ARG, "score_mode=%d", p->score_mode);
+  if (p->window_len < p->s || p->window_len > 65536)
+    return fail(ROPE_ERR_INVALID_ARG, "window_len=%d outside [s,65536]", p->window_len);
+  if (p->stride < 1 || p->stride > 64) return fail(ROPE_ERR_INVALID_ARG, "stride=%d outside [1,64]", p->stride);
+  if (p->bin_of_mer_host) {
+    const int nb = 1 << (2 * p->t);
+    for (int i = 0; i < (1 << (2 * p->s)); ++i)
+      if (p->bin_of_mer_host[i] >= nb) return fail(ROPE_ERR_INVALID_ARG, "bin_of_mer[%d] >= 4^t", i);
+  }
+  return ROPE_OK;
+}
+
+// f_k = a_k / q (default: k/1; fine-tuned: (2k+m-3)/(m-1), f = 1 when m = 1)
+void factor(const rope_params& p, int k, int64_t* a, int64_t* q) {
+  if (p.variant == 1 && p.m > 1) {
+    *a = 2 * (int64_t)k + p.m - 3;
+    *q = p.m - 1;
+  } else {
+    *a = k;
+    *q = 1;
+  }
+}
+
+// exp(2 pi i a x / (q N)) with the exponent reduced modulo qN in integers
+double2 unit(int64_t a, int64_t q, int64_t N, int64_t x) {
+  const int64_t Q = q * N;
+  int64_t r = (a * x) % Q;
+  if (r < 0) r += Q;
+  const double ang = 6.283185307179586476925286766559 * (double)r / (double)Q;
+  return make_double2(std::cos(ang), std::sin(ang));
+}
+
+struct HostTables {
+  std::vector<uint16_t> map;      // 4^s, code with the first letter most significant
+  std::vector<uint16_t> map_lsb;  // 4^s, little-endian 2-bit letter field
+  std::vector<double2> phase, rot, eout, ein;
+  int nb = 0, D = 0, n_loc = 0;
+};
+
+void build_tables(const rope_params& p, HostTables& h) {
+  const int n_codes = 1 << (2 * p.s);
+  h.nb = 1 << (2 * p.t);
+  h.D = p.m * h.nb;
+  h.n_loc = p.window_len - p.s + 1;
+  h.map.resize(n_codes);
+  for (int c = 0; c < n_codes; ++c) {
+    if (p.bin_of_mer_host) {
+      h.map[c] = p.bin_of_mer_host[c];
+    } else if (p.s == p.t) {
+      h.map[c] = (uint16_t)c;
+    } else {
+      const uint64_t x = (uint64_t)c * 0x9E3779B97F4A7C15ull;
+      h.map[c] = (uint16_t)(x >> (64 - 2 * p.t));
+    }
+  }
+  h.map_lsb.resize(n_codes);
+  for (int v = 0; v < n_codes; ++v) {
+    int code = 0;
+    for (int i = 0; i < p.s; ++i) code = code * 4 + ((v >> (2 * i)) & 3);  // letter i at bits 2i
+    h.map_lsb[v] = h.map[code];
+  }
+  const int S = p.stride, N = p.window_len;
+  h.phase.resize((size_t)p.m * h.n_loc);
+  h.rot.resize(p.m);
+  h.eout.resize((size_t)p.m * S);
+  h.ein.resize((size_t)p.m * S);
+  for (int k = 1; k <= p.m; ++k) {
+    int64_t a, q;
+    factor(p, k, &a, &q);
+    for (int loc = 0; loc < h.n_loc; ++loc) h.phase[(size_t)(k - 1) * h.n_loc + loc] = unit(a, q, N, loc);
+    h.rot[k - 1] = unit(a, q, N, -S);
+    for (int u = 0; u < S; ++u) {
+      h.eout[(size_t)(k - 1) * S + u] = unit(a, q, N, u);
+      h.ein[(size_t)(k - 1) * S + u] = unit(a, q, N, N - p.s + 1 + u);
+    }
+  }
+}
+
+std::vector<float2> to_f32(const std::vector<double2>& v) {
+  std::vector<float2> o(v.size());
+  for (size_t i = 0; i < v.size(); ++i) o[i] = make_float2((float)v[i].x, (float)v[i].y);
+  return o;
+}
+
+template <class T>
+rope_status upload(std::vector<void*>& owned, const std::vector<T>& v, T** out, size_t pad_elems = 0) {
+  void* d = nullptr;
+  const size_t bytes = (v.size() + pad_elems) * sizeof(T);
+  cudaError_t e = cudaMalloc(&d, bytes ? bytes : 16);
+  if (e != cudaSuccess) return fail(ROPE_ERR_OOM, "cudaMalloc(%zu): %s", bytes, cudaGetErrorString(e));
+  owned.push_back(d);
+  if (bytes) {
+    ROPE_CUDA(cudaMemset(d, 0, bytes));
+    if (!v.empty()) ROPE_CUDA(cudaMemcpy(d, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice));
+  }
+  *out = static_cast<T*>(d);
+  return ROPE_OK;
+}
+
+// Device tables for read encoding, cached per device and parameter set.
+struct EncEntry {
+  std::vector<void*> owned;
+  EncTables tb;
+};
+std::map<std::string, EncEntry> g_enc_cache;
+
+std::string enc_key(int dev, const rope_params& p) {
+  std::string k = std::to_string(dev) + ":" + std::to_string(p.s) + "," + std::to_string(p.m) + "," +
+                  std::to_string(p.t) + "," + std::to_string(p.variant) + "," + std::to_string(p.window_len) + ":";
+  if (p.bin_of_mer_host) {
+    uint64_t h = 1469598103934665603ull;
+    for (int i = 0; i < (1 << (2 * p.s)); ++i) h = (h ^ p.bin_of_mer_host[i]) * 1099511628211ull;
+    k += std::to_string(h);
+  } else {
+    k += "default";
+  }
+  return k;
+}
+
+rope_status get_enc_tables(const rope_params& p, EncTables* out) {
+  int dev = 0;
+  ROPE_CUDA(cudaGetDevice(&dev));
+  const std::string key = enc_key(dev, p);
+  std::lock_guard<std::mutex> lk(g_mu);
+  auto it = g_enc_cache.find(key);
+  if (it != g_enc_cache.end()) {
+    *out = it->second.tb;
+    return ROPE_OK;
+  }
+  HostTables h;
+  build_tables(p, h);
+  EncEntry e;
+  uint16_t* map = nullptr;
+  float2* ph = nullptr;
+  rope_status st = upload(e.owned, h.map, &map);
+  if (st == ROPE_OK) st = upload(e.owned, to_f32(h.phase), &ph);
+  if (st != ROPE_OK) {
+    for (void* q : e.owned) cudaFree(q);
+    return st;
+  }
+  e.tb = EncTables{p.window_len, p.s, p.m, p.t, h.nb, h.D, map, ph};
+  g_enc_cache.emplace(key, e);
+  *out = e.tb;
+  return ROPE_OK;
+}
+
+// Stage recorder: CUDA events around encode / scan / merge of each call.
+struct Profiler {
+  std::mutex mu;
+  int cap = 0, used = 0;
+  std::vector<cudaEvent_t> ev;  // 4 per call: start, encoded, scanned, merged
+};
+Profiler g_prof;
+
+int prof_begin(cudaStream_t st) {
+  std::lock_guard<std::mutex> lk(g_prof.mu);
+  if (g_prof.used >= g_prof.cap) return -1;
+  const int slot = g_prof.used++;
+  cudaEventRecord(g_prof.ev[4 * slot], st);
+  return slot;
+}
+
+void prof_mark(int slot, int which, cudaStream_t st) {
+  if (slot >= 0) cudaEventRecord(g_prof.ev[4 * slot + which], st);
+}
+
+}  // namespace
+
+extern "C" rope_status rope_profile_enable(int32_t max_calls) {
+  if (max_calls < 0) return fail(ROPE_ERR_INVALID_ARG, "max_calls < 0");
+  std::lock_guard<std::mutex> lk(g_prof.mu);
+  for (cudaEvent_t e : g_prof.ev) cudaEventDestroy(e);
+  g_prof.ev.clear();
+  g_prof.cap = g_prof.used = 0;
+  for (int i = 0; i < 4 * max_calls; ++i) {
+    cudaEvent_t e;
+    ROPE_CUDA(cudaEventCreate(&e));
+    g_prof.ev.push_back(e);
+  }
+  g_prof.cap = max_calls;
+  return ROPE_OK;
+}
+
+extern "C" rope_status rope_profile_read(float* ms_host, int32_t capacity, int32_t* n_calls) {
+  std::lock_guard<std::mutex> lk(g_prof.mu);
+  const int n = g_prof.used < capacity ? g_prof.used : capacity;
+  for (int i = 0; i < n; ++i) {
+    ROPE_CUDA(cudaEventSynchronize(g_prof.ev[4 * i + 3]));
+    for (int k = 0; k < 3; ++k) {
+      float ms = 0.f;
+      ROPE_CUDA(cudaEventElapsedTime(&ms, g_prof.ev[4 * i + k], g_prof.ev[4 * i + k + 1]));
+      ms_host[3 * i + k] = ms;
+    }
+  }
+  if (n_calls) *n_calls = n;
+  return ROPE_OK;
+}
+
+// ---------------------------------------------------------------- index
+
+struct rope_index {
+  int device = 0;
+  rope_params p{};
+  DevIndex ix{};
+  EncTables enc{};
+  std::vector<void*> owned;
+};
+
+extern "C" int32_t rope_dim(const rope_params* p) {
+  if (check_params(p) != ROPE_OK) return -1;
+  return p->m << (2 * p->t);
+}
+
+extern "C" rope_status rope_sync_status(cudaStream_t stream) {
+  DeviceCtx* c;
+  rope_status st = get_ctx(&c);
+  if (st != ROPE_OK) return st;
+  ROPE_CUDA(cudaStreamSynchronize(stream));
+  int v = 0;
+  ROPE_CUDA(cudaMemcpy(&v, c->status, sizeof(int), cudaMemcpyDeviceToHost));
+  ROPE_CUDA(cudaMemset(c->status, 0, sizeof(int)));
+  if (v & kStatusTimeout) return fail(ROPE_ERR_TIMEOUT, "a bounded in-kernel wait ran out");
+  if (v & kStatusBadBase) return fail(ROPE_ERR_INVALID_BASE, "letter outside {A,C,G,T}");
+  if (v & kStatusShortRead) return fail(ROPE_ERR_INVALID_ARG, "a read is shorter than the window length");
+  if (v & kStatusBadArg) return fail(ROPE_ERR_INVALID_ARG, "a kernel saw an out-of-range argument");
+  return ROPE_OK;
+}
+
+extern "C" rope_status rope_pack_2bit(const uint8_t* seq, int64_t len, uint32_t* out_words, cudaStream_t stream) {
+  if (len < 0 || (len > 0 && (!seq || !out_words))) return fail(ROPE_ERR_INVALID_ARG, "bad pack arguments");
+  DeviceCtx* c;
+  rope_status st = get_ctx(&c);
+  if (st != ROPE_OK) return st;
+  ROPE_CUDA(launch_pack(seq, len, out_words, c->status, stream));
+  return ROPE_OK;
+}
+
+extern "C" rope_status rope_mer_bins(const rope_params* p, const uint32_t* packed, int64_t len, uint16_t* out_bins,
+                                     cudaStream_t stream) {
+  rope_status st = check_params(p);
+  if (st != ROPE_OK) return st;
+  if (len < p->s) return fail(ROPE_ERR_INVALID_ARG, "len < s");
+  if (!packed || !out_bins) return fail(ROPE_ERR_INVALID_ARG, "NULL pointer");
+  HostTables h;
+  build_tables(*p, h);
+  uint16_t* d_map = nullptr;
+  ROPE_CUDA(cudaMallocAsync((void**)&d_map, h.map_lsb.size() * sizeof(uint16_t), stream));
+  ROPE_CUDA(cudaMemcpyAsync(d_map, h.map_lsb.data(), h.map_lsb.size() * sizeof(uint16_t), cudaMemcpyHostToDevice,
+                            stream));
+  ROPE_CUDA(launch_mer_bins(packed, len, (len + 15) / 16, p->s, d_map, out_bins, stream));
+  ROPE_CUDA(cudaStreamSynchronize(stream));  // the host table must outlive the copy
+  ROPE_CUDA(cudaFreeAsync(d_map, stream));
+  return ROPE_OK;
+}
+
+extern "C" void rope_index_free(rope_index* idx) {
+  if (!idx) return;
+  int prev = 0;
+  cudaGetDevice(&prev);
+  cudaSetDevice(idx->device);
+  cudaDeviceSynchronize();
+  for (void* q : idx->owned) cudaFree(q);
+  cudaSetDevice(prev);
+  delete idx;
+}
+
+extern "C" rope_status rope_encode_reference(const rope_params* p, const uint8_t* ref, int64_t len, rope_index** out,
+                                             cudaStream_t stream) {
+  rope_status st = check_params(p);
+  if (st != ROPE_OK) return st;
+  if (!out) return fail(ROPE_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (!ref || len < p->window_len) return fail(ROPE_ERR_INVALID_ARG, "reference shorter than the window");
+  const int D = p->m << (2 * p->t);
+  if (D > kMaxScanDim) return fail(ROPE_ERR_UNSUPPORTED, "index dimension %d > %d", D, kMaxScanDim);
+  const int64_t W = (len - p->window_len) / p->stride + 1;
+  if (W >= (int64_t)0xFFFFFFFF) return fail(ROPE_ERR_UNSUPPORTED, "more than 2^32-1 windows");
+  DeviceCtx* c;
+  st = get_ctx(&c);
+  if (st != ROPE_OK) return st;
+
+  rope_index* idx = new rope_index();
+  ROPE_CUDA(cudaGetDevice(&idx->device));
+  idx->p = *p;
+  idx->p.bin_of_mer_host = nullptr;
+  HostTables h;
+  build_tables(*p, h);
+  const int A = kAnchorPeriod;
+  const int64_t n_words = (len + 15) / 16;
+  const int64_t pad_words = 16384 + kPackPadWords;
+  const int64_t n_anchor = (W + A - 1) / A;
+
+  auto cleanup = [&](rope_status s) {
+    rope_index_free(idx);
+    return s;
+  };
+  std::vector<uint32_t> none;
+  uint32_t* packed = nullptr;
+  float* inv_norm = nullptr;
+  float* band_norm = nullptr;
+  float2* anchors = nullptr;
+  uint16_t *map_lsb = nullptr, *map = nullptr;
+  float2 *phase = nullptr, *rot = nullptr, *eout = nullptr, *ein = nullptr;
+  double2 *phase64 = nullptr, *rot64 = nullptr, *eout64 = nullptr, *ein64 = nullptr;
+  if ((st = upload(idx->owned, std::vector<uint32_t>(), &packed, (size_t)(n_words + pad_words))) != ROPE_OK)
+    return cleanup(st);
+  if ((st = upload(idx->owned, std::vector<float>(), &inv_norm, (size_t)W + 8192)) != ROPE_OK) return cleanup(st);
+  if (p->score_mode == 1 &&
+      (st = upload(idx->owned, std::vector<float>(), &band_norm, (size_t)W * p->m + 8192)) != ROPE_OK)
+    return cleanup(st);
+  if ((st = upload(idx->owned, std::vector<float2>(), &anchors, (size_t)(n_anchor + 128) * D)) != ROPE_OK)
+    return cleanup(st);
+  if ((st = upload(idx->owned, h.map_lsb, &map_lsb)) != ROPE_OK) return cleanup(st);
+  if ((st = upload(idx->owned, h.map, &map)) != ROPE_OK) return cleanup(st);
+  if ((st = upload(idx->owned, to_f32(h.phase), &phase)) != ROPE_OK) return cleanup(st);
+  if ((st = upload(idx->owned, to_f32(h.rot), &rot)) != ROPE_OK) return cleanup(st);
+  if ((st = upload(idx->owned, to_f32(h.eout), &eout)) != ROPE_OK) return cleanup(st);
+  if ((st = upload(idx->owned, to_f32(h.ein), &ein)) != ROPE_OK) return cleanup(st);
+  if ((st = upload(idx->owned, h.phase, &phase64)) != ROPE_OK) return cleanup(st);
+  if ((st = upload(idx->owned, h.rot, &rot64)) != ROPE_OK) return cleanup(st);
+  if ((st = upload(idx->owned, h.eout, &eout64)) != ROPE_OK) return cleanup(st);
+  if ((st = upload(idx->owned, h.ein, &ein64)) != ROPE_OK) return cleanup(st);
+
+  DevIndex& ix = idx->ix;
+  ix.packed = packed;
+  ix.L = len;
+  ix.W = W;
+  ix.N = p->window_len;
+  ix.s = p->s;
+  ix.m = p->m;
+  ix.t = p->t;
+  ix.nb = h.nb;
+  ix.D = D;
+  ix.stride = p->stride;
+  ix.A = A;
+  ix.variant = p->variant;
+  ix.score_mode = p->score_mode;
+  ix.inv_norm = inv_norm;
+  ix.band_norm = band_norm;
+  ix.anchors = anchors;
+  ix.map_lsb = map_lsb;
+  ix.phase = phase;
+  ix.rot = rot;
+  ix.eout = eout;
+  ix.ein = ein;
+  idx->enc = EncTables{p->window_len, p->s, p->m, p->t, h.nb, D, map, phase};
+
+  // clear stale status, pack, pre-pass
+  int zero = 0;
+  cudaError_t e = cudaMemcpy(c->status, &zero, sizeof(int), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = launch_pack(ref, len, packed, c->status, stream);
+  if (e == cudaSuccess) {
+    PrepassTables pt{phase64, rot64, eout64, ein64};
+    e = launch_prepass(ix, pt, anchors, inv_norm, band_norm, c->status, stream);
+  }
+  if (e != cudaSuccess) return cleanup(fail(ROPE_ERR_CUDA, "index build launch: %s", cudaGetErrorString(e)));
+  st = rope_sync_status(stream);
+  if (st != ROPE_OK) return cleanup(st);
+  *out = idx;
+  return ROPE_OK;
+}
+
+extern "C" rope_status rope_index_info(const rope_index* idx, int64_t* n_windows, int64_t* ref_len,
+                                       int32_t* anchor_period, const uint32_t** packed, const float** inv_norm) {
+  if (!idx) return fail(ROPE_ERR_INVALID_ARG, "index is NULL");
+  if (n_windows) *n_windows = idx->ix.W;
+  if (ref_len) *ref_len = idx->ix.L;
+  if (anchor_period) *anchor_period = idx->ix.A;
+  if (packed) *packed = idx->ix.packed;
+  if (inv_norm) *inv_norm = idx->ix.inv_norm;
+  return ROPE_OK;
+}
+
+extern "C" rope_status rope_window_embeddings(const rope_index* idx, int64_t j_begin, int64_t count, float* out,
+                                              cudaStream_t stream) {
+  if (!idx || !out) return fail(ROPE_ERR_INVALID_ARG, "NULL argument");
+  if (j_begin < 0 || count < 0 || j_begin + count > idx->ix.W) return fail(ROPE_ERR_INVALID_ARG, "window range");
+  ROPE_CUDA(launch_window_embeddings(idx->ix, j_begin, count, out, stream));
+  return ROPE_OK;
+}
+
+extern "C" rope_status rope_encode_reads(const rope_params* p, const uint8_t* seqs, const int64_t* offsets,
+                                         int64_t n_reads, float* emb_f32, uint16_t* emb_bf16, float* norms,
+                                         cudaStream_t stream) {
+  rope_status st = check_params(p);
+  if (st != ROPE_OK) return st;
+  if (n_reads < 0) return fail(ROPE_ERR_INVALID_ARG, "n_reads < 0");
+  if (n_reads == 0) return ROPE_OK;
+  if (!seqs || !offsets || !norms) return fail(ROPE_ERR_INVALID_ARG, "NULL pointer");
+  DeviceCtx* c;
+  if ((st = get_ctx(&c)) != ROPE_OK) return st;
+  EncTables tb;
+  if ((st = get_enc_tables(*p, &tb)) != ROPE_OK) return st;
+  ROPE_CUDA(launch_encode_reads(tb, seqs, offsets, n_reads, emb_f32, emb_bf16, norms, c->status, stream));
+  return ROPE_OK;
+}
+
+// ---------------------------------------------------------------- scan
+
+namespace {
+
+struct ScanPlan {
+  ScanArgs a{};
+  bool tc = false;
+  size_t cand_bytes = 0;
+};
+
+rope_status plan_scan(const rope_index* idx, int32_t precision, int64_t n_reads, int64_t jb, int64_t je,
+                      int32_t n_ranges_req, int num_sms, ScanPlan* out) {
+  const DevIndex& ix = idx->ix;
+  ScanPlan pl;
+  pl.tc = precision == ROPE_PREC_BF16;
+  int64_t sup;
+  int group;
+  if (pl.tc) {
+    if (!scan_tc_supported(ix.D))
+      return fail(ROPE_ERR_UNSUPPORTED, "tensor-core scan built for complex dimension 32 or 64, not %d", ix.D);
+    if (ix.score_mode != 0) return fail(ROPE_ERR_UNSUPPORTED, "tensor-core scan takes score_mode 0 only");
+    if (ix.stride > 16) return fail(ROPE_ERR_UNSUPPORTED, "tensor-core scan takes stride <= 16");
+    sup = scan_tc_super_tile(ix.D);
+    group = scan_tc_group(ix.D);
+  } else if (precision == ROPE_PREC_FP32) {
+    if (!scan_fp32_supported(ix.D))
+      return fail(ROPE_ERR_UNSUPPORTED, "FP32 scan built for complex dimension <= 64, not %d", ix.D);
+    sup = scan_fp32_super_tile(ix.D);
+    group = scan_fp32_group(ix.D);
+  } else {
+    return fail(ROPE_ERR_INVALID_ARG, "precision %d", precision);
+  }
+  ScanArgs& a = pl.a;
+  a.n_reads = n_reads;
+  a.jb = jb;
+  a.je = je;
+  a.st0 = (jb / sup) * sup;
+  const int64_t n_sup = (je - a.st0 + sup - 1) / sup;
+  a.n_groups = (int32_t)((n_reads + group - 1) / group);
+  int64_t nr = n_ranges_req > 0 ? n_ranges_req : (16LL * num_sms + a.n_groups - 1) / a.n_groups;
+  if (nr < 1) nr = 1;
+  if (nr > n_sup) nr = n_sup;
+  if (nr > 4096) nr = 4096;
+  const int64_t sup_per_range = (n_sup + nr - 1) / nr;
+  a.range_len = sup_per_range * sup;
+  a.n_ranges = (int32_t)((n_sup + sup_per_range - 1) / sup_per_range);
+  *out = pl;
+  return ROPE_OK;
+}
+
+rope_status check_opts(const rope_score_opts* o, rope_score_opts* v) {
+  if (!o) return fail(ROPE_ERR_INVALID_ARG, "opts is NULL");
+  *v = *o;
+  if (v->k < 1 || v->k > 32) return fail(ROPE_ERR_INVALID_ARG, "k=%d outside [1,32]", v->k);
+  if (v->sep < 0) return fail(ROPE_ERR_INVALID_ARG, "sep < 0");
+  if (v->cand_depth == 0) v->cand_depth = 16;
+  if (v->cand_depth < v->k) v->cand_depth = v->k;
+  if (v->cand_depth > 32) return fail(ROPE_ERR_INVALID_ARG, "cand_depth > 32");
+  if (v->rescore_depth == 0) v->rescore_depth = v->k * 2 < 32 ? v->k * 2 : 32;
+  if (v->rescore_depth < v->k) v->rescore_depth = v->k;
+  if (v->rescore_depth > 32) return fail(ROPE_ERR_INVALID_ARG, "rescore_depth > 32");
+  if (v->rescore != 0 && v->rescore != 1) return fail(ROPE_ERR_INVALID_ARG, "rescore must be 0 or 1");
+  return ROPE_OK;
+}
+
+}  // namespace
+
+static rope_status score_topk_impl(const rope_index* idx, const float* emb_f32, const uint16_t* emb_bf16,
+                                   const float* norms, int64_t n_reads, const rope_score_opts* opts,
+                                   int64_t* out_win, float* out_score, cudaStream_t stream, int prof_slot) {
+  if (!idx) return fail(ROPE_ERR_INVALID_ARG, "index is NULL");
+  rope_score_opts o;
+  rope_status st = check_opts(opts, &o);
+  if (st != ROPE_OK) return st;
+  if (n_reads < 0) return fail(ROPE_ERR_INVALID_ARG, "n_reads < 0");
+  if (n_reads == 0) return ROPE_OK;
+  if (!emb_f32 || !norms || !out_win || !out_score) return fail(ROPE_ERR_INVALID_ARG, "NULL pointer");
+  if (o.precision == ROPE_PREC_BF16 && !emb_bf16) return fail(ROPE_ERR_INVALID_ARG, "BF16 scan needs emb_bf16");
+  DeviceCtx* c;
+  if ((st = get_ctx(&c)) != ROPE_OK) return st;
+  const DevIndex& ix = idx->ix;
+  const int64_t jb = o.j_begin > 0 ? o.j_begin : 0;
+  const int64_t je = o.j_end > 0 ? (o.j_end < ix.W ? o.j_end : ix.W) : ix.W;
+  if (jb > ix.W) return fail(ROPE_ERR_INVALID_ARG, "j_begin beyond the last window");
+
+  ScanPlan pl;
+  Candidate* cand = nullptr;
+  int32_t n_ranges = 1;
+  if (je > jb) {
+    if ((st = plan_scan(idx, o.precision, n_reads, jb, je, o.n_ranges, c->num_sms, &pl)) != ROPE_OK) return st;
+    n_ranges = pl.a.n_ranges;
+  }
+  const size_t cand_bytes = (size_t)n_reads * n_ranges * o.cand_depth * sizeof(Candidate);
+  if ((st = pool_alloc(c, (void**)&cand, cand_bytes, stream)) != ROPE_OK) return st;
+  if (je > jb) {
+    pl.a.emb_f32 = emb_f32;
+    pl.a.emb_bf16 = emb_bf16;
+    pl.a.norms = norms;
+    pl.a.cand_depth = o.cand_depth;
+    pl.a.sep = o.sep;
+    pl.a.cand = cand;
+    pl.a.dense = nullptr;
+    pl.a.status = c->status;
+    cudaError_t e = pl.tc ? launch_scan_tc(ix, pl.a, false, c->num_sms, stream)
+                          : launch_scan_fp32(ix, pl.a, false, c->num_sms, stream);
+    if (e != cudaSuccess) {
+      cudaFreeAsync(cand, stream);
+      return fail(ROPE_ERR_CUDA, "scan launch: %s", cudaGetErrorString(e));
+    }
+  } else {
+    ROPE_CUDA(cudaMemsetAsync(cand, 0xFF, cand_bytes, stream));  // every slot empty
+  }
+  prof_mark(prof_slot, 2, stream);
+  MergeArgs m{};
+  m.cand = cand;
+  m.n_reads = n_reads;
+  m.n_ranges = n_ranges;
+  m.cand_depth = o.cand_depth;
+  m.k = o.k;
+  m.sep = o.sep;
+  m.rescore = o.rescore;
+  m.rescore_depth = o.rescore_depth;
+  m.emb_f32 = emb_f32;
+  m.norms = norms;
+  m.out_win = out_win;
+  m.out_score = out_score;
+  m.status = c->status;
+  cudaError_t e = launch_merge(ix, m, stream);
+  prof_mark(prof_slot, 3, stream);
+  cudaFreeAsync(cand, stream);
+  if (e != cudaSuccess) return fail(ROPE_ERR_CUDA, "merge launch: %s", cudaGetErrorString(e));
+  return ROPE_OK;
+}
+
+extern "C" rope_status rope_score_topk(const rope_index* idx, const float* emb_f32, const uint16_t* emb_bf16,
+                                       const float* norms, int64_t n_reads, const rope_score_opts* opts,
+                                       int64_t* out_win, float* out_score, cudaStream_t stream) {
+  const int slot = prof_begin(stream);
+  prof_mark(slot, 1, stream);
+  const rope_status st = score_topk_impl(idx, emb_f32, emb_bf16, norms, n_reads, opts, out_win, out_score, stream,
+                                         slot);
+  if (slot >= 0 && st != ROPE_OK) {
+    prof_mark(slot, 2, stream);
+    prof_mark(slot, 3, stream);
+  }
+  return st;
+}
+
+extern "C" rope_status rope_score_dense(const rope_index* idx, const float* emb_f32, const uint16_t* emb_bf16,
+                                        const float* norms, int64_t n_reads, int32_t precision, int64_t j_begin,
+                                        int64_t count, float* out, cudaStream_t stream) {
+  if (!idx) return fail(ROPE_ERR_INVALID_ARG, "index is NULL");
+  if (n_reads < 0 || count < 0 || j_begin < 0 || j_begin + count > idx->ix.W)
+    return fail(ROPE_ERR_INVALID_ARG, "bad dense range");
+  if (n_reads == 0 || count == 0) return ROPE_OK;
+  if (!emb_f32 || !norms || !out) return fail(ROPE_ERR_INVALID_ARG, "NULL pointer");
+  if (precision == ROPE_PREC_BF16 && !emb_bf16) return fail(ROPE_ERR_INVALID_ARG, "BF16 scan needs emb_bf16");
+  DeviceCtx* c;
+  rope_status st = get_ctx(&c);
+  if (st != ROPE_OK) return st;
+  ScanPlan pl;
+  if ((st = plan_scan(idx, precision, n_reads, j_begin, j_begin + count, 0, c->num_sms, &pl)) != ROPE_OK) return st;
+  pl.a.emb_f32 = emb_f32;
+  pl.a.emb_bf16 = emb_bf16;
+  pl.a.norms = norms;
+  pl.a.cand_depth = 1;
+  pl.a.sep = 0;
+  pl.a.cand = nullptr;
+  pl.a.dense = out;
+  pl.a.status = c->status;
+  cudaError_t e = pl.tc ? launch_scan_tc(idx->ix, pl.a, true, c->num_sms, stream)
+                        : launch_scan_fp32(idx->ix, pl.a, true, c->num_sms, stream);
+  if (e != cudaSuccess) return fail(ROPE_ERR_CUDA, "dense scan launch: %s", cudaGetErrorString(e));
+  return ROPE_OK;
+}
+
+extern "C" rope_status rope_map(const rope_index* idx, const uint8_t* seqs, const int64_t* offsets, int64_t n_reads,
+                                const rope_score_opts* opts, int64_t* out_win, float* out_score, cudaStream_t stream) {
+  if (!idx) return fail(ROPE_ERR_INVALID_ARG, "index is NULL");
+  rope_score_opts o;
+  rope_status st = check_opts(opts, &o);
+  if (st != ROPE_OK) return st;
+  if (n_reads < 0) return fail(ROPE_ERR_INVALID_ARG, "n_reads < 0");
+  if (n_reads == 0) return ROPE_OK;
+  if (!seqs || !offsets || !out_win || !out_score) return fail(ROPE_ERR_INVALID_ARG, "NULL pointer");
+  DeviceCtx* c;
+  if ((st = get_ctx(&c)) != ROPE_OK) return st;
+  const int D = idx->ix.D, m = idx->ix.m;
+  float* emb = nullptr;
+  uint16_t* embh = nullptr;
+  float* norms = nullptr;
+  if ((st = pool_alloc(c, (void**)&emb, (size_t)n_reads * 2 * D * sizeof(float), stream)) != ROPE_OK) return st;
+  if ((st = pool_alloc(c, (void**)&embh, (size_t)n_reads * 2 * D * sizeof(uint16_t), stream)) != ROPE_OK) {
+    cudaFreeAsync(emb, stream);
+    return st;
+  }
+  if ((st = pool_alloc(c, (void**)&norms, (size_t)n_reads * (1 + m) * sizeof(float), stream)) != ROPE_OK) {
+    cudaFreeAsync(emb, stream);
+    cudaFreeAsync(embh, stream);
+    return st;
+  }
+  const int slot = prof_begin(stream);
+  cudaError_t e = launch_encode_reads(idx->enc, seqs, offsets, n_reads, emb, embh, norms, c->status, stream);
+  prof_mark(slot, 1, stream);
+  if (e != cudaSuccess) st = fail(ROPE_ERR_CUDA, "encode launch: %s", cudaGetErrorString(e));
+  if (st == ROPE_OK) {
+    o.j_begin = 0;
+    o.j_end = 0;
+    st = score_topk_impl(idx, emb, embh, norms, n_reads, &o, out_win, out_score, stream, slot);
+  }
+  if (slot >= 0 && st != ROPE_OK) {
+    prof_mark(slot, 2, stream);
+    prof_mark(slot, 3, stream);
+  }
+  cudaFreeAsync(emb, stream);
+  cudaFreeAsync(embh, stream);
+  cudaFreeAsync(norms, stream);
+  return st;
+}

@@ -1,0 +1,306 @@
+// Shared device-side definitions of the RotorMap GB300 library.
+//
+// The device view of a reference index (DevIndex), the status word that kernels
+// report errors through, bounded waits, the s-mer bin lookup on packed words,
+// the window generator (the slide-by-one recurrence of §3.4) and thin inline
+// PTX wrappers for mbarrier, bulk copies and tcgen05.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace rope {
+
+// Bits of the device status word (OR-ed by kernels, read by rope_sync_status).
+enum : int {
+  kStatusBadBase = 1,     // letter outside {A,C,G,T,a,c,g,t}
+  kStatusShortRead = 2,   // read shorter than N
+  kStatusTimeout = 4,     // a bounded wait ran out
+  kStatusBadArg = 8,      // a kernel saw an out-of-range argument
+};
+
+constexpr int kAnchorPeriod = 64;  // windows between exact anchors
+constexpr int kMaxScanDim = 128;   // largest complex dimension the scans take
+constexpr int kPackPadWords = 64;  // zero words after the packed reference
+
+// Device view of a reference index. All pointers are device pointers.
+struct DevIndex {
+  const uint32_t* packed;  // 2-bit letters, + kPackPadWords zero words
+  int64_t L;               // letters
+  int64_t W;               // windows
+  int32_t N, s, m, t, nb, D, stride, A;
+  int32_t variant, score_mode;
+  const float* inv_norm;    // [W] 1/sqrt(|c_j|^2), 0 for a zero vector
+  const float* band_norm;   // [W*m] |c_j,k|^2 (score_mode 1), else null
+  const float2* anchors;    // [ceil(W/A) * D] c(a*A) in FP32
+  const uint16_t* map_lsb;  // [4^s] bin of the little-endian 2s-bit letter field
+  const float2* phase;      // [m * (N-s+1)] exp(2 pi i f_k loc / N)
+  const float2* rot;        // [m] exp(-2 pi i f_k stride / N)
+  const float2* eout;       // [m * stride] exp(2 pi i f_k j / N), j < stride
+  const float2* ein;        // [m * stride] exp(2 pi i f_k (N-s+1+j) / N), j < stride
+};
+
+// ---------------------------------------------------------------- status
+
+__device__ __forceinline__ void set_status(int* status, int bits) {
+  if (status) atomicOr(status, bits);
+}
+
+__device__ __forceinline__ uint64_t globaltimer_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+constexpr uint64_t kWaitLimitNs = 2000000000ull;  // 2 s per wait
+
+// ---------------------------------------------------------------- letters
+
+// A,C,G,T (either case) -> 0..3, else 4
+__device__ __forceinline__ uint32_t letter_code(uint32_t c) {
+  c |= 0x20u;  // lower case
+  return c == 'a' ? 0u : c == 'c' ? 1u : c == 'g' ? 2u : c == 't' ? 3u : 4u;
+}
+
+// bin of the s-mer at position p, read from 2-bit packed words
+__device__ __forceinline__ uint32_t bin_at(const uint32_t* __restrict__ packed, int64_t p, int s,
+                                           const uint16_t* __restrict__ map_lsb) {
+  const int64_t wi = p >> 4;
+  const int sh = (int)(p & 15) * 2;
+  const uint64_t v = ((uint64_t)__ldg(packed + wi + 1) << 32) | __ldg(packed + wi);
+  const uint32_t field = (uint32_t)(v >> sh) & ((1u << (2 * s)) - 1u);
+  return __ldg(map_lsb + field);
+}
+
+// ---------------------------------------------------------------- generator
+
+// One chain of the window generator: LPC = D/4 lanes hold the D complex entries
+// of c(j), four consecutive entries per lane (entries 4l..4l+3 of lane l, all
+// in one band since 4^t is a multiple of 4). A step moves c(j) to c(j+1) by
+// the slide relations of §3.4, for stride S:
+//   c_b <- c_b - sum_{i<S} [bin(w+i) = b] e^{2 pi i f i/N}
+//   c_b <- c_b + sum_{i<S} [bin(w+N-s+1+i) = b] e^{2 pi i f (N-s+1+i)/N}
+//   c   <- c * e^{-2 pi i f S/N}
+// (for S = 1 these are exactly the paper's relations: every entry rotates by
+// w^{-f}, the leaving s-mer loses w^{-f}, the entering one gains w^{f(N-s)}).
+template <int D>
+struct Chain {
+  static constexpr int LPC = D / 4;
+  float cr[4], ci[4];
+  int band;   // band k-1 of this lane's entries
+  int b0;     // bin of entry 0 of this lane
+  float rc, rs;  // rotation e^{-2 pi i f S / N}
+  float ec, es;  // stride-1 entering phase e^{2 pi i f (N-s+1) / N}
+
+  __device__ __forceinline__ void setup(const DevIndex& ix, int lane_in_chain) {
+    const int g0 = 4 * lane_in_chain;
+    band = g0 / ix.nb;
+    b0 = g0 - band * ix.nb;
+    const float2 r = ix.rot[band];
+    rc = r.x;
+    rs = r.y;
+    const float2 e = ix.ein[band * ix.stride];
+    ec = e.x;
+    es = e.y;
+  }
+
+  __device__ __forceinline__ void load(const float2* __restrict__ anchor, int lane_in_chain) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const float2 v = anchor[4 * lane_in_chain + i];
+      cr[i] = v.x;
+      ci[i] = v.y;
+    }
+  }
+
+  __device__ __forceinline__ void rotate() {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const float xr = cr[i], xi = ci[i];
+      cr[i] = fmaf(xr, rc, -xi * rs);
+      ci[i] = fmaf(xr, rs, xi * rc);
+    }
+  }
+
+  // stride 1: bout = bin leaving at the start, bin_in = bin entering at the end
+  __device__ __forceinline__ void step1(uint32_t bout, uint32_t bin_in) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      if ((uint32_t)(b0 + i) == bout) cr[i] -= 1.0f;
+      if ((uint32_t)(b0 + i) == bin_in) {
+        cr[i] += ec;
+        ci[i] += es;
+      }
+    }
+    rotate();
+  }
+
+  // general stride: one leaving (sub_at) or entering (add_at) location
+  __device__ __forceinline__ void sub_at(uint32_t b, float2 v) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+      if ((uint32_t)(b0 + i) == b) {
+        cr[i] -= v.x;
+        ci[i] -= v.y;
+      }
+  }
+  __device__ __forceinline__ void add_at(uint32_t b, float2 v) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+      if ((uint32_t)(b0 + i) == b) {
+        cr[i] += v.x;
+        ci[i] += v.y;
+      }
+  }
+};
+
+// ---------------------------------------------------------------- PTX: mbarrier
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.shared::cta.b64 st, [%0];\n}" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n}" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait on a phase parity. Returns false (and sets the timeout bit and
+// the block's abort flag) if the phase did not complete within kWaitLimitNs,
+// or if another role of the block has already aborted.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag, int* status) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const uint64_t t0 = globaltimer_ns();
+  for (;;) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if (*abort_flag) return false;
+    if (globaltimer_ns() - t0 > kWaitLimitNs) {
+      *abort_flag = 1;
+      set_status(status, kStatusTimeout);
+      return false;
+    }
+  }
+}
+
+// Warp-uniform bounded wait: every lane waits, then the warp agrees (and
+// reconverges) before any .sync.aligned instruction that follows.
+__device__ __forceinline__ bool mbar_wait_warp(uint64_t* bar, uint32_t parity, volatile int* abort_flag,
+                                               int* status) {
+  const bool ok = mbar_wait(bar, parity, abort_flag, status);
+  return __all_sync(0xffffffffu, ok);
+}
+
+// ---------------------------------------------------------------- PTX: bulk copy
+
+// 1-D bulk copy global -> shared, completion signalled on `bar` (tx bytes).
+// Both addresses 16-byte aligned, bytes a multiple of 16.
+__device__ __forceinline__ void bulk_g2s(void* dst_smem, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cta.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(smem_u32(dst_smem)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+__device__ __forceinline__ void fence_barrier_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+
+// ---------------------------------------------------------------- PTX: tcgen05
+
+__device__ __forceinline__ void tmem_alloc(uint32_t* dst_smem, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(dst_smem)),
+               "r"(ncols)
+               : "memory");
+}
+__device__ __forceinline__ void tmem_relinquish() {
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// D[tmem] (+)= A[tmem] * B[smem desc], kind::f16 (BF16 inputs, FP32 accumulate)
+__device__ __forceinline__ void tc_mma_ts(uint32_t d_tmem, uint32_t a_tmem, uint64_t b_desc, uint32_t idesc,
+                                          uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n}" ::"r"(d_tmem),
+      "r"(a_tmem), "l"(b_desc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+// arrive on `bar` once all prior tcgen05 async ops of this thread complete
+__device__ __forceinline__ void tc_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ void tc_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+__device__ __forceinline__ void tc_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+
+// 32 lanes x 16 consecutive 32-bit columns -> 16 registers per thread
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+}
+
+// 32 lanes x 8 consecutive 32-bit columns from 8 registers per thread
+__device__ __forceinline__ void tmem_st8(uint32_t taddr, const uint32_t (&r)[8]) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"r"(taddr), "r"(r[0]), "r"(r[1]),
+      "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7])
+      : "memory");
+}
+
+// Shared-memory matrix descriptor (tcgen05): K-major, 128-byte swizzle, rows of
+// 128 bytes in 8-row (1024-byte) groups. Start address and group stride in
+// 16-byte units; bits 46-47 hold the descriptor version (1), bits 61-63 the
+// layout (2 = 128-byte swizzle).
+__device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
+  d |= (uint64_t)1 << 16;                 // leading byte offset (unused for swizzled K-major)
+  d |= (uint64_t)(1024 >> 4) << 32;       // stride byte offset: next 8-row group
+  d |= (uint64_t)1 << 46;                 // version
+  d |= (uint64_t)2 << 61;                 // 128-byte swizzle
+  return d;
+}
+
+// Instruction descriptor, kind::f16: BF16 A and B (K-major), FP32 D, shape M x N.
+__host__ __device__ constexpr uint32_t idesc_bf16_f32(int M, int N) {
+  return (1u << 4)                       // D format FP32
+         | (1u << 7)                     // A format BF16
+         | (1u << 10)                    // B format BF16
+         | ((uint32_t)(N >> 3) << 17)    // N / 8
+         | ((uint32_t)(M >> 4) << 24);   // M / 16
+}
+
+// byte offset of (row r, byte o of the 128-byte row) in a 128-byte-swizzled
+// K-major tile: 16-byte chunk index XOR (row mod 8), 8-row groups 1024 B apart
+__host__ __device__ __forceinline__ uint32_t sw128_offset(uint32_t r, uint32_t o) {
+  return (r >> 3) * 1024u + (r & 7u) * 128u + ((((o >> 4) ^ (r & 7u)) & 7u) << 4) + (o & 15u);
+}
+
+}  // namespace rope

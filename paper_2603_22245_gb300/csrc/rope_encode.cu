@@ -1,0 +1,360 @@
+// Encoding kernels: 2-bit packing, s-mer bins, read-head encodings (direct
+// summation), the FP64 reference pre-pass (anchors and exact window norms) and
+// the window-embedding inspection kernel.
+#include <cuda_bf16.h>
+
+#include "rope_internal.h"
+
+namespace rope {
+
+// ---------------------------------------------------------------- a1: packing
+
+__device__ __forceinline__ uint32_t pack4(uint32_t x, int& bad) {
+  uint32_t w = 0;
+#pragma unroll
+  for (int b = 0; b < 4; ++b) {
+    const uint32_t c = letter_code((x >> (8 * b)) & 0xFFu);
+    bad |= (c > 3);
+    w |= (c & 3u) << (2 * b);
+  }
+  return w;
+}
+
+// One output word (16 letters) per thread; 16-byte vector loads when aligned.
+// HBM-bound: 1 byte in and 1/4 byte out per letter.
+__global__ void pack_kernel(const uint8_t* __restrict__ seq, int64_t len, uint32_t* __restrict__ out,
+                            int64_t n_words, int* status) {
+  const bool aligned = (((uintptr_t)seq) & 15u) == 0;
+  int bad = 0;
+  for (int64_t w = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; w < n_words;
+       w += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t base = w * 16;
+    uint32_t word = 0;
+    if (aligned && base + 16 <= len) {
+      const uint4 v = __ldg(reinterpret_cast<const uint4*>(seq + base));
+      word = pack4(v.x, bad) | (pack4(v.y, bad) << 8) | (pack4(v.z, bad) << 16) | (pack4(v.w, bad) << 24);
+    } else {
+      for (int i = 0; i < 16 && base + i < len; ++i) {
+        const uint32_t c = letter_code(seq[base + i]);
+        bad |= (c > 3);
+        word |= (c & 3u) << (2 * i);
+      }
+    }
+    out[w] = word;
+  }
+  if (bad) set_status(status, kStatusBadBase);
+}
+
+cudaError_t launch_pack(const uint8_t* seq, int64_t len, uint32_t* out, int* status, cudaStream_t st) {
+  const int64_t n_words = (len + 15) / 16;
+  if (n_words == 0) return cudaSuccess;
+  const int threads = 256;
+  int64_t blocks = (n_words + threads - 1) / threads;
+  if (blocks > 152 * 32) blocks = 152 * 32;
+  pack_kernel<<<(unsigned)blocks, threads, 0, st>>>(seq, len, out, n_words, status);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- a2: bins
+
+__global__ void mer_bins_kernel(const uint32_t* __restrict__ packed, int64_t n_pos, int64_t n_words, int s,
+                                const uint16_t* __restrict__ map_lsb, uint16_t* __restrict__ out) {
+  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n_pos; p += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t wi = p >> 4;
+    const uint32_t lo = packed[wi];
+    const uint32_t hi = wi + 1 < n_words ? packed[wi + 1] : 0u;
+    const uint64_t v = ((uint64_t)hi << 32) | lo;
+    const uint32_t field = (uint32_t)(v >> ((p & 15) * 2)) & ((1u << (2 * s)) - 1u);
+    out[p] = map_lsb[field];
+  }
+}
+
+cudaError_t launch_mer_bins(const uint32_t* packed, int64_t len, int64_t n_words, int s, const uint16_t* map_lsb,
+                            uint16_t* out, cudaStream_t st) {
+  const int64_t n_pos = len - s + 1;
+  if (n_pos <= 0) return cudaSuccess;
+  int64_t blocks = (n_pos + 255) / 256;
+  if (blocks > 152 * 32) blocks = 152 * 32;
+  mer_bins_kernel<<<(unsigned)blocks, 256, 0, st>>>(packed, n_pos, n_words, s, map_lsb, out);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- a3: read heads
+
+// One warp per read. Locations are taken in order; for each location the
+// lanes k < m add exp(2 pi i f_k loc / N) to entry (k, bin) of a per-warp
+// shared accumulator, so every entry is summed in location order (the direct
+// sum of §2.1-§2.3 in FP32, deterministic).
+__global__ void encode_reads_kernel(EncTables tb, const uint8_t* __restrict__ seqs,
+                                    const int64_t* __restrict__ offsets, int64_t n, float* __restrict__ emb_f32,
+                                    __nv_bfloat16* __restrict__ emb_bf16, float* __restrict__ norms, int* status) {
+  extern __shared__ float2 enc_acc[];
+  const int lane = threadIdx.x & 31;
+  const int warp = threadIdx.x >> 5;
+  const int wpb = blockDim.x >> 5;
+  float2* acc = enc_acc + (size_t)warp * tb.D;
+  const int n_loc = tb.N - tb.s + 1;
+  for (int64_t r = (int64_t)blockIdx.x * wpb + warp; r < n; r += (int64_t)gridDim.x * wpb) {
+    const int64_t start = offsets[r];
+    const int64_t len = offsets[r + 1] - start;
+    const uint8_t* seq = seqs + start;
+    for (int g = lane; g < tb.D; g += 32) acc[g] = make_float2(0.f, 0.f);
+    bool ok = len >= tb.N;
+    if (!ok) {
+      if (lane == 0) set_status(status, kStatusShortRead);
+    } else {
+      int bad = 0;
+      for (int i = lane; i < tb.N; i += 32) bad |= letter_code(seq[i]) > 3;
+      if (__any_sync(0xffffffffu, bad)) {
+        ok = false;
+        if (lane == 0) set_status(status, kStatusBadBase);
+      }
+    }
+    __syncwarp();
+    if (ok) {
+      for (int loc0 = 0; loc0 < n_loc; loc0 += 32) {
+        const int loc = loc0 + lane;
+        uint32_t b = 0;
+        if (loc < n_loc) {
+          uint32_t code = 0;
+          for (int i = 0; i < tb.s; ++i) code = code * 4u + (letter_code(seq[loc + i]) & 3u);
+          b = tb.map[code];
+        }
+        const int cnt = min(32, n_loc - loc0);
+        for (int jj = 0; jj < cnt; ++jj) {
+          const uint32_t bj = __shfl_sync(0xffffffffu, b, jj);
+          if (lane < tb.m) {
+            const float2 ph = tb.phase[lane * n_loc + loc0 + jj];
+            float2& a = acc[lane * tb.nb + bj];
+            a.x += ph.x;
+            a.y += ph.y;
+          }
+          __syncwarp();
+        }
+      }
+    }
+    __syncwarp();
+    // per-band squared norms, then the total
+    float total = 0.f;
+    for (int k = 0; k < tb.m; ++k) {
+      float part = 0.f;
+      for (int b = lane; b < tb.nb; b += 32) {
+        const float2 a = acc[k * tb.nb + b];
+        part = fmaf(a.x, a.x, fmaf(a.y, a.y, part));
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+      if (lane == 0) norms[r * (1 + tb.m) + 1 + k] = part;
+      total += part;
+    }
+    if (lane == 0) norms[r * (1 + tb.m)] = total;
+    const float inv = total > 0.f ? rsqrtf(total) : 0.f;
+    for (int g = lane; g < tb.D; g += 32) {
+      const float2 a = acc[g];
+      if (emb_f32) {
+        emb_f32[r * 2 * tb.D + g] = a.x;
+        emb_f32[r * 2 * tb.D + tb.D + g] = a.y;
+      }
+      if (emb_bf16) {
+        emb_bf16[r * 2 * tb.D + g] = __float2bfloat16_rn(a.x * inv);
+        emb_bf16[r * 2 * tb.D + tb.D + g] = __float2bfloat16_rn(a.y * inv);
+      }
+    }
+    __syncwarp();
+  }
+}
+
+cudaError_t launch_encode_reads(const EncTables& tb, const uint8_t* seqs, const int64_t* offsets, int64_t n,
+                                float* emb_f32, uint16_t* emb_bf16, float* norms, int* status, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  int wpb = (int)(48 * 1024 / (tb.D * sizeof(float2)));
+  if (wpb > 8) wpb = 8;
+  if (wpb < 1) wpb = 1;
+  const size_t smem = (size_t)wpb * tb.D * sizeof(float2);
+  int64_t blocks = (n + wpb - 1) / wpb;
+  if (blocks > 152 * 64) blocks = 152 * 64;
+  encode_reads_kernel<<<(unsigned)blocks, wpb * 32, smem, st>>>(tb, seqs, offsets, n, emb_f32,
+                                                                  reinterpret_cast<__nv_bfloat16*>(emb_bf16), norms,
+                                                                  status);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- reference pre-pass
+
+// One warp per anchor chunk of A windows, in FP64. The chunk's first window is
+// summed directly (§2.1-§2.3); it is stored in FP32 as the anchor that seeds
+// the on-chip FP32 recurrence. The chunk is then walked with the slide
+// relations of §3.4 in FP64 and every window's squared norm (and per-band
+// norms for score_mode 1) is reduced across the warp, so the stored
+// 1/sqrt(C_j) does not inherit the FP32 recurrence's drift.
+__global__ void prepass_kernel(DevIndex ix, PrepassTables pt, float2* __restrict__ anchors,
+                               float* __restrict__ inv_norm, float* __restrict__ band_norm) {
+  extern __shared__ double2 pre_acc[];
+  const int lane = threadIdx.x & 31;
+  const int warp = threadIdx.x >> 5;
+  const int wpb = blockDim.x >> 5;
+  double2* acc = pre_acc + (size_t)warp * ix.D;
+  const int64_t n_chunks = (ix.W + ix.A - 1) / ix.A;
+  const int n_loc = ix.N - ix.s + 1;
+  const int S = ix.stride;
+  for (int64_t a = (int64_t)blockIdx.x * wpb + warp; a < n_chunks; a += (int64_t)gridDim.x * wpb) {
+    const int64_t j0 = a * ix.A;
+    const int64_t w0 = j0 * S;
+    for (int g = lane; g < ix.D; g += 32) acc[g] = make_double2(0.0, 0.0);
+    __syncwarp();
+    for (int loc0 = 0; loc0 < n_loc; loc0 += 32) {
+      const int loc = loc0 + lane;
+      const uint32_t b = loc < n_loc ? bin_at(ix.packed, w0 + loc, ix.s, ix.map_lsb) : 0u;
+      const int cnt = min(32, n_loc - loc0);
+      for (int jj = 0; jj < cnt; ++jj) {
+        const uint32_t bj = __shfl_sync(0xffffffffu, b, jj);
+        if (lane < ix.m) {
+          const double2 ph = pt.phase[lane * n_loc + loc0 + jj];
+          double2& v = acc[lane * ix.nb + bj];
+          v.x += ph.x;
+          v.y += ph.y;
+        }
+        __syncwarp();
+      }
+    }
+    // registers: entries g = lane + 32*i
+    double cr[4], ci[4];
+    int kb[4], bb[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int g = lane + 32 * i;
+      const bool v = g < ix.D;
+      cr[i] = v ? acc[g].x : 0.0;
+      ci[i] = v ? acc[g].y : 0.0;
+      kb[i] = v ? g / ix.nb : 0;
+      bb[i] = v ? g % ix.nb : -1;
+      if (v) anchors[a * ix.D + g] = make_float2((float)cr[i], (float)ci[i]);
+    }
+    __syncwarp();
+    const int64_t j_end = min(ix.W, j0 + ix.A);
+    for (int64_t j = j0; j < j_end; ++j) {
+      double part = 0.0;
+#pragma unroll
+      for (int i = 0; i < 4; ++i) part = fma(cr[i], cr[i], fma(ci[i], ci[i], part));
+      double tot = part;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) tot += __shfl_xor_sync(0xffffffffu, tot, o);
+      if (lane == 0) inv_norm[j] = tot > 0.0 ? (float)(1.0 / sqrt(tot)) : 0.f;
+      if (band_norm) {
+        for (int k = 0; k < ix.m; ++k) {
+          double pk = 0.0;
+#pragma unroll
+          for (int i = 0; i < 4; ++i)
+            if (bb[i] >= 0 && kb[i] == k) pk = fma(cr[i], cr[i], fma(ci[i], ci[i], pk));
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) pk += __shfl_xor_sync(0xffffffffu, pk, o);
+          if (lane == 0) band_norm[j * ix.m + k] = (float)pk;
+        }
+      }
+      if (j + 1 < j_end) {
+        const int64_t w = j * S;
+        for (int u = 0; u < S; ++u) {
+          const uint32_t bo = bin_at(ix.packed, w + u, ix.s, ix.map_lsb);
+          const uint32_t bi = bin_at(ix.packed, w + ix.N - ix.s + 1 + u, ix.s, ix.map_lsb);
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            if (bb[i] == (int)bo) {
+              const double2 e = pt.eout[kb[i] * S + u];
+              cr[i] -= e.x;
+              ci[i] -= e.y;
+            }
+            if (bb[i] == (int)bi) {
+              const double2 e = pt.ein[kb[i] * S + u];
+              cr[i] += e.x;
+              ci[i] += e.y;
+            }
+          }
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const double2 r = pt.rot[kb[i]];
+          const double xr = cr[i], xi = ci[i];
+          cr[i] = xr * r.x - xi * r.y;
+          ci[i] = xr * r.y + xi * r.x;
+        }
+      }
+    }
+  }
+}
+
+cudaError_t launch_prepass(const DevIndex& ix, const PrepassTables& pt, float2* anchors, float* inv_norm,
+                           float* band_norm, int* status, cudaStream_t st) {
+  (void)status;
+  const int64_t n_chunks = (ix.W + ix.A - 1) / ix.A;
+  const int wpb = 4;
+  int64_t blocks = (n_chunks + wpb - 1) / wpb;
+  if (blocks > 152 * 64) blocks = 152 * 64;
+  const size_t smem = (size_t)wpb * ix.D * sizeof(double2);
+  prepass_kernel<<<(unsigned)blocks, wpb * 32, smem, st>>>(ix, pt, anchors, inv_norm, band_norm);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- a4: windows
+
+// Each chain of D/4 lanes starts at one anchor and runs the FP32 recurrence
+// through its chunk of A windows, storing the unnormalised c(j) of the
+// requested windows. This is the generator the scans run, exposed for checks.
+template <int D>
+__global__ void window_embeddings_kernel(DevIndex ix, int64_t j_begin, int64_t count, float* __restrict__ out) {
+  constexpr int LPC = Chain<D>::LPC;
+  constexpr int CPW = 32 / LPC;
+  const int lane = threadIdx.x & 31;
+  const int lic = lane % LPC;
+  const int64_t chain = ((int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * CPW + lane / LPC;
+  const int64_t a0 = j_begin / ix.A;
+  const int64_t a = a0 + chain;
+  const int64_t j_end = min(ix.W, j_begin + count);
+  if (a * ix.A >= j_end) return;
+  Chain<D> ch;
+  ch.setup(ix, lic);
+  ch.load(ix.anchors + a * ix.D, lic);
+  const int S = ix.stride;
+  const int64_t jlast = min(j_end, (a + 1) * ix.A);
+  for (int64_t j = a * ix.A; j < jlast; ++j) {
+    if (j >= j_begin) {
+      float* o = out + (j - j_begin) * 2 * D;
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        o[4 * lic + i] = ch.cr[i];
+        o[D + 4 * lic + i] = ch.ci[i];
+      }
+    }
+    const int64_t w = j * S;
+    if (S == 1) {
+      ch.step1(bin_at(ix.packed, w, ix.s, ix.map_lsb), bin_at(ix.packed, w + ix.N - ix.s + 1, ix.s, ix.map_lsb));
+    } else {
+      for (int u = 0; u < S; ++u) {
+        ch.sub_at(bin_at(ix.packed, w + u, ix.s, ix.map_lsb), ix.eout[ch.band * S + u]);
+        ch.add_at(bin_at(ix.packed, w + ix.N - ix.s + 1 + u, ix.s, ix.map_lsb), ix.ein[ch.band * S + u]);
+      }
+      ch.rotate();
+    }
+  }
+}
+
+cudaError_t launch_window_embeddings(const DevIndex& ix, int64_t j_begin, int64_t count, float* out,
+                                     cudaStream_t st) {
+  const int64_t j_end = min(ix.W, j_begin + count);
+  if (j_end <= j_begin) return cudaSuccess;
+  const int64_t n_chains = (j_end - 1) / ix.A - j_begin / ix.A + 1;
+  const int LPC = ix.D / 4;
+  const int cpb = 4 * (32 / LPC);  // 4 warps per block
+  const unsigned blocks = (unsigned)((n_chains + cpb - 1) / cpb);
+  switch (ix.D) {
+    case 4: window_embeddings_kernel<4><<<blocks, 128, 0, st>>>(ix, j_begin, count, out); break;
+    case 8: window_embeddings_kernel<8><<<blocks, 128, 0, st>>>(ix, j_begin, count, out); break;
+    case 16: window_embeddings_kernel<16><<<blocks, 128, 0, st>>>(ix, j_begin, count, out); break;
+    case 32: window_embeddings_kernel<32><<<blocks, 128, 0, st>>>(ix, j_begin, count, out); break;
+    case 64: window_embeddings_kernel<64><<<blocks, 128, 0, st>>>(ix, j_begin, count, out); break;
+    case 128: window_embeddings_kernel<128><<<blocks, 128, 0, st>>>(ix, j_begin, count, out); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace rope

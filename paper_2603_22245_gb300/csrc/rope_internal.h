@@ -1,0 +1,85 @@
+// Host-side interface between the C ABI (rope_api.cu) and the kernel
+// launchers of the other translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "rope_common.cuh"
+
+namespace rope {
+
+// Tables a read encoder needs (device pointers).
+struct EncTables {
+  int32_t N, s, m, t, nb, D;
+  const uint16_t* map;   // [4^s] bin of the s-mer code (first letter most significant)
+  const float2* phase;   // [m * (N-s+1)] exp(2 pi i f_k loc / N)
+};
+
+struct Candidate {
+  float score;
+  uint32_t win;  // window number; 0xFFFFFFFF = empty
+};
+
+// Arguments shared by the scan kernels.
+struct ScanArgs {
+  const float* emb_f32;      // [n_reads, 2D] unnormalised (FP32 scan)
+  const uint16_t* emb_bf16;  // [n_reads, 2D] normalised bf16 (tensor-core scan)
+  const float* norms;        // [n_reads, 1+m]
+  int64_t n_reads;
+  int64_t jb, je;            // scanned windows [jb, je)
+  int64_t st0;               // first super-tile start (multiple of the super-tile)
+  int64_t range_len;         // windows per range (multiple of the super-tile)
+  int32_t n_ranges;
+  int32_t n_groups;
+  int32_t cand_depth;        // candidates kept per read per range
+  int32_t sep;
+  Candidate* cand;           // [n_reads, n_ranges, cand_depth]
+  float* dense;              // [n_reads, je-jb] (dense mode)
+  int* status;
+};
+
+struct MergeArgs {
+  const Candidate* cand;
+  int64_t n_reads;
+  int32_t n_ranges, cand_depth, k, sep, rescore, rescore_depth;
+  const float* emb_f32;
+  const float* norms;
+  int64_t* out_win;
+  float* out_score;
+  int* status;
+};
+
+// rope_encode.cu
+cudaError_t launch_pack(const uint8_t* seq, int64_t len, uint32_t* out, int* status, cudaStream_t st);
+cudaError_t launch_mer_bins(const uint32_t* packed, int64_t len, int64_t n_words, int s, const uint16_t* map_lsb,
+                            uint16_t* out, cudaStream_t st);
+cudaError_t launch_encode_reads(const EncTables& tb, const uint8_t* seqs, const int64_t* offsets, int64_t n,
+                                float* emb_f32, uint16_t* emb_bf16, float* norms, int* status, cudaStream_t st);
+struct PrepassTables {
+  const double2* phase;  // [m*(N-s+1)]
+  const double2* rot;    // [m]
+  const double2* eout;   // [m*stride]
+  const double2* ein;    // [m*stride]
+};
+cudaError_t launch_prepass(const DevIndex& ix, const PrepassTables& pt, float2* anchors, float* inv_norm,
+                           float* band_norm, int* status, cudaStream_t st);
+cudaError_t launch_window_embeddings(const DevIndex& ix, int64_t j_begin, int64_t count, float* out,
+                                     cudaStream_t st);
+
+// rope_scan_fp32.cu
+int scan_fp32_supported(int D);
+int64_t scan_fp32_super_tile(int D);
+int scan_fp32_group(int D);
+cudaError_t launch_scan_fp32(const DevIndex& ix, const ScanArgs& a, bool dense, int num_sms, cudaStream_t st);
+
+// rope_scan_tc.cu
+int scan_tc_supported(int D);
+int64_t scan_tc_super_tile(int D);
+int scan_tc_group(int D);
+cudaError_t launch_scan_tc(const DevIndex& ix, const ScanArgs& a, bool dense, int num_sms, cudaStream_t st);
+
+// rope_merge.cu
+cudaError_t launch_merge(const DevIndex& ix, const MergeArgs& a, cudaStream_t st);
+
+}  // namespace rope

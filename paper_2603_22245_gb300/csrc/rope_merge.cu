@@ -1,0 +1,179 @@
+// Merge of the per-range candidate lists, optional FP32 re-scoring by direct
+// summation, and the final per-read top-k (§3.5, generalised from top-1).
+//
+// One warp per read. Candidates are ordered by the 64-bit key
+// (orderable score << 32 | ~window), so the best entry is the key maximum and
+// ties in score go to the lower window. The warp extracts the best
+// `depth` candidates one at a time (with sep > 0, skipping windows whose
+// bucket is already taken); if re-scoring is on, each kept window's
+// encoding is rebuilt by direct summation over its N-s+1 locations (§2.1-§2.3,
+// FP32, location order) and its fidelity recomputed against the read's FP32
+// encoding; the kept entries are then sorted across the warp (bitonic) and the
+// first k written.
+#include "rope_internal.h"
+#include "rope_topk.cuh"
+
+namespace rope {
+
+__device__ __forceinline__ uint32_t ord_float(float f) {
+  const uint32_t b = __float_as_uint(f);
+  return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+}
+__device__ __forceinline__ float unord_float(uint32_t u) {
+  return __uint_as_float((u & 0x80000000u) ? (u ^ 0x80000000u) : ~u);
+}
+__device__ __forceinline__ uint64_t cand_key(float s, uint32_t w) {
+  return ((uint64_t)ord_float(s) << 32) | (uint64_t)(0xFFFFFFFFu - w);
+}
+
+__device__ __forceinline__ uint64_t warp_max_u64(uint64_t v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const uint64_t u = __shfl_xor_sync(0xffffffffu, v, o);
+    v = u > v ? u : v;
+  }
+  return v;
+}
+
+__global__ void merge_kernel(DevIndex ix, MergeArgs a) {
+  extern __shared__ float2 merge_acc[];
+  const int lane = threadIdx.x & 31;
+  const int warp = threadIdx.x >> 5;
+  const int wpb = blockDim.x >> 5;
+  float2* acc = merge_acc + (size_t)warp * ix.D;
+  const int total = a.n_ranges * a.cand_depth;
+  const int depth = a.rescore ? a.rescore_depth : a.k;
+  const int n_loc = ix.N - ix.s + 1;
+  const int D = ix.D;
+
+  for (int64_t r = (int64_t)blockIdx.x * wpb + warp; r < a.n_reads; r += (int64_t)gridDim.x * wpb) {
+    const Candidate* cands = a.cand + (size_t)r * total;
+    uint64_t last = ~0ull;
+    int n_sel = 0;
+    uint64_t my_key = 0;  // entry `lane` of the kept list
+    while (n_sel < depth) {
+      uint64_t best = 0;
+      for (int e = lane; e < total; e += 32) {
+        const Candidate c = cands[e];
+        if (c.win == kEmptyWin) continue;
+        const uint64_t key = cand_key(c.score, c.win);
+        if (key < last && key > best) best = key;
+      }
+      best = warp_max_u64(best);
+      if (best == 0) break;
+      last = best;
+      if (a.sep > 0) {
+        const uint32_t w = 0xFFFFFFFFu - (uint32_t)best;
+        const int64_t bucket = (int64_t)w * ix.stride / a.sep;
+        const uint32_t mine = 0xFFFFFFFFu - (uint32_t)my_key;
+        const bool dup = lane < n_sel && (int64_t)mine * ix.stride / a.sep == bucket;
+        if (__any_sync(0xffffffffu, dup)) continue;
+      }
+      if (lane == n_sel) my_key = best;
+      ++n_sel;
+    }
+
+    if (a.rescore && n_sel > 0) {
+      const float* x = a.emb_f32 + (size_t)r * 2 * D;
+      const float* nr = a.norms + (size_t)r * (1 + ix.m);
+      for (int i = 0; i < n_sel; ++i) {
+        const uint64_t key = __shfl_sync(0xffffffffu, my_key, i);
+        const uint32_t jw = 0xFFFFFFFFu - (uint32_t)key;
+        const int64_t w0 = (int64_t)jw * ix.stride;
+        for (int g = lane; g < D; g += 32) acc[g] = make_float2(0.f, 0.f);
+        __syncwarp();
+        for (int loc0 = 0; loc0 < n_loc; loc0 += 32) {
+          const int loc = loc0 + lane;
+          const uint32_t b = loc < n_loc ? bin_at(ix.packed, w0 + loc, ix.s, ix.map_lsb) : 0u;
+          const int cnt = min(32, n_loc - loc0);
+          for (int jj = 0; jj < cnt; ++jj) {
+            const uint32_t bj = __shfl_sync(0xffffffffu, b, jj);
+            if (lane < ix.m) {
+              const float2 ph = ix.phase[lane * n_loc + loc0 + jj];
+              float2& v = acc[lane * ix.nb + bj];
+              v.x += ph.x;
+              v.y += ph.y;
+            }
+            __syncwarp();
+          }
+        }
+        float fid = 0.f;
+        if (ix.score_mode == 0) {
+          float re = 0.f, im = 0.f, C = 0.f;
+          for (int g = lane; g < D; g += 32) {
+            const float xr = x[g], xi = x[D + g];
+            const float2 c = acc[g];
+            re = fmaf(xr, c.x, fmaf(xi, c.y, re));
+            im = fmaf(xr, c.y, fmaf(-xi, c.x, im));
+            C = fmaf(c.x, c.x, fmaf(c.y, c.y, C));
+          }
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) {
+            re += __shfl_xor_sync(0xffffffffu, re, o);
+            im += __shfl_xor_sync(0xffffffffu, im, o);
+            C += __shfl_xor_sync(0xffffffffu, C, o);
+          }
+          const float X = nr[0];
+          fid = (X > 0.f && C > 0.f) ? fmaf(re, re, im * im) / (X * C) : 0.f;
+        } else {
+          for (int k = 0; k < ix.m; ++k) {
+            float re = 0.f, im = 0.f, C = 0.f;
+            for (int b = lane; b < ix.nb; b += 32) {
+              const int g = k * ix.nb + b;
+              const float xr = x[g], xi = x[D + g];
+              const float2 c = acc[g];
+              re = fmaf(xr, c.x, fmaf(xi, c.y, re));
+              im = fmaf(xr, c.y, fmaf(-xi, c.x, im));
+              C = fmaf(c.x, c.x, fmaf(c.y, c.y, C));
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+              re += __shfl_xor_sync(0xffffffffu, re, o);
+              im += __shfl_xor_sync(0xffffffffu, im, o);
+              C += __shfl_xor_sync(0xffffffffu, C, o);
+            }
+            const float Xk = nr[1 + k];
+            fid += (Xk > 0.f && C > 0.f) ? fmaf(re, re, im * im) / (Xk * C) : 0.f;
+          }
+          fid /= ix.m;
+        }
+        if (lane == i) my_key = cand_key(fid, jw);
+        __syncwarp();
+      }
+    }
+
+    // bitonic sort of the kept keys across the warp, descending
+#pragma unroll
+    for (int k2 = 2; k2 <= 32; k2 <<= 1) {
+#pragma unroll
+      for (int j2 = k2 >> 1; j2 > 0; j2 >>= 1) {
+        const uint64_t other = __shfl_xor_sync(0xffffffffu, my_key, j2);
+        const int p = lane ^ j2;
+        const bool take_max = (((lane & k2) == 0) == (lane < p));
+        my_key = take_max ? (other > my_key ? other : my_key) : (other < my_key ? other : my_key);
+      }
+    }
+    if (lane < a.k) {
+      int64_t ow = -1;
+      float os = -INFINITY;
+      if (lane < n_sel && my_key != 0) {
+        ow = (int64_t)(0xFFFFFFFFu - (uint32_t)my_key) * ix.stride;
+        os = unord_float((uint32_t)(my_key >> 32));
+      }
+      a.out_win[r * a.k + lane] = ow;
+      a.out_score[r * a.k + lane] = os;
+    }
+  }
+}
+
+cudaError_t launch_merge(const DevIndex& ix, const MergeArgs& a, cudaStream_t st) {
+  if (a.n_reads <= 0) return cudaSuccess;
+  const int wpb = 8;
+  int64_t blocks = (a.n_reads + wpb - 1) / wpb;
+  if (blocks > 152 * 32) blocks = 152 * 32;
+  const size_t smem = (size_t)wpb * ix.D * sizeof(float2);
+  merge_kernel<<<(unsigned)blocks, wpb * 32, smem, st>>>(ix, a);
+  return cudaGetLastError();
+}
+
+}  // namespace rope

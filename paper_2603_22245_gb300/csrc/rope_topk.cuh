@@ -1,0 +1,80 @@
+// Per-thread candidate list used by the scan epilogues: cand_depth entries of
+// (score, window number) held in shared memory, entry-major ([e][thread]) so
+// that a warp's accesses fall in distinct banks. The list keeps the best
+// entries by (score descending, window ascending); with sep > 0 it keeps at
+// most one window per bucket floor(start/sep), the best one. The worst entry
+// and its score (thr) are cached so that the scan compares each score with
+// one register and enters this code only on an improvement.
+#pragma once
+
+#include <stdint.h>
+
+namespace rope {
+
+constexpr uint32_t kEmptyWin = 0xFFFFFFFFu;
+
+__device__ __forceinline__ bool cand_better(float s1, uint32_t j1, float s2, uint32_t j2) {
+  return s1 > s2 || (s1 == s2 && j1 < j2);
+}
+
+struct ThreadList {
+  float* s;       // &list_s[thread]
+  uint32_t* w;    // &list_w[thread]
+  int stride;     // threads per entry row
+  int depth;
+  int worst;
+  float thr;
+
+  __device__ __forceinline__ float S(int e) const { return s[e * stride]; }
+  __device__ __forceinline__ uint32_t Wn(int e) const { return w[e * stride]; }
+
+  __device__ __forceinline__ void reset() {
+    for (int e = 0; e < depth; ++e) {
+      s[e * stride] = -INFINITY;
+      w[e * stride] = kEmptyWin;
+    }
+    worst = 0;
+    thr = -INFINITY;
+  }
+
+  __device__ __forceinline__ void rescan() {
+    int wi = 0;
+    float ws = S(0);
+    uint32_t ww = Wn(0);
+    for (int e = 1; e < depth; ++e) {
+      const float se = S(e);
+      const uint32_t we = Wn(e);
+      if (cand_better(ws, ww, se, we)) {
+        wi = e;
+        ws = se;
+        ww = we;
+      }
+    }
+    worst = wi;
+    thr = ws;
+  }
+
+  // window number j starts at j*stride_pos; buckets are floor(start / sep)
+  __device__ __forceinline__ void insert(float sc, uint32_t j, int sep, int stride_pos) {
+    if (sep > 0) {
+      const int64_t bucket = (int64_t)j * stride_pos / sep;
+      for (int e = 0; e < depth; ++e) {
+        const uint32_t we = Wn(e);
+        if (we != kEmptyWin && (int64_t)we * stride_pos / sep == bucket) {
+          if (cand_better(sc, j, S(e), we)) {
+            s[e * stride] = sc;
+            w[e * stride] = j;
+            rescan();
+          }
+          return;
+        }
+      }
+    }
+    if (!cand_better(sc, j, S(worst), Wn(worst))) return;
+    s[worst * stride] = sc;
+    w[worst * stride] = j;
+    rescan();
+  }
+};
+
+}  // namespace rope
