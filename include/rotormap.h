@@ -195,6 +195,18 @@ rope_status rope_score_dense(const rope_index* idx, const float* emb_f32, const 
 rope_status rope_map(const rope_index* idx, const uint8_t* seqs, const int64_t* offsets, int64_t n_reads,
                      const rope_score_opts* opts, int64_t* out_win, float* out_score, cudaStream_t stream);
 
+/* ---- multi-GPU: merge of window-range shards (host only) ---------------
+ * The reference's windows can be split into disjoint ranges scanned on
+ * different GPUs (segments are independent, §2.8). win_host/score_host hold
+ * n_shards x n_reads x k_in results of rope_score_topk (shard-major); the
+ * best k_out per read over all shards are written to out_* (n_reads x k_out)
+ * by (score descending, start ascending), at most one per bucket
+ * floor(start/sep) when sep > 0, missing entries (-1, -inf). Pure host code:
+ * no device, no allocation visible to the caller. */
+rope_status rope_merge_shards_host(const int64_t* win_host, const float* score_host, int32_t n_shards,
+                                   int64_t n_reads, int32_t k_in, int32_t k_out, int32_t sep, int64_t* out_win_host,
+                                   float* out_score_host);
+
 /* ---- stage timing (tracing) ---------------------------------------------
  * rope_profile_enable(max_calls) starts recording: every following
  * rope_score_topk / rope_map call (up to max_calls) records CUDA events on its

@@ -206,6 +206,12 @@ int oracle_embed_matrix_form(const uint8_t* seq, int N, int s, int m, int t, int
 /* ---------------------------------------------------------------------- */
 /* Fidelity (§2.4: fid = |<RoPE(a)|RoPE(b)>|^2 of normalised encodings)     */
 
+/* A vector whose squared norm is at most ZERO_NORM2 is the zero vector: §3.3
+ * states that evenly spaced unit phases sum to zero; in floating point that
+ * sum leaves rounding residue (about 1e-28 in FP64) instead of 0, while any
+ * nonzero encoding has a squared norm of order N. */
+#define ZERO_NORM2 1e-6
+
 /* |<x|y>|^2 / (||x||^2 ||y||^2), <x|y> = sum conj(x) y. A zero vector gives 0. */
 double oracle_fidelity(const double* xr, const double* xi, const double* yr, const double* yi, int D) {
   double ipr = 0, ipi = 0, nx = 0, ny = 0;
@@ -215,7 +221,7 @@ double oracle_fidelity(const double* xr, const double* xi, const double* yr, con
     nx += xr[i] * xr[i] + xi[i] * xi[i];
     ny += yr[i] * yr[i] + yi[i] * yi[i];
   }
-  if (nx == 0.0 || ny == 0.0) return 0.0;
+  if (nx <= ZERO_NORM2 || ny <= ZERO_NORM2) return 0.0;
   return (ipr * ipr + ipi * ipi) / (nx * ny);
 }
 

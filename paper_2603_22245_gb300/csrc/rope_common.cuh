@@ -22,6 +22,11 @@ enum : int {
 constexpr int kAnchorPeriod = 64;  // windows between exact anchors
 constexpr int kMaxScanDim = 128;   // largest complex dimension the scans take
 constexpr int kPackPadWords = 64;  // zero words after the packed reference
+// A vector whose squared norm is at most this is the zero vector (§3.3: evenly
+// spaced unit phases sum to zero exactly; rounding leaves ~1e-28 in FP64 and
+// ~1e-12 in FP32, while a nonzero encoding has a squared norm of order N).
+// Its fidelity with anything is 0.
+constexpr float kZeroNorm2 = 1e-6f;
 
 // Device view of a reference index. All pointers are device pointers.
 struct DevIndex {

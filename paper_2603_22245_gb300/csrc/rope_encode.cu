@@ -148,7 +148,7 @@ __global__ void encode_reads_kernel(EncTables tb, const uint8_t* __restrict__ se
       total += part;
     }
     if (lane == 0) norms[r * (1 + tb.m)] = total;
-    const float inv = total > 0.f ? rsqrtf(total) : 0.f;
+    const float inv = total > kZeroNorm2 ? rsqrtf(total) : 0.f;
     for (int g = lane; g < tb.D; g += 32) {
       const float2 a = acc[g];
       if (emb_f32) {
@@ -239,7 +239,7 @@ __global__ void prepass_kernel(DevIndex ix, PrepassTables pt, float2* __restrict
       double tot = part;
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) tot += __shfl_xor_sync(0xffffffffu, tot, o);
-      if (lane == 0) inv_norm[j] = tot > 0.0 ? (float)(1.0 / sqrt(tot)) : 0.f;
+      if (lane == 0) inv_norm[j] = tot > (double)kZeroNorm2 ? (float)(1.0 / sqrt(tot)) : 0.f;
       if (band_norm) {
         for (int k = 0; k < ix.m; ++k) {
           double pk = 0.0;

@@ -114,7 +114,7 @@ __global__ void merge_kernel(DevIndex ix, MergeArgs a) {
             C += __shfl_xor_sync(0xffffffffu, C, o);
           }
           const float X = nr[0];
-          fid = (X > 0.f && C > 0.f) ? fmaf(re, re, im * im) / (X * C) : 0.f;
+          fid = (X > kZeroNorm2 && C > kZeroNorm2) ? fmaf(re, re, im * im) / (X * C) : 0.f;
         } else {
           for (int k = 0; k < ix.m; ++k) {
             float re = 0.f, im = 0.f, C = 0.f;
@@ -133,7 +133,7 @@ __global__ void merge_kernel(DevIndex ix, MergeArgs a) {
               C += __shfl_xor_sync(0xffffffffu, C, o);
             }
             const float Xk = nr[1 + k];
-            fid += (Xk > 0.f && C > 0.f) ? fmaf(re, re, im * im) / (Xk * C) : 0.f;
+            fid += (Xk > kZeroNorm2 && C > kZeroNorm2) ? fmaf(re, re, im * im) / (Xk * C) : 0.f;
           }
           fid /= ix.m;
         }

@@ -66,14 +66,14 @@ __global__ void __launch_bounds__(kF32Threads) scan_fp32_kernel(DevIndex ix, Sca
       float inv = 0.f;
       if (!kPerBand) {
         const float X = nr[0];
-        inv = (have_read && X > 0.f) ? rsqrtf(X) : 0.f;
+        inv = (have_read && X > kZeroNorm2) ? rsqrtf(X) : 0.f;
       }
 #pragma unroll
       for (int g = 0; g < D; ++g) {
         float sc = inv;
         if (kPerBand) {
           const float Xk = nr[1 + g / ix.nb];
-          sc = (have_read && Xk > 0.f) ? rsqrtf(Xk) : 0.f;
+          sc = (have_read && Xk > kZeroNorm2) ? rsqrtf(Xk) : 0.f;
         }
         xr[g] = e[g] * sc;
         xi[g] = e[D + g] * sc;
@@ -84,7 +84,12 @@ __global__ void __launch_bounds__(kF32Threads) scan_fp32_kernel(DevIndex ix, Sca
     for (int64_t st = st_begin; st < j_hi; st += Sh::SUP) {
       const int64_t a_idx = st / ix.A + chain;
       const bool chain_live = a_idx * ix.A < ix.W;
-      if (chain_live) ch.load(ix.anchors + a_idx * D, lic);
+      if (chain_live) {
+        ch.load(ix.anchors + a_idx * D, lic);
+      } else {
+#pragma unroll
+        for (int i = 0; i < 4; ++i) ch.cr[i] = ch.ci[i] = 0.f;
+      }
       for (int rd = 0; rd < kAnchorPeriod / kF32Steps; ++rd) {
         // ---- generate kF32Steps windows per chain into the tile
 #pragma unroll 1
@@ -99,7 +104,7 @@ __global__ void __launch_bounds__(kF32Threads) scan_fp32_kernel(DevIndex ix, Sca
             vi = make_float4(ch.ci[0] * inv, ch.ci[1] * inv, ch.ci[2] * inv, ch.ci[3] * inv);
           } else {
             const float Ck = live ? ix.band_norm[j * ix.m + ch.band] : 0.f;
-            const float inv = Ck > 0.f ? rsqrtf(Ck) : 0.f;
+            const float inv = Ck > kZeroNorm2 ? rsqrtf(Ck) : 0.f;
             vr = make_float4(ch.cr[0] * inv, ch.cr[1] * inv, ch.cr[2] * inv, ch.cr[3] * inv);
             vi = make_float4(ch.ci[0] * inv, ch.ci[1] * inv, ch.ci[2] * inv, ch.ci[3] * inv);
           }

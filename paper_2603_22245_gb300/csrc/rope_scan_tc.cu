@@ -169,24 +169,26 @@ __global__ void __launch_bounds__(Sh::NTHREADS, 1) scan_tc_kernel(DevIndex ix, S
           const uint32_t s = gs % STAGES;
           if (!mbar_wait_warp(&bar_afull[s], (gs / STAGES) & 1, abort_flag, a.status)) goto epi_done;
           tc_fence_after();
-          uint32_t v[2 * T];
           const uint32_t col = (uint32_t)(Sh::ACC0 + ((int)s * NT + tile) * 2 * T);
+          const int64_t jbase = st + i;  // column n holds window jbase + n*A
+          float mx = -INFINITY;
+          float sc[T];
 #pragma unroll
-          for (int c = 0; c < 2 * T / 16; ++c)
-            tmem_ld16(tbase + lane_base + col + 16 * c, *reinterpret_cast<uint32_t(*)[16]>(v + 16 * c));
-          tc_wait_ld();
+          for (int c0 = 0; c0 < T; c0 += 16) {
+            uint32_t vr[16], vi[16];
+            tmem_ld16(tbase + lane_base + col + c0, vr);
+            tmem_ld16(tbase + lane_base + col + T + c0, vi);
+            tc_wait_ld();
+#pragma unroll
+            for (int n = 0; n < 16; ++n) {
+              const float re = __uint_as_float(vr[n]);
+              const float im = __uint_as_float(vi[n]);
+              sc[c0 + n] = fmaf(re, re, im * im);
+            }
+          }
           tc_fence_before();
           __syncwarp();
           if (lane == 0) mbar_arrive(&bar_aempty[s]);
-          // fidelities of the T windows of this stage: window j = st + n*A + i
-          float sc[T];
-#pragma unroll
-          for (int n = 0; n < T; ++n) {
-            const float re = __uint_as_float(v[n]);
-            const float im = __uint_as_float(v[T + n]);
-            sc[n] = fmaf(re, re, im * im);
-          }
-          const int64_t jbase = st + i;
           const bool full = jbase >= j_lo && jbase + (int64_t)(T - 1) * A < j_hi;
           if (kDense) {
             if (have_read) {
@@ -197,14 +199,12 @@ __global__ void __launch_bounds__(Sh::NTHREADS, 1) scan_tc_kernel(DevIndex ix, S
               }
             }
           } else {
-            float mx;
             if (full) {
               mx = sc[0];
 #pragma unroll
               for (int n = 1; n + 1 < T; n += 2) mx = fmax3(mx, sc[n], sc[n + 1]);
               if ((T & 1) == 0) mx = fmaxf(mx, sc[T - 1]);
             } else {
-              mx = -INFINITY;
 #pragma unroll
               for (int n = 0; n < T; ++n) {
                 const int64_t j = jbase + (int64_t)n * A;
@@ -232,6 +232,7 @@ __global__ void __launch_bounds__(Sh::NTHREADS, 1) scan_tc_kernel(DevIndex ix, S
     if (lane == 0) {
       uint32_t gs = 0, gb = 0, it = 0;
       bool ok = true;
+      const uint64_t b_desc0 = smem_desc_sw128(smem_u32(b_ring));
       for (int item = blockIdx.x; item < n_items && ok; item += gridDim.x, ++it) {
         const int rng = item / a.n_groups;
         const int64_t st_begin = a.st0 + (int64_t)rng * a.range_len;
@@ -245,13 +246,14 @@ __global__ void __launch_bounds__(Sh::NTHREADS, 1) scan_tc_kernel(DevIndex ix, S
           if (!mbar_wait(&bar_bfull[slot], (gb / NB) & 1, abort_flag, a.status)) { ok = false; break; }
           if (!mbar_wait(&bar_aempty[s], ((gs / STAGES) & 1) ^ 1, abort_flag, a.status)) { ok = false; break; }
           tc_fence_after();
-          const uint32_t b_addr = smem_u32(b_ring + slot * Sh::B_SLOT_BYTES);
+          // descriptors differ between B slots only in the start-address field
+          const uint64_t slot_desc = b_desc0 + (uint64_t)((slot * Sh::B_SLOT_BYTES) >> 4);
 #pragma unroll
           for (int t = 0; t < NT; ++t) {
             const uint32_t d_tmem = tbase + (uint32_t)(Sh::ACC0 + ((int)s * NT + t) * 2 * T);
 #pragma unroll
             for (int kk = 0; kk < Sh::KSTEPS; ++kk) {
-              const uint64_t bdesc = smem_desc_sw128(b_addr + (kk >> 2) * Sh::KBLK_BYTES + (kk & 3) * 32);
+              const uint64_t bdesc = slot_desc + (uint64_t)((((kk >> 2) * Sh::KBLK_BYTES) + (kk & 3) * 32) >> 4);
               tc_mma_ts(d_tmem, tbase + (uint32_t)(t * D + 8 * kk), bdesc, Sh::IDESC, kk > 0 ? 1u : 0u);
             }
           }

@@ -54,8 +54,10 @@ struct ThreadList {
     thr = ws;
   }
 
-  // window number j starts at j*stride_pos; buckets are floor(start / sep)
-  __device__ __forceinline__ void insert(float sc, uint32_t j, int sep, int stride_pos) {
+  // window number j starts at j*stride_pos; buckets are floor(start / sep).
+  // Out of line: the scans call it rarely, and inlining it at every score
+  // position would bloat the instruction stream of the hot loop.
+  __device__ __noinline__ void insert(float sc, uint32_t j, int sep, int stride_pos) {
     if (sep > 0) {
       const int64_t bucket = (int64_t)j * stride_pos / sep;
       for (int e = 0; e < depth; ++e) {

@@ -60,6 +60,7 @@ EXPORTS = {
     "rope_score_topk": ([_P, _P, _P, _P, _I64, _P, _P, _P, _P], ctypes.c_int),
     "rope_score_dense": ([_P, _P, _P, _P, _I64, _I32, _I64, _I64, _P, _P], ctypes.c_int),
     "rope_map": ([_P, _P, _P, _I64, _P, _P, _P, _P], ctypes.c_int),
+    "rope_merge_shards_host": ([_P, _P, _I32, _I64, _I32, _I32, _I32, _P, _P], ctypes.c_int),
     "rope_profile_enable": ([_I32], ctypes.c_int),
     "rope_profile_read": ([_P, _I32, _P], ctypes.c_int),
 }
@@ -144,7 +145,7 @@ def rope_mer_bins(p: Params, packed: torch.Tensor, length: int, stream=None) -> 
 
 class _CudaArray:
     def __init__(self, ptr: int, n: int, typestr: str):
-        self.__cuda_array_interface__ = dict(shape=(n,), typestr=typestr, data=(ptr, True), version=3)
+        self.__cuda_array_interface__ = dict(shape=(n,), typestr=typestr, data=(ptr, False), version=3)
 
 
 def _device_view(ptr: int, n: int, typestr: str, dtype) -> torch.Tensor:
@@ -279,3 +280,15 @@ def rope_profile_read(capacity: int) -> np.ndarray:
     n = ctypes.c_int32()
     _check(load().rope_profile_read(ms.ctypes.data, capacity, ctypes.byref(n)))
     return ms[: 3 * n.value].reshape(n.value, 3).astype(np.float64)
+
+
+def rope_merge_shards_host(wins: np.ndarray, scores: np.ndarray, k_out: int, sep: int = 0):
+    """Merge per-shard top-k lists [n_shards, n_reads, k_in] (host arrays)."""
+    wins = np.ascontiguousarray(wins, dtype=np.int64)
+    scores = np.ascontiguousarray(scores, dtype=np.float32)
+    n_shards, n_reads, k_in = wins.shape
+    ow = np.empty((n_reads, k_out), dtype=np.int64)
+    os_ = np.empty((n_reads, k_out), dtype=np.float32)
+    _check(load().rope_merge_shards_host(wins.ctypes.data, scores.ctypes.data, n_shards, n_reads, k_in, k_out, sep,
+                                         ow.ctypes.data, os_.ctypes.data))
+    return ow, os_
