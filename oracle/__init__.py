@@ -61,6 +61,9 @@ def _load():
             "oracle_levenshtein": ([p, i32, p, i32], i32),
             "oracle_levenshtein_pairs": ([p, i64, p, p, p, p, i64, i32, i32, p], i32),
             "oracle_max_threads": ([], i32),
+            "oracle_mlp_forward": ([p, p, p, f64, i32, i32, p, i64, p], None),
+            "oracle_mlp_grad": ([p, p, p, f64, i32, i32, p, p, i64, p, p, p, p], f64),
+            "oracle_adamw": ([p, p, p, p, i64, i64, f64, f64, f64, f64, f64], None),
         }
         for name, (args, res) in sig.items():
             fn = getattr(lib, name)
@@ -246,3 +249,45 @@ def levenshtein_pairs(ref, seqs, offsets, read_idx, win_start, N: int, n_threads
 
 def max_threads() -> int:
     return _load().oracle_max_threads()
+
+
+# ------------------------------------------------------------ reranker network
+
+class MLP:
+    """FP64 reference of the reranker network: y = w2 . GELU(W1 x + b1) + b2."""
+
+    def __init__(self, W1, b1, w2, b2):
+        self.W1 = np.ascontiguousarray(W1, dtype=np.float64)
+        self.b1 = np.ascontiguousarray(b1, dtype=np.float64)
+        self.w2 = np.ascontiguousarray(w2, dtype=np.float64)
+        self.b2 = float(b2)
+
+    @property
+    def shape(self):
+        return self.W1.shape  # (H, F)
+
+    def forward(self, X) -> np.ndarray:
+        X = np.ascontiguousarray(X, dtype=np.float64)
+        H, F = self.shape
+        y = np.empty(len(X))
+        _load().oracle_mlp_forward(_p(self.W1), _p(self.b1), _p(self.w2), self.b2, F, H, _p(X), len(X), _p(y))
+        return y
+
+    def grad(self, X, t):
+        """(loss, dW1, db1, dw2, db2) of the mean squared error."""
+        X = np.ascontiguousarray(X, dtype=np.float64)
+        t = np.ascontiguousarray(t, dtype=np.float64)
+        H, F = self.shape
+        gW1, gb1, gw2 = np.empty((H, F)), np.empty(H), np.empty(H)
+        gb2 = ctypes.c_double()
+        loss = _load().oracle_mlp_grad(_p(self.W1), _p(self.b1), _p(self.w2), self.b2, F, H, _p(X), _p(t), len(X),
+                                       _p(gW1), _p(gb1), _p(gw2), ctypes.byref(gb2))
+        return loss, gW1, gb1, gw2, gb2.value
+
+
+def adamw(p, g, m, v, step, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, wd=0.01):
+    """In-place FP64 AdamW step on flat float64 arrays p, m, v with gradient g."""
+    for a in (p, m, v):
+        assert a.dtype == np.float64 and a.flags.c_contiguous
+    g = np.ascontiguousarray(g, dtype=np.float64)
+    _load().oracle_adamw(_p(p), _p(g), _p(m), _p(v), len(p), step, lr, beta1, beta2, eps, wd)

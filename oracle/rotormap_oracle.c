@@ -558,3 +558,77 @@ int oracle_max_threads(void) {
   return 1;
 #endif
 }
+
+/* ---------------------------------------------------------------------- */
+/* Candidate reranker network (the paper has none; this is the reference of  */
+/* the library's learned reranker). Two layers, FP64:                        */
+/*   pre = W1 x + b1   (W1: H x F, row-major),  h = GELU(pre),               */
+/*   y   = w2 . h + b2,                                                       */
+/* GELU(z) = z * Phi(z) = 0.5 z (1 + erf(z / sqrt 2)) (exact, not tanh).     */
+/* Loss: mean over the batch of (y - t)^2.                                   */
+/* Parity: the backward is pinned by finite differences of the forward, the */
+/* forward by GELU's closed form; no passage of the paper pins either.      */
+
+static double gelu(double z) { return 0.5 * z * (1.0 + erf(z / 1.4142135623730951)); }
+static double gelu_grad(double z) {
+  return 0.5 * (1.0 + erf(z / 1.4142135623730951)) + z * exp(-0.5 * z * z) / 2.5066282746310002;
+}
+
+/* y[b] for b < B; X is B x F row-major */
+void oracle_mlp_forward(const double* W1, const double* b1, const double* w2, double b2, int F, int H,
+                        const double* X, int64_t B, double* y) {
+  for (int64_t b = 0; b < B; ++b) {
+    double acc = b2;
+    for (int j = 0; j < H; ++j) {
+      double z = b1[j];
+      for (int f = 0; f < F; ++f) z += W1[j * F + f] * X[b * F + f];
+      acc += w2[j] * gelu(z);
+    }
+    y[b] = acc;
+  }
+}
+
+/* loss and gradients of the mean squared error over the batch */
+double oracle_mlp_grad(const double* W1, const double* b1, const double* w2, double b2, int F, int H,
+                       const double* X, const double* t, int64_t B, double* gW1, double* gb1, double* gw2,
+                       double* gb2) {
+  double* z = (double*)malloc(sizeof(double) * H);
+  for (int i = 0; i < H * F; ++i) gW1[i] = 0.0;
+  for (int j = 0; j < H; ++j) gb1[j] = gw2[j] = 0.0;
+  *gb2 = 0.0;
+  double loss = 0.0;
+  for (int64_t b = 0; b < B; ++b) {
+    double y = b2;
+    for (int j = 0; j < H; ++j) {
+      z[j] = b1[j];
+      for (int f = 0; f < F; ++f) z[j] += W1[j * F + f] * X[b * F + f];
+      y += w2[j] * gelu(z[j]);
+    }
+    const double r = y - t[b];
+    loss += r * r / (double)B;
+    const double dy = 2.0 * r / (double)B;
+    *gb2 += dy;
+    for (int j = 0; j < H; ++j) {
+      gw2[j] += dy * gelu(z[j]);
+      const double dz = dy * w2[j] * gelu_grad(z[j]);
+      gb1[j] += dz;
+      for (int f = 0; f < F; ++f) gW1[j * F + f] += dz * X[b * F + f];
+    }
+  }
+  free(z);
+  return loss;
+}
+
+/* One AdamW step (Loshchilov & Hutter, decoupled weight decay) on n
+ * parameters at step number `step` (1-based):
+ *   m = b1 m + (1-b1) g;  v = b2 v + (1-b2) g^2;
+ *   p = p (1 - lr wd) - lr (m / (1-b1^step)) / (sqrt(v / (1-b2^step)) + eps) */
+void oracle_adamw(double* p, const double* g, double* m, double* v, int64_t n, int64_t step, double lr, double beta1,
+                  double beta2, double eps, double wd) {
+  const double c1 = 1.0 - pow(beta1, (double)step), c2 = 1.0 - pow(beta2, (double)step);
+  for (int64_t i = 0; i < n; ++i) {
+    m[i] = beta1 * m[i] + (1.0 - beta1) * g[i];
+    v[i] = beta2 * v[i] + (1.0 - beta2) * g[i] * g[i];
+    p[i] = p[i] * (1.0 - lr * wd) - lr * (m[i] / c1) / (sqrt(v[i] / c2) + eps);
+  }
+}

@@ -2,6 +2,7 @@
 // launchers of the other translation units.
 #pragma once
 
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -81,5 +82,28 @@ cudaError_t launch_scan_tc(const DevIndex& ix, const ScanArgs& a, bool dense, in
 
 // rope_merge.cu
 cudaError_t launch_merge(const DevIndex& ix, const MergeArgs& a, cudaStream_t st);
+
+// rope_rerank.cu
+constexpr int kMaxFeatures = 32;
+struct MlpWeights {
+  int32_t F, H;
+  __nv_bfloat16* W1;  // [H, F]
+  float* b1;          // [H]
+  __nv_bfloat16* w2;  // [H]
+  float* b2;          // [1]
+};
+cudaError_t launch_levenshtein(const uint32_t* packed, const uint8_t* seqs, const int64_t* offsets,
+                               const int64_t* read_idx, const int64_t* win_start, int64_t n_pairs, int N, int32_t* out,
+                               cudaStream_t st);
+cudaError_t launch_features(const DevIndex& ix, const float* emb_f32, const float* norms, const int64_t* cand_win,
+                            const float* cand_score, int64_t n_reads, int K, int F, float* X, cudaStream_t st);
+cudaError_t launch_mlp_forward(const MlpWeights& w, const float* X, int64_t B, float* y, float* pre, const float* t,
+                               float* dy, float* sq, cudaStream_t st);
+cudaError_t launch_mlp_backward(const MlpWeights& w, const float* X, int64_t B, const float* pre, const float* dy,
+                                const float* sq, float* grad, float* loss, cudaStream_t st);
+cudaError_t launch_adamw(const MlpWeights& w, const float* grad, float* master, float* m1, float* m2, int64_t step,
+                         float lr, float beta1, float beta2, float eps, float wd, cudaStream_t st);
+cudaError_t launch_prune(const int64_t* cand_win, const float* cand_score, const float* pred, int64_t n_reads, int K,
+                         int keep, int64_t* out_win, float* out_score, float* out_pred, cudaStream_t st);
 
 }  // namespace rope

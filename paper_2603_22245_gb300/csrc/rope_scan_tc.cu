@@ -54,6 +54,7 @@ struct TcShape {
   static_assert(A_COLS + STAGES * NT * 2 * T <= TMEM_COLS, "tensor memory budget");
   static_assert(B_SLOT_BYTES % 1024 == 0 && KBLK_BYTES % 1024 == 0, "swizzle atoms");
   static_assert((2 * T) % 16 == 0 && 2 * T <= 256, "MMA N");
+  static_assert(T == 8 || T % 16 == 0, "the epilogue loads 16-column chunks (or one for T = 8)");
 };
 
 struct TcLaunch {
@@ -173,17 +174,30 @@ __global__ void __launch_bounds__(Sh::NTHREADS, 1) scan_tc_kernel(DevIndex ix, S
           const int64_t jbase = st + i;  // column n holds window jbase + n*A
           float mx = -INFINITY;
           float sc[T];
-#pragma unroll
-          for (int c0 = 0; c0 < T; c0 += 16) {
-            uint32_t vr[16], vi[16];
-            tmem_ld16(tbase + lane_base + col + c0, vr);
-            tmem_ld16(tbase + lane_base + col + T + c0, vi);
+          if constexpr (T == 8) {
+            // one 16-column load holds Re (columns 0..7) and Im (8..15)
+            uint32_t v[16];
+            tmem_ld16(tbase + lane_base + col, v);
             tc_wait_ld();
 #pragma unroll
-            for (int n = 0; n < 16; ++n) {
-              const float re = __uint_as_float(vr[n]);
-              const float im = __uint_as_float(vi[n]);
-              sc[c0 + n] = fmaf(re, re, im * im);
+            for (int n = 0; n < 8; ++n) {
+              const float re = __uint_as_float(v[n]);
+              const float im = __uint_as_float(v[8 + n]);
+              sc[n] = fmaf(re, re, im * im);
+            }
+          } else {
+#pragma unroll
+            for (int c0 = 0; c0 < T; c0 += 16) {
+              uint32_t vr[16], vi[16];
+              tmem_ld16(tbase + lane_base + col + c0, vr);
+              tmem_ld16(tbase + lane_base + col + T + c0, vi);
+              tc_wait_ld();
+#pragma unroll
+              for (int n = 0; n < 16; ++n) {
+                const float re = __uint_as_float(vr[n]);
+                const float im = __uint_as_float(vi[n]);
+                sc[c0 + n] = fmaf(re, re, im * im);
+              }
             }
           }
           tc_fence_before();

@@ -434,3 +434,59 @@ def test_levenshtein_of_planted_reads_bounded_by_edits():
     for i in range(rd.n):
         span = ref[rd.true_pos[i]:rd.true_pos[i] + rd.true_span[i]].tobytes()
         assert oracle.levenshtein(rd.read(i), span) <= rd.n_edits[i]
+
+
+# ------------------------------------------------------------------ reranker network reference
+
+def _mlp(F=7, H=5, seed=0):
+    rng = np.random.default_rng(seed)
+    return oracle.MLP(rng.normal(size=(H, F)) * 0.5, rng.normal(size=H) * 0.1, rng.normal(size=H) * 0.5, 0.3)
+
+
+def test_mlp_forward_gelu_closed_form():
+    """GELU(z) = z * Phi(z): with one hidden unit, W1 = e_f, b1 = 0, w2 = 1, b2 = 0
+    the network returns z * Phi(z) of the chosen input."""
+    from scipy.stats import norm
+
+    net = oracle.MLP(np.array([[0.0, 1.0, 0.0]]), np.zeros(1), np.ones(1), 0.0)
+    z = np.array([-3.0, -1.0, -0.2, 0.0, 0.5, 1.0, 2.5])
+    X = np.stack([np.full_like(z, 7.0), z, np.full_like(z, -4.0)], axis=1)
+    assert np.allclose(net.forward(X), z * norm.cdf(z), rtol=1e-14, atol=1e-16)
+
+
+def test_mlp_grad_finite_differences():
+    net = _mlp()
+    rng = np.random.default_rng(1)
+    X, t = rng.normal(size=(11, 7)), rng.normal(size=11)
+    loss, gW1, gb1, gw2, gb2 = net.grad(X, t)
+    assert loss == pytest.approx(np.mean((net.forward(X) - t) ** 2), rel=1e-13)
+    h = 1e-6
+    for name, arr, g in (("W1", net.W1, gW1), ("b1", net.b1, gb1), ("w2", net.w2, gw2)):
+        flat, gflat = arr.reshape(-1), g.reshape(-1)
+        for i in range(flat.size):
+            old = flat[i]
+            flat[i] = old + h
+            lp = np.mean((net.forward(X) - t) ** 2)
+            flat[i] = old - h
+            lm = np.mean((net.forward(X) - t) ** 2)
+            flat[i] = old
+            assert gflat[i] == pytest.approx((lp - lm) / (2 * h), rel=1e-6, abs=1e-9), (name, i)
+    b = net.b2
+    net.b2 = b + h
+    lp = np.mean((net.forward(X) - t) ** 2)
+    net.b2 = b - h
+    lm = np.mean((net.forward(X) - t) ** 2)
+    net.b2 = b
+    assert gb2 == pytest.approx((lp - lm) / (2 * h), rel=1e-6)
+
+
+def test_adamw_first_step_closed_form():
+    """At step 1 the bias-corrected update is -lr * sign(g) (|g| >> eps), plus
+    the decoupled decay p * lr * wd."""
+    p = np.array([1.0, -2.0, 0.5])
+    g = np.array([0.3, -0.7, 2.0])
+    m, v = np.zeros(3), np.zeros(3)
+    p0 = p.copy()
+    oracle.adamw(p, g, m, v, 1, lr=1e-2, wd=0.1)
+    assert np.allclose(p, p0 * (1 - 1e-3) - 1e-2 * np.sign(g), rtol=0, atol=1e-9)
+    assert np.allclose(m, 0.1 * g) and np.allclose(v, 0.001 * g * g)
