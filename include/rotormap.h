@@ -180,6 +180,29 @@ rope_status rope_score_topk(const rope_index* idx, const float* emb_f32, const u
                             const float* norms, int64_t n_reads, const rope_score_opts* opts, int64_t* out_win,
                             float* out_score, cudaStream_t stream);
 
+/* Allocation-free variant of rope_score_topk (the paper has no counterpart:
+ * this is for callers, not for the method). For callers that must not have
+ * the library allocate device memory during the call -- e.g. a process that
+ * gives nearly all device memory to its own arena at start-up, or a
+ * latency-critical loop that cannot take the device-wide synchronisation of
+ * cudaMalloc/cudaFree. Same arguments, results and kernels as
+ * rope_score_topk; the caller still passes the inputs and outputs. The
+ * scratch (status word + candidate lists) is a 16 MiB array inside the
+ * library that every GPU which loads the library holds until exit; a call
+ * needing more (n_reads * n_ranges * cand_depth * 8 bytes beyond 16 MiB - 256 B)
+ * is rejected with ROPE_ERR_INVALID_ARG and a message giving the limit
+ * (n_ranges = 0 picks the largest split that fits). No cudaMalloc, cudaFree
+ * or pool allocation happens. The first call on a device looks up the array's
+ * device address (cudaGetSymbolAddress), so make that first call before any
+ * stream capture on that device. All calls on a device share the one array:
+ * calls that overlap on the GPU (e.g. on two streams at once) race and
+ * corrupt each other's results; serialise them. A bounded in-kernel wait that
+ * runs out here is recorded only in the array's own status word (not the one
+ * rope_sync_status reads) and shows up as (-1, -inf) entries. */
+rope_status rope_score_topk_noalloc(const rope_index* idx, const float* emb_f32, const uint16_t* emb_bf16,
+                                    const float* norms, int64_t n_reads, const rope_score_opts* opts,
+                                    int64_t* out_win, float* out_score, cudaStream_t stream);
+
 /* Every score of every read against windows [j_begin, j_begin+count), as
  * n_reads x count floats, computed by the same scan kernel as rope_score_topk
  * (FP32 or BF16 tensor-core path) with its top-k stage replaced by a store.

@@ -724,3 +724,128 @@ extern "C" rope_status rope_map(const rope_index* idx, const uint8_t* seqs, cons
   cudaFreeAsync(norms, stream);
   return st;
 }
+
+// ---------------------------------------------------------------- allocation-free scan
+//
+// rope_score_topk_noalloc: the same scan, merge and re-scoring as
+// rope_score_topk, for callers that must not have the library allocate device
+// memory at call time -- for example a process that hands nearly all device
+// memory to its own arena up front, or a latency-critical loop that cannot
+// afford the device-wide synchronisation cudaMalloc/cudaFree imply. Its scratch
+// (a status word and the per-read candidate lists) is this file-scope array,
+// which every GPU that loads the library holds until the process exits.
+
+namespace {
+
+constexpr size_t kNoAllocScratchBytes = (size_t)16 << 20;  // 16 MiB per device
+constexpr size_t kNoAllocHeadBytes = 256;                   // status word, padded
+__device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+constexpr int kNoAllocMaxDevices = 64;
+std::mutex g_noalloc_mu;
+void* g_noalloc_addr[kNoAllocMaxDevices];  // device address of g_noalloc_scratch
+int g_noalloc_sms[kNoAllocMaxDevices];
+
+// Once per device, with that device current: the host-side name of the array
+// is only a stand-in, so fetch the array's device address.
+rope_status noalloc_setup(int dev, void** addr, int* sms) {
+  std::lock_guard<std::mutex> lk(g_noalloc_mu);
+  if (!g_noalloc_addr[dev]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return fail(ROPE_ERR_CUDA, "cudaGetSymbolAddress: %s", cudaGetErrorString(e));
+    int n = 0;
+    e = cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return fail(ROPE_ERR_CUDA, "cudaDeviceGetAttribute: %s", cudaGetErrorString(e));
+    g_noalloc_sms[dev] = n;
+    g_noalloc_addr[dev] = p;
+  }
+  *addr = g_noalloc_addr[dev];
+  *sms = g_noalloc_sms[dev];
+  return ROPE_OK;
+}
+
+}  // namespace
+
+extern "C" rope_status rope_score_topk_noalloc(const rope_index* idx, const float* emb_f32, const uint16_t* emb_bf16,
+                                               const float* norms, int64_t n_reads, const rope_score_opts* opts,
+                                               int64_t* out_win, float* out_score, cudaStream_t stream) {
+  if (!idx) return fail(ROPE_ERR_INVALID_ARG, "index is NULL");
+  rope_score_opts o;
+  rope_status st = check_opts(opts, &o);
+  if (st != ROPE_OK) return st;
+  if (n_reads < 0) return fail(ROPE_ERR_INVALID_ARG, "n_reads < 0");
+  if (n_reads == 0) return ROPE_OK;
+  if (!emb_f32 || !norms || !out_win || !out_score) return fail(ROPE_ERR_INVALID_ARG, "NULL pointer");
+  if (o.precision == ROPE_PREC_BF16 && !emb_bf16) return fail(ROPE_ERR_INVALID_ARG, "BF16 scan needs emb_bf16");
+  int dev = 0;
+  ROPE_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kNoAllocMaxDevices) return fail(ROPE_ERR_UNSUPPORTED, "device ordinal %d", dev);
+  void* base = nullptr;
+  int num_sms = 0;
+  if ((st = noalloc_setup(dev, &base, &num_sms)) != ROPE_OK) return st;
+
+  const DevIndex& ix = idx->ix;
+  const int64_t jb = o.j_begin > 0 ? o.j_begin : 0;
+  const int64_t je = o.j_end > 0 ? (o.j_end < ix.W ? o.j_end : ix.W) : ix.W;
+  if (jb > ix.W) return fail(ROPE_ERR_INVALID_ARG, "j_begin beyond the last window");
+  const size_t cap = kNoAllocScratchBytes - kNoAllocHeadBytes;
+  const size_t per_range = (size_t)n_reads * o.cand_depth * sizeof(Candidate);
+  if (per_range > cap)
+    return fail(ROPE_ERR_INVALID_ARG,
+                "n_reads=%lld x cand_depth=%d needs %zu bytes of candidates per window range; the allocation-free "
+                "scratch holds %zu bytes (at most %zu reads at this depth)",
+                (long long)n_reads, o.cand_depth, per_range, cap, cap / ((size_t)o.cand_depth * sizeof(Candidate)));
+
+  ScanPlan pl;
+  int32_t n_ranges = 1;
+  if (je > jb) {
+    if ((st = plan_scan(idx, o.precision, n_reads, jb, je, o.n_ranges, num_sms, &pl)) != ROPE_OK) return st;
+    if ((size_t)pl.a.n_ranges * per_range > cap) {
+      if (o.n_ranges > 0)
+        return fail(ROPE_ERR_INVALID_ARG, "n_ranges=%d needs %zu bytes of scratch; the allocation-free scratch "
+                    "holds %zu", o.n_ranges, (size_t)pl.a.n_ranges * per_range, cap);
+      if ((st = plan_scan(idx, o.precision, n_reads, jb, je, (int32_t)(cap / per_range), num_sms, &pl)) != ROPE_OK)
+        return st;
+    }
+    n_ranges = pl.a.n_ranges;
+  }
+  int* status = static_cast<int*>(base);
+  Candidate* cand = reinterpret_cast<Candidate*>(static_cast<unsigned char*>(base) + kNoAllocHeadBytes);
+  const size_t cand_bytes = (size_t)n_ranges * per_range;
+  // the status word must start at zero; the candidate lists are fully written
+  // by the scan (or set empty below) before the merge reads them
+  ROPE_CUDA(cudaMemsetAsync(status, 0, sizeof(int), stream));
+  if (je > jb) {
+    pl.a.emb_f32 = emb_f32;
+    pl.a.emb_bf16 = emb_bf16;
+    pl.a.norms = norms;
+    pl.a.cand_depth = o.cand_depth;
+    pl.a.sep = o.sep;
+    pl.a.cand = cand;
+    pl.a.dense = nullptr;
+    pl.a.status = status;
+    cudaError_t e = pl.tc ? launch_scan_tc(ix, pl.a, false, num_sms, stream)
+                          : launch_scan_fp32(ix, pl.a, false, num_sms, stream);
+    if (e != cudaSuccess) return fail(ROPE_ERR_CUDA, "scan launch: %s", cudaGetErrorString(e));
+  } else {
+    ROPE_CUDA(cudaMemsetAsync(cand, 0xFF, cand_bytes, stream));  // every slot empty
+  }
+  MergeArgs m{};
+  m.cand = cand;
+  m.n_reads = n_reads;
+  m.n_ranges = n_ranges;
+  m.cand_depth = o.cand_depth;
+  m.k = o.k;
+  m.sep = o.sep;
+  m.rescore = o.rescore;
+  m.rescore_depth = o.rescore_depth;
+  m.emb_f32 = emb_f32;
+  m.norms = norms;
+  m.out_win = out_win;
+  m.out_score = out_score;
+  m.status = status;
+  cudaError_t e = launch_merge(ix, m, stream);
+  if (e != cudaSuccess) return fail(ROPE_ERR_CUDA, "merge launch: %s", cudaGetErrorString(e));
+  return ROPE_OK;
+}

@@ -58,6 +58,7 @@ EXPORTS = {
     "rope_window_embeddings": ([_P, _I64, _I64, _P, _P], ctypes.c_int),
     "rope_encode_reads": ([_P, _P, _P, _I64, _P, _P, _P, _P], ctypes.c_int),
     "rope_score_topk": ([_P, _P, _P, _P, _I64, _P, _P, _P, _P], ctypes.c_int),
+    "rope_score_topk_noalloc": ([_P, _P, _P, _P, _I64, _P, _P, _P, _P], ctypes.c_int),
     "rope_score_dense": ([_P, _P, _P, _P, _I64, _I32, _I64, _I64, _P, _P], ctypes.c_int),
     "rope_map": ([_P, _P, _P, _I64, _P, _P, _P, _P], ctypes.c_int),
     "rope_merge_shards_host": ([_P, _P, _I32, _I64, _I32, _I32, _I32, _P, _P], ctypes.c_int),
@@ -243,6 +244,21 @@ def rope_score_topk(idx: Index, emb_f32: torch.Tensor, emb_bf16: torch.Tensor | 
     o = _opts(k, sep, precision, rescore, cand_depth, rescore_depth, n_ranges, j_begin, j_end)
     _check(load().rope_score_topk(idx.handle, _ptr(emb_f32), _ptr(emb_bf16), _ptr(norms), n, ctypes.byref(o),
                                   _ptr(out[0]), _ptr(out[1]), _stream(stream)))
+    return out
+
+
+def rope_score_topk_noalloc(idx: Index, emb_f32: torch.Tensor, emb_bf16: torch.Tensor | None, norms: torch.Tensor,
+                            out: tuple, k: int = 8, sep: int = 0, precision="bf16", rescore=None, cand_depth: int = 0,
+                            rescore_depth: int = 0, n_ranges: int = 0, j_begin: int = 0, j_end: int = 0,
+                            stream=None):
+    """rope_score_topk without any device allocation inside the library: the
+    caller passes the outputs (starts int64 [n, k], fidelities float32 [n, k])
+    and the scratch comes from the library's fixed 16 MiB per-device array.
+    Calls overlapping on one GPU race on that array."""
+    n = norms.shape[0]
+    o = _opts(k, sep, precision, rescore, cand_depth, rescore_depth, n_ranges, j_begin, j_end)
+    _check(load().rope_score_topk_noalloc(idx.handle, _ptr(emb_f32), _ptr(emb_bf16), _ptr(norms), n,
+                                          ctypes.byref(o), _ptr(out[0]), _ptr(out[1]), _stream(stream)))
     return out
 
 
