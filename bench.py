@@ -71,6 +71,8 @@ def parse():
     ap.add_argument("--cpu-reads", type=int, default=32)
     ap.add_argument("--cpu-windows", type=int, default=1_000_000)
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--rerank-train-reads", type=int, default=65536)
+    ap.add_argument("--rerank-eval-reads", type=int, default=32768)
     return ap.parse_args()
 
 
@@ -177,6 +179,49 @@ def cpu_baseline(ref, rd, wl, n_reads, n_windows):
     return {"value": sub.n * n_windows / dt, "unit": UNIT, "cores": oracle.max_threads(), "kind": "oracle",
             "sample": f"{sub.n} reads x the first {n_windows} windows, exhaustive FP64 scoring + full sort",
             "seconds": dt}
+
+
+def rerank_leg(rm, idx, ref, wl, args):
+    """Learned reranker (outside the timed region): candidates k=16 (one per
+    bucket of width N) of reads at 0-15% error, exact Levenshtein labels, 5
+    AdamW epochs on the GPU, then on new reads: keep 2 of 16 by predicted
+    distance vs by score, against the plain top-8."""
+    import torch
+
+    import synth
+    from paper_2603_22245_gb300 import rerank
+
+    K, N = 16, wl["N"]
+    tr = synth.reads_mixed_error(ref, args.rerank_train_reads, seed=wl["read_seed"] + 500)
+    te = synth.reads_mixed_error(ref, args.rerank_eval_reads, seed=wl["read_seed"] + 900)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    X, t, valid, _ = rerank.training_set(idx, torch.from_numpy(tr.seqs).cuda(), torch.from_numpy(tr.offsets).cuda(),
+                                         k=K)
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    rr = rerank.Reranker(rerank.n_features(K, wl["m"]), 128, seed=11)
+    losses = rerank.train(rr, X, t, valid, epochs=5, batch=4096, lr=1e-3, weight_decay=0.01)
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    sd, od = torch.from_numpy(te.seqs).cuda(), torch.from_numpy(te.offsets).cuda()
+    rerank.rope_map_rerank(idx, sd, od, rr, k=K, keep=2)
+    torch.cuda.synchronize()
+    t3 = time.perf_counter()
+    w_rr, _, _ = rerank.rope_map_rerank(idx, sd, od, rr, k=K, keep=2)
+    torch.cuda.synchronize()
+    t4 = time.perf_counter()
+    w_sc, _, _ = rerank.rope_map_rerank(idx, sd, od, None, k=K, keep=2)
+    w8, _ = rm.rope_map(idx, sd, od, k=8, sep=N)
+    rm.rope_sync_status()
+    hit = lambda w: float((np.abs(w.cpu().numpy() - te.true_pos[:, None]) < N).any(axis=1).mean())
+    n_pairs = int(valid.numel())
+    rr.free()
+    return {"train_pairs": n_pairs, "label_s": t1 - t0, "train_s": t2 - t1, "epochs": 5,
+            "train_pairs_per_s": 5 * n_pairs / (t2 - t1), "epoch_loss": [round(x, 6) for x in losses],
+            "eval_reads": te.n, "map_rerank_reads_per_s": te.n / (t4 - t3),
+            "recall_top2_reranked": hit(w_rr), "recall_top2_score": hit(w_sc), "recall_top8_score": hit(w8),
+            "errors": "0-15% per read (2:1 substitutions : indel events)"}
 
 
 def run_reference(args, wl):
@@ -360,6 +405,10 @@ def main():
                "h2d_bytes_per_step": int(seq_pin.numel() + off_pin.numel() * 8),
                "d2h_bytes_per_step": int(w_pin.numel() * 8 + s_pin.numel() * 4)}
 
+    reranker = None
+    if args.rerank_train_reads > 0:
+        reranker = rerank_leg(rm, idx, ref, wl, args)
+
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu:
         cpu = cpu_baseline(ref, rd, wl, args.cpu_reads, args.cpu_windows)
@@ -374,7 +423,7 @@ def main():
                    f"reads sharded over {ws} GPU(s)"},
         "reads_per_s": reads_s, "top1_acc": acc_bf16, "fp32_plain": fp32,
         "speedup_vs_fp32_plain": value / ws / fp32["value"],
-        "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": 3 * args.steps, "clocks": clocks,
+        "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "reranker": reranker, "gpu_launches": 3 * args.steps, "clocks": clocks,
     }
     if rank == 0:
         print(json.dumps(line), flush=True)

@@ -218,6 +218,76 @@ rope_status rope_score_dense(const rope_index* idx, const float* emb_f32, const 
 rope_status rope_map(const rope_index* idx, const uint8_t* seqs, const int64_t* offsets, int64_t n_reads,
                      const rope_score_opts* opts, int64_t* out_win, float* out_score, cudaStream_t stream);
 
+/* ---- learned reranker (steps a8, a9) -------------------------------------
+ * The paper relates fidelity to Levenshtein distance (§1, §2.4) and keeps
+ * candidate loci by score or per-fragment thresholds (§3.3, §3.5). This
+ * optional stage learns, from the scan's own score features, each candidate's
+ * Levenshtein distance (§1) to the read head as a fraction of N, and keeps the
+ * candidates with the smallest prediction. Network: y = w2 . GELU(W1 x + b1)
+ * + b2 with exact GELU (z Phi(z)), W1 [hidden x F] and w2 stored in BF16, b1,
+ * b2 and all arithmetic in FP32; FP32 master weights and AdamW state
+ * (beta1 0.9, beta2 0.999, eps 1e-8, decoupled weight decay) for training.
+ * Parameters are flattened as W1 (row-major), b1, w2, b2: P = H*F + 2H + 1. */
+typedef struct rope_reranker rope_reranker;
+
+/* New network on the current device: F in [1,32] features, H in [1,1024]
+ * hidden units, Glorot-uniform weights from `seed`, zero biases. */
+rope_status rope_reranker_create(int32_t n_features, int32_t hidden, uint64_t seed, rope_reranker** out);
+void rope_reranker_free(rope_reranker* rr);
+/* FP32 master parameters (P floats, host) and the number of training steps taken. Synchronising. */
+rope_status rope_reranker_get(const rope_reranker* rr, float* params_host, int64_t* step);
+/* Replaces the parameters (P floats, host); reset_optimizer zeroes the AdamW
+ * moments and the step count. Synchronising. */
+rope_status rope_reranker_set(rope_reranker* rr, const float* params_host, int32_t reset_optimizer);
+/* Gradient (P floats, device) and mean squared error (device float) of the
+ * batch {X[sample_idx[i]], t[sample_idx[i]] : i < B} (rows 0..B-1 when
+ * sample_idx is NULL). X: rows of F floats. Deterministic reductions. */
+rope_status rope_reranker_grad(rope_reranker* rr, const float* X, const float* t, const int64_t* sample_idx,
+                               int64_t B, float* grad, float* loss, cudaStream_t stream);
+/* One AdamW step on that batch; its mean squared error is added to *loss_sum
+ * (device float) when loss_sum is not NULL. */
+rope_status rope_reranker_train_step(rope_reranker* rr, const float* X, const float* t, const int64_t* sample_idx,
+                                     int64_t B, float lr, float weight_decay, float* loss_sum, cudaStream_t stream);
+/* y[b] for the B rows of X (device). */
+rope_status rope_reranker_predict(const rope_reranker* rr, const float* X, int64_t B, float* y, cudaStream_t stream);
+/* Checkpoint: "ROPERR01", int32 F, int32 H, int64 step, then P floats each of
+ * parameters, first and second moments (little endian). Load requires the same
+ * F and H and restores the training state exactly. */
+rope_status rope_reranker_save(const rope_reranker* rr, const char* path);
+rope_status rope_reranker_load(rope_reranker* rr, const char* path);
+
+/* Exact Levenshtein distance (§1) between each read head (length N of the
+ * index) and the reference window starting at win_start[i], for the pairs
+ * (read_idx[i], win_start[i]); out_ld int32 [n_pairs], out_frac (may be NULL)
+ * float distance / N. Bit-parallel DP (Myers; global form), N <= 256. */
+rope_status rope_levenshtein(const rope_index* idx, const uint8_t* seqs, const int64_t* offsets,
+                             const int64_t* read_idx, const int64_t* win_start, int64_t n_pairs, int32_t* out_ld,
+                             float* out_frac, cudaStream_t stream);
+
+/* Feature rows X [n_reads * K, F], F = K + 2 + m, for each read's K candidates
+ * (cand_win/cand_score [n_reads, K] from rope_score_topk, best first):
+ * the read's K scores (missing = 0), the candidate's fidelity, its m per-band
+ * fidelities (§2.5, FP32 direct sums), and rank / K. Rows of missing
+ * candidates (start -1) are zero. */
+rope_status rope_rerank_features(const rope_index* idx, const float* emb_f32, const float* norms,
+                                 const int64_t* cand_win, const float* cand_score, int64_t n_reads, int32_t K,
+                                 float* X, cudaStream_t stream);
+
+/* Per read, the `keep` of its K candidates with the smallest pred (ties: higher
+ * score, then lower start); out_* [n_reads, keep], missing (-1, -inf, +inf). */
+rope_status rope_rerank_prune(const int64_t* cand_win, const float* cand_score, const float* pred, int64_t n_reads,
+                              int32_t K, int32_t keep, int64_t* out_win, float* out_score, float* out_pred,
+                              cudaStream_t stream);
+
+/* rope_map with opts->k candidates per read (use opts->sep = N for one per
+ * locus), then pruning to `keep` by the network's predicted distance; with
+ * rr = NULL the plain score ranking is kept (the fallback). out_pred
+ * [n_reads, keep] (may be NULL) receives the predicted distance / N (the rank
+ * for the fallback). */
+rope_status rope_map_rerank(const rope_index* idx, const uint8_t* seqs, const int64_t* offsets, int64_t n_reads,
+                            const rope_score_opts* opts, const rope_reranker* rr, int32_t keep, int64_t* out_win,
+                            float* out_score, float* out_pred, cudaStream_t stream);
+
 /* ---- multi-GPU: merge of window-range shards (host only) ---------------
  * The reference's windows can be split into disjoint ranges scanned on
  * different GPUs (segments are independent, §2.8). win_host/score_host hold

@@ -13,8 +13,7 @@
 #include <string>
 #include <vector>
 
-#include "rope_internal.h"
-#include "rotormap.h"
+#include "rope_host.h"
 
 using namespace rope;
 
@@ -23,6 +22,14 @@ using namespace rope;
 static thread_local char g_last_error[512] = "";
 
 static rope_status fail(rope_status st, const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_last_error, sizeof(g_last_error), fmt, ap);
+  va_end(ap);
+  return st;
+}
+
+rope_status rope::host_fail(rope_status st, const char* fmt, ...) {
   va_list ap;
   va_start(ap, fmt);
   vsnprintf(g_last_error, sizeof(g_last_error), fmt, ap);
@@ -55,12 +62,6 @@ extern "C" const char* rope_last_error(void) { return g_last_error; }
 // ---------------------------------------------------------------- per-device context
 
 namespace {
-
-struct DeviceCtx {
-  int* status = nullptr;       // device status word
-  cudaMemPool_t pool = nullptr;
-  int num_sms = 0;
-};
 
 std::mutex g_mu;
 std::map<int, DeviceCtx> g_ctx;
@@ -98,6 +99,15 @@ rope_status pool_alloc(DeviceCtx* c, void** p, size_t bytes, cudaStream_t st) {
   if (e != cudaSuccess) return fail(ROPE_ERR_CUDA, "cudaMallocFromPoolAsync: %s", cudaGetErrorString(e));
   return ROPE_OK;
 }
+
+}  // namespace
+
+rope_status rope::host_ctx(DeviceCtx** out) { return get_ctx(out); }
+rope_status rope::host_pool_alloc(DeviceCtx* c, void** p, size_t bytes, cudaStream_t st) {
+  return pool_alloc(c, p, bytes, st);
+}
+
+namespace {
 
 // ---------------------------------------------------------------- parameters and tables
 
@@ -307,14 +317,6 @@ extern "C" rope_status rope_profile_read(float* ms_host, int32_t capacity, int32
 }
 
 // ---------------------------------------------------------------- index
-
-struct rope_index {
-  int device = 0;
-  rope_params p{};
-  DevIndex ix{};
-  EncTables enc{};
-  std::vector<void*> owned;
-};
 
 extern "C" int32_t rope_dim(const rope_params* p) {
   if (check_params(p) != ROPE_OK) return -1;
@@ -526,7 +528,8 @@ rope_status plan_scan(const rope_index* idx, int32_t precision, int64_t n_reads,
     if (!scan_tc_supported(ix.D))
       return fail(ROPE_ERR_UNSUPPORTED, "tensor-core scan built for complex dimension 32 or 64, not %d", ix.D);
     if (ix.score_mode != 0) return fail(ROPE_ERR_UNSUPPORTED, "tensor-core scan takes score_mode 0 only");
-    if (ix.stride > 16) return fail(ROPE_ERR_UNSUPPORTED, "tensor-core scan takes stride <= 16");
+    if (ix.stride > scan_tc_max_stride())
+      return fail(ROPE_ERR_UNSUPPORTED, "tensor-core scan takes stride <= %d", scan_tc_max_stride());
     sup = scan_tc_super_tile(ix.D);
     group = scan_tc_group(ix.D);
   } else if (precision == ROPE_PREC_FP32) {

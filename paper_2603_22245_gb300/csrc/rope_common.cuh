@@ -79,26 +79,25 @@ __device__ __forceinline__ uint32_t bin_at(const uint32_t* __restrict__ packed, 
 
 // ---------------------------------------------------------------- generator
 
-// One chain of the window generator: LPC = D/4 lanes hold the D complex entries
-// of c(j), four consecutive entries per lane (entries 4l..4l+3 of lane l, all
-// in one band since 4^t is a multiple of 4). A step moves c(j) to c(j+1) by
+// One chain of the window generator: lanes hold the D complex entries of c(j),
+// BPL consecutive entries per lane (entries BPL*l .. BPL*l+BPL-1 of lane l, all
+// in one band since 4^t is a multiple of BPL). A step moves c(j) to c(j+1) by
 // the slide relations of §3.4, for stride S:
 //   c_b <- c_b - sum_{i<S} [bin(w+i) = b] e^{2 pi i f i/N}
 //   c_b <- c_b + sum_{i<S} [bin(w+N-s+1+i) = b] e^{2 pi i f (N-s+1+i)/N}
 //   c   <- c * e^{-2 pi i f S/N}
 // (for S = 1 these are exactly the paper's relations: every entry rotates by
 // w^{-f}, the leaving s-mer loses w^{-f}, the entering one gains w^{f(N-s)}).
-template <int D>
-struct Chain {
-  static constexpr int LPC = D / 4;
-  float cr[4], ci[4];
+template <int BPL>
+struct ChainB {
+  float cr[BPL], ci[BPL];
   int band;   // band k-1 of this lane's entries
   int b0;     // bin of entry 0 of this lane
   float rc, rs;  // rotation e^{-2 pi i f S / N}
   float ec, es;  // stride-1 entering phase e^{2 pi i f (N-s+1) / N}
 
   __device__ __forceinline__ void setup(const DevIndex& ix, int lane_in_chain) {
-    const int g0 = 4 * lane_in_chain;
+    const int g0 = BPL * lane_in_chain;
     band = g0 / ix.nb;
     b0 = g0 - band * ix.nb;
     const float2 r = ix.rot[band];
@@ -111,16 +110,21 @@ struct Chain {
 
   __device__ __forceinline__ void load(const float2* __restrict__ anchor, int lane_in_chain) {
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      const float2 v = anchor[4 * lane_in_chain + i];
+    for (int i = 0; i < BPL; ++i) {
+      const float2 v = anchor[BPL * lane_in_chain + i];
       cr[i] = v.x;
       ci[i] = v.y;
     }
   }
 
+  __device__ __forceinline__ void zero() {
+#pragma unroll
+    for (int i = 0; i < BPL; ++i) cr[i] = ci[i] = 0.f;
+  }
+
   __device__ __forceinline__ void rotate() {
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
+    for (int i = 0; i < BPL; ++i) {
       const float xr = cr[i], xi = ci[i];
       cr[i] = fmaf(xr, rc, -xi * rs);
       ci[i] = fmaf(xr, rs, xi * rc);
@@ -130,7 +134,7 @@ struct Chain {
   // stride 1: bout = bin leaving at the start, bin_in = bin entering at the end
   __device__ __forceinline__ void step1(uint32_t bout, uint32_t bin_in) {
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
+    for (int i = 0; i < BPL; ++i) {
       if ((uint32_t)(b0 + i) == bout) cr[i] -= 1.0f;
       if ((uint32_t)(b0 + i) == bin_in) {
         cr[i] += ec;
@@ -143,7 +147,7 @@ struct Chain {
   // general stride: one leaving (sub_at) or entering (add_at) location
   __device__ __forceinline__ void sub_at(uint32_t b, float2 v) {
 #pragma unroll
-    for (int i = 0; i < 4; ++i)
+    for (int i = 0; i < BPL; ++i)
       if ((uint32_t)(b0 + i) == b) {
         cr[i] -= v.x;
         ci[i] -= v.y;
@@ -151,12 +155,18 @@ struct Chain {
   }
   __device__ __forceinline__ void add_at(uint32_t b, float2 v) {
 #pragma unroll
-    for (int i = 0; i < 4; ++i)
+    for (int i = 0; i < BPL; ++i)
       if ((uint32_t)(b0 + i) == b) {
         cr[i] += v.x;
         ci[i] += v.y;
       }
   }
+};
+
+// Chains of D/4 lanes, four entries per lane (FP32 scan, window inspection).
+template <int D>
+struct Chain : ChainB<4> {
+  static constexpr int LPC = D / 4;
 };
 
 // ---------------------------------------------------------------- PTX: mbarrier
@@ -250,6 +260,16 @@ __device__ __forceinline__ void tc_mma_ts(uint32_t d_tmem, uint32_t a_tmem, uint
       "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
       " tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n}" ::"r"(d_tmem),
       "r"(a_tmem), "l"(b_desc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+// D[tmem] (+)= A[smem desc] * B[smem desc], kind::f16 (BF16 inputs, FP32 accumulate)
+__device__ __forceinline__ void tc_mma_ss(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc, uint32_t idesc,
+                                          uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(d_tmem),
+      "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(accumulate)
       : "memory");
 }
 

@@ -78,6 +78,7 @@ cudaError_t launch_scan_fp32(const DevIndex& ix, const ScanArgs& a, bool dense, 
 int scan_tc_supported(int D);
 int64_t scan_tc_super_tile(int D);
 int scan_tc_group(int D);
+int scan_tc_max_stride();
 cudaError_t launch_scan_tc(const DevIndex& ix, const ScanArgs& a, bool dense, int num_sms, cudaStream_t st);
 
 // rope_merge.cu
@@ -97,12 +98,15 @@ cudaError_t launch_levenshtein(const uint32_t* packed, const uint8_t* seqs, cons
                                cudaStream_t st);
 cudaError_t launch_features(const DevIndex& ix, const float* emb_f32, const float* norms, const int64_t* cand_win,
                             const float* cand_score, int64_t n_reads, int K, int F, float* X, cudaStream_t st);
-cudaError_t launch_mlp_forward(const MlpWeights& w, const float* X, int64_t B, float* y, float* pre, const float* t,
-                               float* dy, float* sq, cudaStream_t st);
-cudaError_t launch_mlp_backward(const MlpWeights& w, const float* X, int64_t B, const float* pre, const float* dy,
-                                const float* sq, float* grad, float* loss, cudaStream_t st);
+cudaError_t launch_mlp_forward(const MlpWeights& w, const float* X, const int64_t* idx, int64_t B, float* y, float* pre,
+                               const float* t, float* dy, float* sq, cudaStream_t st);
+cudaError_t launch_mlp_backward(const MlpWeights& w, const float* X, const int64_t* idx, int64_t B, const float* pre,
+                                const float* dy, const float* sq, float* grad, float* loss, int accumulate,
+                                cudaStream_t st);
 cudaError_t launch_adamw(const MlpWeights& w, const float* grad, float* master, float* m1, float* m2, int64_t step,
                          float lr, float beta1, float beta2, float eps, float wd, cudaStream_t st);
+cudaError_t launch_ld_fraction(const int32_t* ld, int64_t n, int N, float* out, cudaStream_t st);
+cudaError_t launch_rank_as_prediction(int64_t n_reads, int K, float* pred, cudaStream_t st);
 cudaError_t launch_prune(const int64_t* cand_win, const float* cand_score, const float* pred, int64_t n_reads, int K,
                          int keep, int64_t* out_win, float* out_score, float* out_pred, cudaStream_t st);
 

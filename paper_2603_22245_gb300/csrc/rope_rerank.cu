@@ -198,9 +198,10 @@ __device__ __forceinline__ float gelu_grad_f(float z) {
 // Forward: one thread per sample; BF16 weights staged in shared memory as FP32.
 // pre[s][j] is stored when `pre` is non-null (training), and with targets the
 // per-sample residual gradient dy = 2 (y - t) / B and squared error.
-__global__ void mlp_forward_kernel(MlpWeights w, const float* __restrict__ X, int64_t B, float* __restrict__ y,
-                                   float* __restrict__ pre, const float* __restrict__ t, float* __restrict__ dy,
-                                   float* __restrict__ sq) {
+// Sample s of the batch is row idx[s] of X and t (row s when idx is null).
+__global__ void mlp_forward_kernel(MlpWeights w, const float* __restrict__ X, const int64_t* __restrict__ idx,
+                                   int64_t B, float* __restrict__ y, float* __restrict__ pre,
+                                   const float* __restrict__ t, float* __restrict__ dy, float* __restrict__ sq) {
   extern __shared__ float mlp_smem[];
   float* W1 = mlp_smem;                  // H x F
   float* b1 = W1 + w.H * w.F;            // H
@@ -213,9 +214,10 @@ __global__ void mlp_forward_kernel(MlpWeights w, const float* __restrict__ X, in
   __syncthreads();
   const float b2 = w.b2[0];
   for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < B; s += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t row = idx ? idx[s] : s;
     float xs[kMaxFeatures];
 #pragma unroll
-    for (int f = 0; f < kMaxFeatures; ++f) xs[f] = f < w.F ? X[s * w.F + f] : 0.f;
+    for (int f = 0; f < kMaxFeatures; ++f) xs[f] = f < w.F ? X[row * w.F + f] : 0.f;
     float acc = b2;
     for (int j = 0; j < w.H; ++j) {
       float z = b1[j];
@@ -227,7 +229,7 @@ __global__ void mlp_forward_kernel(MlpWeights w, const float* __restrict__ X, in
     }
     if (y) y[s] = acc;
     if (t) {
-      const float r = acc - t[s];
+      const float r = acc - t[row];
       dy[s] = 2.0f * r / (float)B;
       sq[s] = r * r;
     }
@@ -238,9 +240,12 @@ __global__ void mlp_forward_kernel(MlpWeights w, const float* __restrict__ X, in
 // block reduces in a fixed order (deterministic):
 //   dW1[j][f] = sum_s dy_s w2_j GELU'(pre_sj) x_sf,  db1[j] = sum_s dy_s w2_j GELU'(pre_sj)
 //   dw2[j]    = sum_s dy_s GELU(pre_sj);  block H also forms db2 = sum_s dy_s and the loss.
-__global__ void mlp_backward_kernel(MlpWeights w, const float* __restrict__ X, int64_t B,
-                                    const float* __restrict__ pre, const float* __restrict__ dy,
-                                    const float* __restrict__ sq, float* __restrict__ grad, float* __restrict__ loss) {
+// `loss` receives the batch mean squared error, or has it added when
+// accumulate != 0.
+__global__ void mlp_backward_kernel(MlpWeights w, const float* __restrict__ X, const int64_t* __restrict__ idx,
+                                    int64_t B, const float* __restrict__ pre, const float* __restrict__ dy,
+                                    const float* __restrict__ sq, float* __restrict__ grad, float* __restrict__ loss,
+                                    int accumulate) {
   constexpr int kT = 256;
   __shared__ float red[kT];
   const int j = blockIdx.x;
@@ -255,18 +260,21 @@ __global__ void mlp_backward_kernel(MlpWeights w, const float* __restrict__ X, i
       const float z = pre[s * w.H + j];
       const float d = dy[s];
       const float dz = d * w2j * gelu_grad_f(z);
+      const int64_t row = idx ? idx[s] : s;
       gb1 += dz;
       gw2 = fmaf(d, gelu_f(z), gw2);
 #pragma unroll
       for (int f = 0; f < kMaxFeatures; ++f)
-        if (f < w.F) gW[f] = fmaf(dz, X[s * w.F + f], gW[f]);
+        if (f < w.F) gW[f] = fmaf(dz, X[row * w.F + f], gW[f]);
     }
     // fixed-order tree reductions: F entries of W1's row, then b1, then w2
     for (int f = 0; f < w.F + 2; ++f) {
-      float v = f < w.F ? 0.f : (f == w.F ? gb1 : gw2);
+      float v = f == w.F ? gb1 : gw2;
+      if (f < w.F) {
 #pragma unroll
-      for (int ff = 0; ff < kMaxFeatures; ++ff)
-        if (ff == f) v = gW[ff];
+        for (int ff = 0; ff < kMaxFeatures; ++ff)
+          if (ff == f) v = gW[ff];
+      }
       red[tid] = v;
       __syncthreads();
       for (int o = kT / 2; o > 0; o >>= 1) {
@@ -293,7 +301,7 @@ __global__ void mlp_backward_kernel(MlpWeights w, const float* __restrict__ X, i
       }
       if (tid == 0) {
         if (pass == 0) grad[w.H * w.F + 2 * w.H] = red[0];
-        else if (loss) loss[0] = red[0] / (float)B;
+        else if (loss) loss[0] = (accumulate ? loss[0] : 0.f) + red[0] / (float)B;
       }
       __syncthreads();
     }
@@ -322,20 +330,21 @@ __global__ void adamw_kernel(MlpWeights w, const float* __restrict__ grad, float
   }
 }
 
-cudaError_t launch_mlp_forward(const MlpWeights& w, const float* X, int64_t B, float* y, float* pre, const float* t,
-                               float* dy, float* sq, cudaStream_t st) {
+cudaError_t launch_mlp_forward(const MlpWeights& w, const float* X, const int64_t* idx, int64_t B, float* y, float* pre,
+                               const float* t, float* dy, float* sq, cudaStream_t st) {
   if (B <= 0) return cudaSuccess;
   const int threads = 128;
   int64_t blocks = (B + threads - 1) / threads;
   if (blocks > 152 * 16) blocks = 152 * 16;
   const size_t smem = (size_t)(w.H * w.F + 2 * w.H) * sizeof(float);
-  mlp_forward_kernel<<<(unsigned)blocks, threads, smem, st>>>(w, X, B, y, pre, t, dy, sq);
+  mlp_forward_kernel<<<(unsigned)blocks, threads, smem, st>>>(w, X, idx, B, y, pre, t, dy, sq);
   return cudaGetLastError();
 }
 
-cudaError_t launch_mlp_backward(const MlpWeights& w, const float* X, int64_t B, const float* pre, const float* dy,
-                                const float* sq, float* grad, float* loss, cudaStream_t st) {
-  mlp_backward_kernel<<<w.H + 1, 256, 0, st>>>(w, X, B, pre, dy, sq, grad, loss);
+cudaError_t launch_mlp_backward(const MlpWeights& w, const float* X, const int64_t* idx, int64_t B, const float* pre,
+                                const float* dy, const float* sq, float* grad, float* loss, int accumulate,
+                                cudaStream_t st) {
+  mlp_backward_kernel<<<w.H + 1, 256, 0, st>>>(w, X, idx, B, pre, dy, sq, grad, loss, accumulate);
   return cudaGetLastError();
 }
 
@@ -391,6 +400,40 @@ cudaError_t launch_prune(const int64_t* cand_win, const float* cand_score, const
   if (blocks > 152 * 32) blocks = 152 * 32;
   prune_kernel<<<(unsigned)blocks, 256, 0, st>>>(cand_win, cand_score, pred, n_reads, K, keep, out_win, out_score,
                                                   out_pred);
+  return cudaGetLastError();
+}
+
+}  // namespace rope
+
+namespace rope {
+
+__global__ void ld_fraction_kernel(const int32_t* __restrict__ ld, int64_t n, float inv_n, float* __restrict__ out) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = (float)ld[i] * inv_n;
+}
+
+cudaError_t launch_ld_fraction(const int32_t* ld, int64_t n, int N, float* out, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  int64_t blocks = (n + 255) / 256;
+  if (blocks > 152 * 32) blocks = 152 * 32;
+  ld_fraction_kernel<<<(unsigned)blocks, 256, 0, st>>>(ld, n, 1.0f / (float)N, out);
+  return cudaGetLastError();
+}
+
+// The fallback without a network: candidate c of every read is given the
+// "prediction" c, so pruning keeps the scan's own ranking.
+__global__ void rank_prediction_kernel(int64_t n_reads, int K, float* __restrict__ pred) {
+  const int64_t n = n_reads * K;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    pred[i] = (float)(i % K);
+}
+
+cudaError_t launch_rank_as_prediction(int64_t n_reads, int K, float* pred, cudaStream_t st) {
+  const int64_t n = n_reads * K;
+  if (n <= 0) return cudaSuccess;
+  int64_t blocks = (n + 255) / 256;
+  if (blocks > 152 * 32) blocks = 152 * 32;
+  rank_prediction_kernel<<<(unsigned)blocks, 256, 0, st>>>(n_reads, K, pred);
   return cudaGetLastError();
 }
 

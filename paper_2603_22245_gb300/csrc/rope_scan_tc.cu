@@ -2,22 +2,24 @@
 //
 // The fidelity of a read x against a window c is |<x|c>|^2 for normalised
 // vectors (§2.4); with x = xr + i xi and c = cr + i ci, Re<x|c> = xr.cr + xi.ci
-// and Im<x|c> = xr.ci - xi.cr (the real identity of §4). Per block:
-//   * A operand (tensor memory): NT tiles of 128 reads, each row the read's
-//     normalised [xr | xi] in BF16 (K = 2D), written once per work item by the
-//     epilogue warps with tcgen05.st.
-//   * B operand (shared memory, 128-byte swizzled K-major): per stage, T windows
-//     as 2T rows, row n = [cr | ci] and row T+n = [ci | -cr] of window n. The
-//     generator warps produce them: each chain of D/4 lanes runs the §3.4
-//     recurrence from an exact anchor through 64 consecutive windows and emits
-//     one window per stage, scaled by the stored 1/sqrt(C_j), rounded to BF16.
+// and Im<x|c> = xr.ci - xi.cr (the real identity of §4). Per block (one per SM):
+//   * A operand (shared memory, 128-byte swizzled K-major): NT tiles of 128
+//     reads, row = the read's normalised [xr | xi] in BF16 (K = 2D), written
+//     once per work item by the epilogue warps.
+//   * B operand (shared memory, same layout): per stage T windows as 2T rows,
+//     row n = [cr | ci] and row T+n = [ci | -cr] of window n. The generator
+//     warps produce them: each chain of 8 lanes runs the §3.4 recurrence from
+//     an exact anchor through 64 consecutive windows and emits one window per
+//     stage, scaled by the stored 1/sqrt(C_j) and rounded to BF16.
 //   * D (tensor memory): per stage and tile a 128 x 2T FP32 accumulator whose
-//     columns are Re (0..T-1) and Im (T..2T-1); STAGES stages in flight.
-//   * One thread issues tcgen05.mma (M=128, N=2T, K=16 steps) and commits to
-//     mbarriers; a producer warp streams the 2-bit packed reference, the
-//     window norms and the anchors of each super-tile into shared memory with
-//     bulk copies (TMA); epilogue warps (thread = read) load the accumulators
-//     with tcgen05.ld, form Re^2+Im^2, and keep the read's best windows.
+//     columns are Re (0..T-1) and Im (T..2T-1).
+//   * One thread issues tcgen05.mma (M = 128, N = 2T = 128, K = 16 per
+//     instruction; an MMA costs at least ~45 cycles whatever N is, so N = 128
+//     keeps the tensor pipe saturated) and commits to mbarriers; a producer
+//     warp streams the 2-bit packed reference and the window norms of each
+//     super-tile into shared memory with bulk copies (TMA); epilogue warps
+//     (thread = read) load the accumulators with tcgen05.ld in 16-column
+//     chunks, form Re^2 + Im^2 and keep the read's best windows.
 // Every wait is bounded; a wait that runs out sets the timeout status bit and
 // the block drains its in-flight copies and MMAs, frees tensor memory and exits.
 #include <cuda_bf16.h>
@@ -27,12 +29,13 @@
 
 namespace rope {
 
-template <int D_, int NT_, int T_, int STAGES_>
+template <int D_, int NT_, int T_, int STAGES_, int NB_>
 struct TcShape {
-  static constexpr int D = D_, NT = NT_, T = T_, STAGES = STAGES_;
+  static constexpr int D = D_, NT = NT_, T = T_, STAGES = STAGES_, NB = NB_;
   static constexpr int A = kAnchorPeriod;
-  static constexpr int LPC = D / 4;
-  static constexpr int CPW = 32 / LPC;
+  static constexpr int BPL = D / 8;              // complex entries per generator lane
+  static constexpr int LPC = 8;                  // lanes per chain
+  static constexpr int CPW = 32 / LPC;           // chains per warp
   static constexpr int GEN_WARPS = T / CPW;
   static constexpr int EPI_WARPS = 4 * NT;
   static constexpr int WARP_MMA = EPI_WARPS;
@@ -40,27 +43,28 @@ struct TcShape {
   static constexpr int WARP_GEN0 = EPI_WARPS + 2;
   static constexpr int NWARPS = EPI_WARPS + 2 + GEN_WARPS;
   static constexpr int NTHREADS = 32 * NWARPS;
-  static constexpr int SUP = T * A;              // windows per super-tile
-  static constexpr int GROUP = NT * 128;         // reads per work item
-  static constexpr int KSTEPS = 2 * D / 16;      // K = 2D in steps of 16
-  static constexpr int KBLK_BYTES = 2 * T * 128; // one 64-element K block of the B tile
-  static constexpr int B_SLOT_BYTES = 2 * T * 4 * D;
-  static constexpr int NB = 4;                   // B tiles in flight
-  static constexpr int A_COLS = NT * D;          // tensor-memory columns of the A operand
-  static constexpr int ACC0 = A_COLS;
+  static constexpr int SUP = T * A;                   // windows per super-tile
+  static constexpr int GROUP = NT * 128;              // reads per work item
+  static constexpr int KSTEPS = 2 * D / 16;           // K = 2D in steps of 16
+  static constexpr int KBLOCKS = 2 * D / 64;          // 64-element (128-byte) K blocks
+  static constexpr int A_KBLK_BYTES = 128 * 128;      // one K block of an A tile
+  static constexpr int A_TILE_BYTES = KBLOCKS * A_KBLK_BYTES;
+  static constexpr int B_KBLK_BYTES = 2 * T * 128;    // one K block of a B tile
+  static constexpr int B_SLOT_BYTES = KBLOCKS * B_KBLK_BYTES;
   static constexpr int TMEM_COLS = 512;
   static constexpr uint32_t IDESC = idesc_bf16_f32(128, 2 * T);
+  static_assert(D == 32 || D == 64, "complex dimension");
   static_assert(GEN_WARPS * CPW == T, "T must be a multiple of chains per warp");
-  static_assert(A_COLS + STAGES * NT * 2 * T <= TMEM_COLS, "tensor memory budget");
-  static_assert(B_SLOT_BYTES % 1024 == 0 && KBLK_BYTES % 1024 == 0, "swizzle atoms");
+  static_assert(STAGES * NT * 2 * T <= TMEM_COLS, "tensor memory budget");
+  static_assert(T % 16 == 0, "the epilogue loads 16-column chunks");
   static_assert((2 * T) % 16 == 0 && 2 * T <= 256, "MMA N");
-  static_assert(T == 8 || T % 16 == 0, "the epilogue loads 16-column chunks (or one for T = 8)");
+  static_assert(NTHREADS <= 1024, "block size");
 };
 
 struct TcLaunch {
   int32_t words_per_slot;  // packed words staged per super-tile (multiple of 4)
   int32_t st_slot_bytes;   // bytes of one super-tile data slot
-  int32_t bins_bytes;      // bytes of the per-chain bin arrays
+  int32_t bins_bytes;      // bytes of the per-chain bin arrays (stride 1)
 };
 
 __device__ __forceinline__ float fmax3(float a, float b, float c) {
@@ -69,9 +73,18 @@ __device__ __forceinline__ float fmax3(float a, float b, float c) {
   return d;
 }
 
+// bin of position p from the super-tile's staged words (word index relative to word0)
+__device__ __forceinline__ uint32_t bin_staged(const uint32_t* words, int64_t word0, int64_t p, int s,
+                                               const uint16_t* __restrict__ map_lsb) {
+  const int64_t wi = (p >> 4) - word0;
+  const uint64_t v = ((uint64_t)words[wi + 1] << 32) | words[wi];
+  const uint32_t field = (uint32_t)(v >> ((p & 15) * 2)) & ((1u << (2 * s)) - 1u);
+  return __ldg(map_lsb + field);
+}
+
 template <class Sh, bool kDense>
 __global__ void __launch_bounds__(Sh::NTHREADS, 1) scan_tc_kernel(DevIndex ix, ScanArgs a, TcLaunch L) {
-  constexpr int D = Sh::D, NT = Sh::NT, T = Sh::T, STAGES = Sh::STAGES, NB = Sh::NB, A = Sh::A;
+  constexpr int D = Sh::D, NT = Sh::NT, T = Sh::T, STAGES = Sh::STAGES, NB = Sh::NB, A = Sh::A, BPL = Sh::BPL;
   extern __shared__ __align__(1024) uint8_t tc_smem_raw[];
   __shared__ __align__(8) uint64_t bar_bfull[NB], bar_bempty[NB];
   __shared__ __align__(8) uint64_t bar_afull[STAGES], bar_aempty[STAGES];
@@ -80,9 +93,10 @@ __global__ void __launch_bounds__(Sh::NTHREADS, 1) scan_tc_kernel(DevIndex ix, S
   __shared__ uint32_t tmem_base_s;
   __shared__ int abort_s;
 
-  // dynamic shared memory: [B ring | 2 super-tile slots | chain bins | lists]
+  // dynamic shared memory: [A tiles | B ring | 2 super-tile slots | chain bins | lists]
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(tc_smem_raw) + 1023) & ~uintptr_t(1023));
-  uint8_t* b_ring = smem;
+  uint8_t* a_tiles = smem;
+  uint8_t* b_ring = a_tiles + NT * Sh::A_TILE_BYTES;
   uint8_t* st_slots = b_ring + NB * Sh::B_SLOT_BYTES;
   uint8_t* chain_bins = st_slots + 2 * L.st_slot_bytes;
   float* list_s = reinterpret_cast<float*>(chain_bins + L.bins_bytes);
@@ -120,22 +134,21 @@ __global__ void __launch_bounds__(Sh::NTHREADS, 1) scan_tc_kernel(DevIndex ix, S
   __syncthreads();
   tc_fence_after();
   const uint32_t tbase = tmem_base_s;
-
   const int n_items = a.n_groups * a.n_ranges;
-  const int64_t words_total_needed = (int64_t)L.words_per_slot;  // staged per super-tile
-  (void)words_total_needed;
 
   if (warp < Sh::EPI_WARPS) {
     // ================================================================ epilogue
     const int q = warp & 3;
     const int tile = warp >> 2;
-    const int rs = tile * 128 + 32 * q + lane;  // read slot within the group
+    const int rs = tile * 128 + 32 * q + lane;  // read slot in the group
+    const int arow = 32 * q + lane;             // its row in the A tile
     ThreadList lst;
     lst.s = list_s + rs;
     lst.w = list_w + rs;
     lst.stride = Sh::GROUP;
     lst.depth = a.cand_depth;
     const uint32_t lane_base = (uint32_t)(32 * q) << 16;
+    uint8_t* arow_base = a_tiles + tile * Sh::A_TILE_BYTES;
     uint32_t gs = 0;
     for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
       const int grp = item % a.n_groups;
@@ -146,20 +159,19 @@ __global__ void __launch_bounds__(Sh::NTHREADS, 1) scan_tc_kernel(DevIndex ix, S
       const int64_t j_lo = max(st_begin, a.jb);
       const int64_t j_hi = min(st_begin + a.range_len, a.je);
       const int64_t n_st = (j_hi - st_begin + Sh::SUP - 1) / Sh::SUP;
-      // A operand: this read's normalised BF16 row into tensor memory
+      // A operand: this read's normalised BF16 row, 16-byte chunks into the
+      // swizzled tile. The previous item's MMAs have all completed: this
+      // thread consumed every accumulator they wrote.
       {
         const uint4* src = reinterpret_cast<const uint4*>(a.emb_bf16 + (have_read ? r : 0) * 2 * D);
 #pragma unroll
-        for (int c8 = 0; c8 < D / 8; ++c8) {
-          uint32_t v[8];
-          const uint4 lo = have_read ? __ldg(src + 2 * c8) : make_uint4(0, 0, 0, 0);
-          const uint4 hi = have_read ? __ldg(src + 2 * c8 + 1) : make_uint4(0, 0, 0, 0);
-          v[0] = lo.x; v[1] = lo.y; v[2] = lo.z; v[3] = lo.w;
-          v[4] = hi.x; v[5] = hi.y; v[6] = hi.z; v[7] = hi.w;
-          tmem_st8(tbase + lane_base + (uint32_t)(tile * D + 8 * c8), v);
+        for (int c = 0; c < 2 * D / 8; ++c) {
+          const uint4 v = have_read ? __ldg(src + c) : make_uint4(0, 0, 0, 0);
+          const int kb = c >> 3;
+          *reinterpret_cast<uint4*>(arow_base + kb * Sh::A_KBLK_BYTES +
+                                    sw128_offset((uint32_t)arow, (uint32_t)((c & 7) * 16))) = v;
         }
-        tc_wait_st();
-        tc_fence_before();
+        fence_proxy_async_smem();
         __syncwarp();
         if (lane == 0) mbar_arrive(&bar_aready);
       }
@@ -170,66 +182,58 @@ __global__ void __launch_bounds__(Sh::NTHREADS, 1) scan_tc_kernel(DevIndex ix, S
           const uint32_t s = gs % STAGES;
           if (!mbar_wait_warp(&bar_afull[s], (gs / STAGES) & 1, abort_flag, a.status)) goto epi_done;
           tc_fence_after();
-          const uint32_t col = (uint32_t)(Sh::ACC0 + ((int)s * NT + tile) * 2 * T);
+          const uint32_t col = (uint32_t)(((int)s * NT + tile) * 2 * T);
           const int64_t jbase = st + i;  // column n holds window jbase + n*A
-          float mx = -INFINITY;
-          float sc[T];
-          if constexpr (T == 8) {
-            // one 16-column load holds Re (columns 0..7) and Im (8..15)
-            uint32_t v[16];
-            tmem_ld16(tbase + lane_base + col, v);
-            tc_wait_ld();
+          const bool full = jbase >= j_lo && jbase + (int64_t)(T - 1) * A < j_hi;
 #pragma unroll
-            for (int n = 0; n < 8; ++n) {
-              const float re = __uint_as_float(v[n]);
-              const float im = __uint_as_float(v[8 + n]);
+          for (int c0 = 0; c0 < T; c0 += 16) {
+            uint32_t vr[16], vi[16];
+            tmem_ld16(tbase + lane_base + col + c0, vr);
+            tmem_ld16(tbase + lane_base + col + T + c0, vi);
+            tc_wait_ld();
+            if (c0 + 16 == T) {
+              // the last chunk is in registers: hand the accumulator back
+              tc_fence_before();
+              __syncwarp();
+              if (lane == 0) mbar_arrive(&bar_aempty[s]);
+            }
+            float sc[16];
+#pragma unroll
+            for (int n = 0; n < 16; ++n) {
+              const float re = __uint_as_float(vr[n]);
+              const float im = __uint_as_float(vi[n]);
               sc[n] = fmaf(re, re, im * im);
             }
-          } else {
+            const int64_t jc = jbase + (int64_t)c0 * A;
+            if (kDense) {
+              if (have_read) {
 #pragma unroll
-            for (int c0 = 0; c0 < T; c0 += 16) {
-              uint32_t vr[16], vi[16];
-              tmem_ld16(tbase + lane_base + col + c0, vr);
-              tmem_ld16(tbase + lane_base + col + T + c0, vi);
-              tc_wait_ld();
-#pragma unroll
-              for (int n = 0; n < 16; ++n) {
-                const float re = __uint_as_float(vr[n]);
-                const float im = __uint_as_float(vi[n]);
-                sc[c0 + n] = fmaf(re, re, im * im);
+                for (int n = 0; n < 16; ++n) {
+                  const int64_t j = jc + (int64_t)n * A;
+                  if (j >= j_lo && j < j_hi) a.dense[r * (a.je - a.jb) + (j - a.jb)] = sc[n];
+                }
               }
-            }
-          }
-          tc_fence_before();
-          __syncwarp();
-          if (lane == 0) mbar_arrive(&bar_aempty[s]);
-          const bool full = jbase >= j_lo && jbase + (int64_t)(T - 1) * A < j_hi;
-          if (kDense) {
-            if (have_read) {
-#pragma unroll
-              for (int n = 0; n < T; ++n) {
-                const int64_t j = jbase + (int64_t)n * A;
-                if (j >= j_lo && j < j_hi) a.dense[r * (a.je - a.jb) + (j - a.jb)] = sc[n];
-              }
-            }
-          } else {
-            if (full) {
-              mx = sc[0];
-#pragma unroll
-              for (int n = 1; n + 1 < T; n += 2) mx = fmax3(mx, sc[n], sc[n + 1]);
-              if ((T & 1) == 0) mx = fmaxf(mx, sc[T - 1]);
             } else {
+              float mx;
+              if (full) {
+                mx = fmax3(sc[0], sc[1], sc[2]);
 #pragma unroll
-              for (int n = 0; n < T; ++n) {
-                const int64_t j = jbase + (int64_t)n * A;
-                if (j >= j_lo && j < j_hi) mx = fmaxf(mx, sc[n]);
+                for (int n = 3; n + 1 < 16; n += 2) mx = fmax3(mx, sc[n], sc[n + 1]);
+                mx = fmaxf(mx, sc[15]);
+              } else {
+                mx = -INFINITY;
+#pragma unroll
+                for (int n = 0; n < 16; ++n) {
+                  const int64_t j = jc + (int64_t)n * A;
+                  if (j >= j_lo && j < j_hi) mx = fmaxf(mx, sc[n]);
+                }
               }
-            }
-            if (have_read && mx >= lst.thr) {
+              if (have_read && mx >= lst.thr) {
 #pragma unroll
-              for (int n = 0; n < T; ++n) {
-                const int64_t j = jbase + (int64_t)n * A;
-                if (j >= j_lo && j < j_hi && sc[n] >= lst.thr) lst.insert(sc[n], (uint32_t)j, a.sep, S);
+                for (int n = 0; n < 16; ++n) {
+                  const int64_t j = jc + (int64_t)n * A;
+                  if (j >= j_lo && j < j_hi && sc[n] >= lst.thr) lst.insert(sc[n], (uint32_t)j, a.sep, S);
+                }
               }
             }
           }
@@ -246,6 +250,7 @@ __global__ void __launch_bounds__(Sh::NTHREADS, 1) scan_tc_kernel(DevIndex ix, S
     if (lane == 0) {
       uint32_t gs = 0, gb = 0, it = 0;
       bool ok = true;
+      const uint64_t a_desc0 = smem_desc_sw128(smem_u32(a_tiles));
       const uint64_t b_desc0 = smem_desc_sw128(smem_u32(b_ring));
       for (int item = blockIdx.x; item < n_items && ok; item += gridDim.x, ++it) {
         const int rng = item / a.n_groups;
@@ -253,22 +258,24 @@ __global__ void __launch_bounds__(Sh::NTHREADS, 1) scan_tc_kernel(DevIndex ix, S
         const int64_t j_hi = min(st_begin + a.range_len, a.je);
         const int64_t n_stage = (j_hi - st_begin + Sh::SUP - 1) / Sh::SUP * A;
         if (!mbar_wait(&bar_aready, it & 1, abort_flag, a.status)) break;
-        tc_fence_after();
         for (int64_t k = 0; k < n_stage; ++k, ++gs, ++gb) {
           const uint32_t slot = gb % NB;
           const uint32_t s = gs % STAGES;
           if (!mbar_wait(&bar_bfull[slot], (gb / NB) & 1, abort_flag, a.status)) { ok = false; break; }
           if (!mbar_wait(&bar_aempty[s], ((gs / STAGES) & 1) ^ 1, abort_flag, a.status)) { ok = false; break; }
           tc_fence_after();
-          // descriptors differ between B slots only in the start-address field
+          // descriptors differ only in the start-address field (16-byte units)
           const uint64_t slot_desc = b_desc0 + (uint64_t)((slot * Sh::B_SLOT_BYTES) >> 4);
 #pragma unroll
           for (int t = 0; t < NT; ++t) {
-            const uint32_t d_tmem = tbase + (uint32_t)(Sh::ACC0 + ((int)s * NT + t) * 2 * T);
+            const uint32_t d_tmem = tbase + (uint32_t)(((int)s * NT + t) * 2 * T);
+            const uint64_t tile_desc = a_desc0 + (uint64_t)((t * Sh::A_TILE_BYTES) >> 4);
 #pragma unroll
             for (int kk = 0; kk < Sh::KSTEPS; ++kk) {
-              const uint64_t bdesc = slot_desc + (uint64_t)((((kk >> 2) * Sh::KBLK_BYTES) + (kk & 3) * 32) >> 4);
-              tc_mma_ts(d_tmem, tbase + (uint32_t)(t * D + 8 * kk), bdesc, Sh::IDESC, kk > 0 ? 1u : 0u);
+              const uint32_t kb = kk >> 2, ko = (kk & 3) * 32;
+              const uint64_t ad = tile_desc + (uint64_t)((kb * Sh::A_KBLK_BYTES + ko) >> 4);
+              const uint64_t bd = slot_desc + (uint64_t)((kb * Sh::B_KBLK_BYTES + ko) >> 4);
+              tc_mma_ss(d_tmem, ad, bd, Sh::IDESC, kk > 0 ? 1u : 0u);
             }
           }
           tc_commit(&bar_bempty[slot]);
@@ -297,36 +304,32 @@ __global__ void __launch_bounds__(Sh::NTHREADS, 1) scan_tc_kernel(DevIndex ix, S
           const int64_t word0 = ((st * S) >> 4) & ~int64_t(3);
           const uint32_t wbytes = (uint32_t)L.words_per_slot * 4u;
           const uint32_t nbytes = (uint32_t)Sh::SUP * 4u;
-          const uint32_t abytes = (uint32_t)(T * D) * 8u;
-          mbar_expect_tx(&bar_stfull[slot], wbytes + nbytes + abytes);
+          mbar_expect_tx(&bar_stfull[slot], wbytes + nbytes);
           bulk_g2s(dst, ix.packed + word0, wbytes, &bar_stfull[slot]);
           bulk_g2s(dst + wbytes, ix.inv_norm + st, nbytes, &bar_stfull[slot]);
-          bulk_g2s(dst + wbytes + nbytes, ix.anchors + (st / A) * D, abytes, &bar_stfull[slot]);
         }
         if (!ok) break;
       }
       // wait for the copies still in flight into either slot (the latest phase of each)
-      for (uint32_t h = (g >= 2 ? g - 2 : 0); h < g; ++h) mbar_wait(&bar_stfull[h & 1], (h >> 1) & 1, abort_flag, a.status);
+      for (uint32_t h = (g >= 2 ? g - 2 : 0); h < g; ++h)
+        mbar_wait(&bar_stfull[h & 1], (h >> 1) & 1, abort_flag, a.status);
     }
   } else {
     // ================================================================ window generators
     const int gw = warp - Sh::WARP_GEN0;
-    const int chain = gw * Sh::CPW + lane / Sh::LPC;  // = B row (Re) and column
+    const int chain = gw * Sh::CPW + lane / Sh::LPC;  // B row (Re) and column of its windows
     const int lic = lane % Sh::LPC;
-    const int chain_lane0 = (lane / Sh::LPC) * Sh::LPC;
-    const unsigned chain_mask = (Sh::LPC == 32) ? 0xffffffffu : (((1u << Sh::LPC) - 1u) << chain_lane0);
-    (void)chain_mask;
-    uint8_t* bins_out = chain_bins + (size_t)chain * 2 * A * S;
-    uint8_t* bins_in = bins_out + A * S;
-    Chain<D> ch;
+    uint8_t* bins_out = chain_bins + (size_t)chain * 2 * A;
+    uint8_t* bins_in = bins_out + A;
+    ChainB<BPL> ch;
     ch.setup(ix, lic);
-    // byte offsets of this lane's four 8-byte pieces in a B slot:
-    //   row chain: [cr | ci], row T+chain: [ci | -cr]
+    // byte offsets of this lane's pieces in a B slot: row chain = [cr | ci],
+    // row T+chain = [ci | -cr]; BPL bf16 (2*BPL bytes) each
     uint32_t off_re_cr, off_re_ci, off_im_ci, off_im_cr;
     {
-      const int e_lo = 4 * lic, e_hi = D + 4 * lic;
+      const int e_lo = BPL * lic, e_hi = D + BPL * lic;
       auto off = [&](int row, int e) -> uint32_t {
-        return (uint32_t)((e >> 6) * Sh::KBLK_BYTES) + sw128_offset((uint32_t)row, (uint32_t)((e & 63) * 2));
+        return (uint32_t)((e >> 6) * Sh::B_KBLK_BYTES) + sw128_offset((uint32_t)row, (uint32_t)((e & 63) * 2));
       };
       off_re_cr = off(chain, e_lo);
       off_re_ci = off(chain, e_hi);
@@ -334,7 +337,6 @@ __global__ void __launch_bounds__(Sh::NTHREADS, 1) scan_tc_kernel(DevIndex ix, S
       off_im_cr = off(T + chain, e_hi);
     }
     uint32_t g = 0, gb = 0;
-    const int span = A * S;
     for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
       const int rng = item / a.n_groups;
       const int64_t st_begin = a.st0 + (int64_t)rng * a.range_len;
@@ -347,19 +349,17 @@ __global__ void __launch_bounds__(Sh::NTHREADS, 1) scan_tc_kernel(DevIndex ix, S
         const uint8_t* src = st_slots + slot * L.st_slot_bytes;
         const uint32_t* words = reinterpret_cast<const uint32_t*>(src);
         const float* inv = reinterpret_cast<const float*>(src + (size_t)L.words_per_slot * 4);
-        const float2* anc = reinterpret_cast<const float2*>(src + (size_t)L.words_per_slot * 4 + Sh::SUP * 4);
         const int64_t word0 = ((st * S) >> 4) & ~int64_t(3);
-        // bins of this chain's leaving and entering locations
+        const int64_t a_idx = st / A + chain;  // this chain's anchor (padded past the last window)
         const int64_t p_out0 = (st + (int64_t)chain * A) * S;
         const int64_t p_in0 = p_out0 + ix.N - ix.s + 1;
-        for (int u = lic; u < 2 * span; u += Sh::LPC) {
-          const int64_t p = (u < span ? p_out0 + u : p_in0 + (u - span));
-          const int64_t wi = (p >> 4) - word0;
-          const uint64_t v = ((uint64_t)words[wi + 1] << 32) | words[wi];
-          const uint32_t field = (uint32_t)(v >> ((p & 15) * 2)) & ((1u << (2 * ix.s)) - 1u);
-          bins_out[u] = (uint8_t)__ldg(ix.map_lsb + field);
+        if (S == 1) {
+          for (int u = lic; u < 2 * A; u += Sh::LPC) {
+            const int64_t p = u < A ? p_out0 + u : p_in0 + (u - A);
+            bins_out[u] = (uint8_t)bin_staged(words, word0, p, ix.s, ix.map_lsb);
+          }
         }
-        ch.load(anc + chain * D, lic);
+        ch.load(ix.anchors + a_idx * D, lic);
         __syncwarp();
         for (int i = 0; i < A; ++i, ++gb) {
           const uint32_t bslot = gb % NB;
@@ -367,21 +367,26 @@ __global__ void __launch_bounds__(Sh::NTHREADS, 1) scan_tc_kernel(DevIndex ix, S
           if (!mbar_wait_warp(&bar_bempty[bslot], ((gb / NB) & 1) ^ 1, abort_flag, a.status)) goto gen_done;
           {
             uint8_t* bt = b_ring + bslot * Sh::B_SLOT_BYTES;
-            const __nv_bfloat162 r01 = __floats2bfloat162_rn(ch.cr[0] * nv, ch.cr[1] * nv);
-            const __nv_bfloat162 r23 = __floats2bfloat162_rn(ch.cr[2] * nv, ch.cr[3] * nv);
-            const __nv_bfloat162 i01 = __floats2bfloat162_rn(ch.ci[0] * nv, ch.ci[1] * nv);
-            const __nv_bfloat162 i23 = __floats2bfloat162_rn(ch.ci[2] * nv, ch.ci[3] * nv);
-            uint2 cr2, ci2, ncr2;
-            cr2.x = *reinterpret_cast<const uint32_t*>(&r01);
-            cr2.y = *reinterpret_cast<const uint32_t*>(&r23);
-            ci2.x = *reinterpret_cast<const uint32_t*>(&i01);
-            ci2.y = *reinterpret_cast<const uint32_t*>(&i23);
-            ncr2.x = cr2.x ^ 0x80008000u;
-            ncr2.y = cr2.y ^ 0x80008000u;
-            *reinterpret_cast<uint2*>(bt + off_re_cr) = cr2;
-            *reinterpret_cast<uint2*>(bt + off_re_ci) = ci2;
-            *reinterpret_cast<uint2*>(bt + off_im_ci) = ci2;
-            *reinterpret_cast<uint2*>(bt + off_im_cr) = ncr2;
+            uint32_t pr[BPL / 2], pi[BPL / 2], pn[BPL / 2];
+#pragma unroll
+            for (int h = 0; h < BPL / 2; ++h) {
+              const __nv_bfloat162 rr = __floats2bfloat162_rn(ch.cr[2 * h] * nv, ch.cr[2 * h + 1] * nv);
+              const __nv_bfloat162 ii = __floats2bfloat162_rn(ch.ci[2 * h] * nv, ch.ci[2 * h + 1] * nv);
+              pr[h] = *reinterpret_cast<const uint32_t*>(&rr);
+              pi[h] = *reinterpret_cast<const uint32_t*>(&ii);
+              pn[h] = pr[h] ^ 0x80008000u;
+            }
+            if constexpr (BPL == 4) {
+              *reinterpret_cast<uint2*>(bt + off_re_cr) = make_uint2(pr[0], pr[1]);
+              *reinterpret_cast<uint2*>(bt + off_re_ci) = make_uint2(pi[0], pi[1]);
+              *reinterpret_cast<uint2*>(bt + off_im_ci) = make_uint2(pi[0], pi[1]);
+              *reinterpret_cast<uint2*>(bt + off_im_cr) = make_uint2(pn[0], pn[1]);
+            } else {
+              *reinterpret_cast<uint4*>(bt + off_re_cr) = make_uint4(pr[0], pr[1], pr[2], pr[3]);
+              *reinterpret_cast<uint4*>(bt + off_re_ci) = make_uint4(pi[0], pi[1], pi[2], pi[3]);
+              *reinterpret_cast<uint4*>(bt + off_im_ci) = make_uint4(pi[0], pi[1], pi[2], pi[3]);
+              *reinterpret_cast<uint4*>(bt + off_im_cr) = make_uint4(pn[0], pn[1], pn[2], pn[3]);
+            }
           }
           fence_proxy_async_smem();
           __syncwarp();
@@ -390,9 +395,11 @@ __global__ void __launch_bounds__(Sh::NTHREADS, 1) scan_tc_kernel(DevIndex ix, S
           if (S == 1) {
             ch.step1(bins_out[i], bins_in[i]);
           } else {
+            const int64_t po = p_out0 + (int64_t)i * S;
             for (int u = 0; u < S; ++u) {
-              ch.sub_at(bins_out[i * S + u], ix.eout[ch.band * S + u]);
-              ch.add_at(bins_in[i * S + u], ix.ein[ch.band * S + u]);
+              ch.sub_at(bin_staged(words, word0, po + u, ix.s, ix.map_lsb), ix.eout[ch.band * S + u]);
+              ch.add_at(bin_staged(words, word0, po + ix.N - ix.s + 1 + u, ix.s, ix.map_lsb),
+                        ix.ein[ch.band * S + u]);
             }
             ch.rotate();
           }
@@ -415,30 +422,38 @@ __global__ void __launch_bounds__(Sh::NTHREADS, 1) scan_tc_kernel(DevIndex ix, S
 
 // ---------------------------------------------------------------- configurations
 
-using TcShape32 = TcShape<32, 4, 16, 3>;  // d = 64:  512 reads x 16 windows per stage
-using TcShape64 = TcShape<64, 4, 8, 4>;   // d = 128: 512 reads x 8 windows per stage
+using TcShape32 = TcShape<32, 2, 64, 2, 4>;  // d = 64:  256 reads x 64 windows per stage, MMA N = 128
+using TcShape64 = TcShape<64, 2, 64, 2, 2>;  // d = 128: 256 reads x 64 windows per stage, MMA N = 128
 
 int scan_tc_supported(int D) { return D == 32 || D == 64; }
 
-int64_t scan_tc_super_tile(int D) {
-  return D == 32 ? TcShape32::SUP : D == 64 ? TcShape64::SUP : 0;
-}
+int64_t scan_tc_super_tile(int D) { return D == 32 ? TcShape32::SUP : D == 64 ? TcShape64::SUP : 0; }
 
 int scan_tc_group(int D) { return D == 32 ? TcShape32::GROUP : D == 64 ? TcShape64::GROUP : 0; }
 
-template <class Sh, bool kDense>
-static cudaError_t launch_tc(const DevIndex& ix, const ScanArgs& a, int num_sms, cudaStream_t st) {
+int scan_tc_max_stride() { return 8; }
+
+template <class Sh>
+static size_t tc_smem_bytes(const DevIndex& ix, int cand_depth, bool dense, TcLaunch* Lout) {
   TcLaunch L;
   const int S = ix.stride;
   int64_t words = ((int64_t)Sh::SUP * S + ix.N + 64) / 16 + 8;
   words = (words + 3) & ~int64_t(3);
   L.words_per_slot = (int32_t)words;
-  int64_t slot = words * 4 + (int64_t)Sh::SUP * 4 + (int64_t)Sh::T * Sh::D * 8;
+  int64_t slot = words * 4 + (int64_t)Sh::SUP * 4;
   slot = (slot + 127) & ~int64_t(127);
   L.st_slot_bytes = (int32_t)slot;
-  L.bins_bytes = (int32_t)(((int64_t)Sh::T * 2 * Sh::A * S + 127) & ~int64_t(127));
-  const size_t lists = kDense ? 0 : (size_t)a.cand_depth * Sh::GROUP * 8;
-  const size_t smem = 1024 + (size_t)Sh::NB * Sh::B_SLOT_BYTES + 2 * (size_t)L.st_slot_bytes + L.bins_bytes + lists;
+  L.bins_bytes = S == 1 ? (int32_t)(Sh::T * 2 * Sh::A) : 0;
+  const size_t lists = dense ? 0 : (size_t)cand_depth * Sh::GROUP * 8;
+  if (Lout) *Lout = L;
+  return 1024 + (size_t)Sh::NT * Sh::A_TILE_BYTES + (size_t)Sh::NB * Sh::B_SLOT_BYTES + 2 * (size_t)L.st_slot_bytes +
+         L.bins_bytes + lists;
+}
+
+template <class Sh, bool kDense>
+static cudaError_t launch_tc(const DevIndex& ix, const ScanArgs& a, int num_sms, cudaStream_t st) {
+  TcLaunch L;
+  const size_t smem = tc_smem_bytes<Sh>(ix, a.cand_depth, kDense, &L);
   if (smem > 227 * 1024) return cudaErrorInvalidValue;
   auto kern = scan_tc_kernel<Sh, kDense>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -451,9 +466,11 @@ static cudaError_t launch_tc(const DevIndex& ix, const ScanArgs& a, int num_sms,
 }
 
 cudaError_t launch_scan_tc(const DevIndex& ix, const ScanArgs& a, bool dense, int num_sms, cudaStream_t st) {
-  if (ix.stride > 16) return cudaErrorInvalidValue;
-  if (ix.D == 32) return dense ? launch_tc<TcShape32, true>(ix, a, num_sms, st) : launch_tc<TcShape32, false>(ix, a, num_sms, st);
-  if (ix.D == 64) return dense ? launch_tc<TcShape64, true>(ix, a, num_sms, st) : launch_tc<TcShape64, false>(ix, a, num_sms, st);
+  if (ix.stride > scan_tc_max_stride()) return cudaErrorInvalidValue;
+  if (ix.D == 32)
+    return dense ? launch_tc<TcShape32, true>(ix, a, num_sms, st) : launch_tc<TcShape32, false>(ix, a, num_sms, st);
+  if (ix.D == 64)
+    return dense ? launch_tc<TcShape64, true>(ix, a, num_sms, st) : launch_tc<TcShape64, false>(ix, a, num_sms, st);
   return cudaErrorInvalidValue;
 }
 

@@ -61,6 +61,19 @@ EXPORTS = {
     "rope_score_topk_noalloc": ([_P, _P, _P, _P, _I64, _P, _P, _P, _P], ctypes.c_int),
     "rope_score_dense": ([_P, _P, _P, _P, _I64, _I32, _I64, _I64, _P, _P], ctypes.c_int),
     "rope_map": ([_P, _P, _P, _I64, _P, _P, _P, _P], ctypes.c_int),
+    "rope_reranker_create": ([_I32, _I32, ctypes.c_uint64, _P], ctypes.c_int),
+    "rope_reranker_free": ([_P], None),
+    "rope_reranker_get": ([_P, _P, _P], ctypes.c_int),
+    "rope_reranker_set": ([_P, _P, _I32], ctypes.c_int),
+    "rope_reranker_grad": ([_P, _P, _P, _P, _I64, _P, _P, _P], ctypes.c_int),
+    "rope_reranker_train_step": ([_P, _P, _P, _P, _I64, ctypes.c_float, ctypes.c_float, _P, _P], ctypes.c_int),
+    "rope_reranker_predict": ([_P, _P, _I64, _P, _P], ctypes.c_int),
+    "rope_reranker_save": ([_P, ctypes.c_char_p], ctypes.c_int),
+    "rope_reranker_load": ([_P, ctypes.c_char_p], ctypes.c_int),
+    "rope_levenshtein": ([_P, _P, _P, _P, _P, _I64, _P, _P, _P], ctypes.c_int),
+    "rope_rerank_features": ([_P, _P, _P, _P, _P, _I64, _I32, _P, _P], ctypes.c_int),
+    "rope_rerank_prune": ([_P, _P, _P, _I64, _I32, _I32, _P, _P, _P, _P], ctypes.c_int),
+    "rope_map_rerank": ([_P, _P, _P, _I64, _P, _P, _I32, _P, _P, _P, _P], ctypes.c_int),
     "rope_merge_shards_host": ([_P, _P, _I32, _I64, _I32, _I32, _I32, _P, _P], ctypes.c_int),
     "rope_profile_enable": ([_I32], ctypes.c_int),
     "rope_profile_read": ([_P, _I32, _P], ctypes.c_int),

@@ -119,6 +119,30 @@ def reads(ref: np.ndarray, n: int, seed: int, length: int = 150, sub_rate: float
     return Reads(seqs[:w].copy(), offsets, tp, ts, ne, ln)
 
 
+def concat(parts: list[Reads]) -> Reads:
+    seqs = np.concatenate([p.seqs for p in parts]) if parts else np.empty(0, np.uint8)
+    offs = [0]
+    for p in parts:
+        offs.extend((p.offsets[1:] + offs[-1]).tolist())
+    cat = lambda f, dt: np.concatenate([getattr(p, f) for p in parts]).astype(dt)
+    return Reads(seqs, np.array(offs, dtype=np.int64), cat("true_pos", np.int64), cat("true_span", np.int32),
+                 cat("n_edits", np.int32), cat("lengths", np.int32))
+
+
+def reads_mixed_error(ref: np.ndarray, n: int, seed: int, max_rate: float = 0.15, groups: int = 10,
+                      length: int = 150, sub_share: float = 2.0 / 3.0) -> Reads:
+    """Reads whose error rates spread uniformly over [0, max_rate] (group g at
+    rate max_rate*(g+0.5)/groups), split sub_share : 1-sub_share between
+    substitutions and indel events (2:1 is the mix of 1% / 0.5%)."""
+    parts = []
+    for g in range(groups):
+        e = max_rate * (g + 0.5) / groups
+        cnt = n // groups + (1 if g < n % groups else 0)
+        parts.append(reads(ref, cnt, seed=seed + 7919 * g, length=length, sub_rate=sub_share * e,
+                           indel_rate=(1 - sub_share) * e))
+    return concat(parts)
+
+
 # Workload recipes. Sizes follow the five configurations the benchmark and the
 # parity tests use; "reads" gives (count, length, sub, indel, seed).
 WORKLOADS = {
