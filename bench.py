@@ -51,6 +51,19 @@ WORKLOADS = {
         L=100_000_000, gc=0.41, tandem=0.025, segdup=0.025, inter=0.0, ref_seed=3,
         n_reads=1_000_000, read_len=150, sub=0.01, indel=0.005, read_seed=4,
         s=4, m=2, t=2, variant=1, N=150, stride=1, k=8),
+    "markov10M_lognormal": dict(
+        desc="10 Mbp order-2 Markov reference (GC 41%, 2.5% tandem repeats, 2.5% segmental duplicates), 200k "
+             "planted reads of lognormal length (median 2 kbp, sigma 0.7, clipped to 100-10000), 8% errors (3.2% "
+             "sub, 4.8% indel geom p=0.7), d=64 (s=4 m=2 t=2 fine-tuned), stride 8, length ladder "
+             "floor(100*2^(j/8)) <= 10 kbp (54 window lengths; each read mapped by its longest fitting head), top-8",
+        L=10_000_000, gc=0.41, tandem=0.025, segdup=0.025, inter=0.0, ref_seed=5,
+        n_reads=200_000, read_len=2000, sigma=0.7, len_min=100, len_max=10000, sub=0.032, indel=0.048,
+        read_seed=6, s=4, m=2, t=2, variant=1, N=100, stride=8, k=8, ladder=(100, 10000, 8)),
+    "markov10M_lognormal_d128": dict(
+        desc="as markov10M_lognormal with d=128 (s=4 m=4 t=2 fine-tuned)",
+        L=10_000_000, gc=0.41, tandem=0.025, segdup=0.025, inter=0.0, ref_seed=5,
+        n_reads=200_000, read_len=2000, sigma=0.7, len_min=100, len_max=10000, sub=0.032, indel=0.048,
+        read_seed=6, s=4, m=4, t=2, variant=1, N=100, stride=8, k=8, ladder=(100, 10000, 8)),
     "uniform100k": dict(
         desc="100 kbp uniform reference, 256 x 150 bp planted reads (1% sub, 0.5% indel), d=64, stride 1, top-8",
         L=100_000, gc=None, ref_seed=1, n_reads=256, read_len=150, sub=0.01, indel=0.005, read_seed=2,
@@ -84,7 +97,8 @@ def make_inputs(wl, rank):
     else:
         ref = synth.markov_ref(wl["L"], wl["gc"], wl["ref_seed"], wl["tandem"], wl["segdup"], wl["inter"])
     rd = synth.reads(ref, wl["n_reads"], seed=wl["read_seed"] + 1000 * rank, length=wl["read_len"],
-                     sub_rate=wl["sub"], indel_rate=wl["indel"])
+                     sub_rate=wl["sub"], indel_rate=wl["indel"], lognormal_sigma=wl.get("sigma"),
+                     len_min=wl.get("len_min", 100), len_max=wl.get("len_max", 10000))
     return ref, rd
 
 
@@ -256,11 +270,106 @@ def run_reference(args, wl):
     print(json.dumps(line), flush=True)
 
 
+def run_ladder(args, wl):
+    """Reads of many lengths through the length ladder: a step maps the whole
+    read set (every read against every window of its bucket's index)."""
+    import torch
+
+    ws, rank, local = dist_setup(args)
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+    from paper_2603_22245_gb300 import rotormap as rm
+
+    rm.load()
+    ref, rd = make_inputs(wl, rank)
+    p = rm.Params(s=wl["s"], m=wl["m"], t=wl["t"], variant=wl["variant"], window_len=wl["N"], stride=wl["stride"])
+    dref = torch.from_numpy(ref).cuda()
+    t0 = time.perf_counter()
+    lad = rm.rope_ladder_create(p, dref, *wl["ladder"])
+    torch.cuda.synchronize()
+    index_s = time.perf_counter() - t0
+    del dref
+    seqs = torch.from_numpy(rd.seqs).cuda()
+    offs = torch.from_numpy(rd.offsets).cuda()
+    n, k = rd.n, wl["k"]
+    outs = [(torch.empty((n, k), dtype=torch.int64, device="cuda"), torch.empty((n, k), dtype=torch.float32,
+                                                                              device="cuda"),
+             torch.empty((n,), dtype=torch.int32, device="cuda")) for _ in range(2)]
+    for i in range(args.warmup):
+        rm.rope_ladder_map(lad, seqs, offs, k=k, out=outs[i % 2])
+    rm.rope_sync_status()
+    used = outs[0][2].cpu().numpy()
+    lens = np.array(lad.lengths)
+    W_of = {N: (len(ref) - N) // wl["stride"] + 1 for N in lad.lengths}
+    scores_step = int(sum(W_of[int(N)] for N in used[used > 0]))
+    rm.rope_profile_enable(args.steps)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clk = Clocks(local)
+    clk.start()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record()
+    for i in range(args.steps):
+        rm.rope_ladder_map(lad, seqs, offs, k=k, out=outs[i % 2])
+    ev1.record()
+    torch.cuda.synchronize()
+    clocks = clk.stop()
+    elapsed = ev0.elapsed_time(ev1) / 1000.0
+    if dist:
+        t = torch.tensor([elapsed], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed = float(t.item())
+        dist.barrier()
+    rm.rope_sync_status()
+    stage_ms = rm.rope_profile_read(args.steps)
+    rm.rope_profile_enable(0)
+    w = outs[(args.steps - 1) % 2][0][:, 0].cpu().numpy()
+    ok = used > 0
+    acc = float(np.mean(np.abs(w[ok] - rd.true_pos[ok]) < used[ok]))
+    value = ws * args.steps * scores_step / elapsed
+    work_ms = float(np.mean(stage_ms[:, 1]))  # encode + scan + merge of every bucket (streams joined)
+    flops = scores_step * 8 * p.dim
+    peaks, peak_src = measured_peaks()
+    peak = peaks["bf16_tflops_sustained"]
+    achieved = flops / (work_ms / 1000.0) / 1e12
+    roofline = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": None, "kernel": "scan_tc_kernel over all buckets (encode and merge included: the "
+                "buckets overlap on 4 streams)", "peak_source": f"{peak_src} bf16_tflops_sustained",
+                "flops_per_step": flops,
+                "stage_ms": {"bucket_sort_and_sync": float(np.mean(stage_ms[:, 0])), "buckets": work_ms,
+                             "free": float(np.mean(stage_ms[:, 2]))}}
+    hist = {int(N): int(c) for N, c in zip(*np.unique(used[ok], return_counts=True))}
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1000.0 * elapsed / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+        "config": {"workload": args.workload + ": " + wl["desc"], "reads_per_step_per_gpu": n,
+                   "scores_per_step_per_gpu": scores_step, "ladder_lengths": len(lens), "reads_per_length": hist,
+                   "reads_too_short": int((~ok).sum()), "index_build_s": index_s,
+                   "l2": "inputs larger than L2 (54 bucket indexes, 0.5 GB)"},
+        "reads_per_s": ws * args.steps * n / elapsed, "top1_acc": acc, "roofline": roofline,
+        "gpu_launches": None, "clocks": clocks,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    lad.free()
+    if dist:
+        dist.destroy_process_group()
+
+
 def main():
     args = parse()
     wl = WORKLOADS[args.workload]
     if args.impl == "reference":
         run_reference(args, wl)
+        return
+    if "ladder" in wl:
+        run_ladder(args, wl)
         return
 
     import torch

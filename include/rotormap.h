@@ -288,6 +288,44 @@ rope_status rope_map_rerank(const rope_index* idx, const uint8_t* seqs, const in
                             const rope_score_opts* opts, const rope_reranker* rr, int32_t keep, int64_t* out_win,
                             float* out_score, float* out_pred, cudaStream_t stream);
 
+/* ---- length ladder: reads of many lengths (§3.5) -------------------------
+ * §3.5 maps a read by its head of one fixed window length N. For reads of
+ * many lengths a ladder of window lengths N_j = floor(n_min * 2^(j/steps)),
+ * j = 0, 1, ... while N_j <= min(n_max, reference length) (repeats dropped),
+ * is indexed, and each read is mapped by its head of the largest N_j not
+ * longer than the read. Every bucket j is a full index (window norms,
+ * anchors) with window length N_j and the parameters' s, m, t, variant,
+ * score_mode and stride, built over one shared packed copy of the
+ * reference. */
+typedef struct rope_ladder rope_ladder;
+
+/* The ladder's lengths, host only: returns their number (or -1 for n_min < 1,
+ * n_max < n_min or steps outside [1, 64]) and writes the first `cap` of them to
+ * out_host (may be NULL). */
+int32_t rope_ladder_lengths(int32_t n_min, int32_t n_max, int32_t steps_per_octave, int32_t* out_host, int32_t cap);
+
+/* Builds the ladder over a device reference (as rope_encode_reference;
+ * p->window_len is ignored). At most 64 lengths (ROPE_ERR_UNSUPPORTED above);
+ * n_min must be >= p->s. Synchronises `stream`. */
+rope_status rope_ladder_create(const rope_params* p, const uint8_t* ref, int64_t len, int32_t n_min, int32_t n_max,
+                               int32_t steps_per_octave, rope_ladder** out, cudaStream_t stream);
+void rope_ladder_free(rope_ladder* lad);
+/* number of lengths; bucket j's index (owned by the ladder; NULL out of range) */
+int32_t rope_ladder_size(const rope_ladder* lad);
+const rope_index* rope_ladder_bucket(const rope_ladder* lad, int32_t j);
+
+/* Maps reads of any length: per read the bucket's k best window starts and
+ * fidelities as rope_map gives for that bucket's index (opts as for
+ * rope_score_topk; j_begin/j_end must be 0). out_len [n_reads] (may be NULL)
+ * receives the window length used, -1 for a read shorter than n_min, whose
+ * outputs are all (-1, -inf). Synchronises `stream` once (after bucketing the
+ * reads on the device, to read back the bucket sizes); the buckets then run on
+ * the ladder's own streams and `stream` waits for them before returning. Not
+ * for concurrent calls on one ladder from several host threads. */
+rope_status rope_ladder_map(const rope_ladder* lad, const uint8_t* seqs, const int64_t* offsets, int64_t n_reads,
+                            const rope_score_opts* opts, int64_t* out_win, float* out_score, int32_t* out_len,
+                            cudaStream_t stream);
+
 /* ---- multi-GPU: merge of window-range shards (host only) ---------------
  * The reference's windows can be split into disjoint ranges scanned on
  * different GPUs (segments are independent, §2.8). win_host/score_host hold

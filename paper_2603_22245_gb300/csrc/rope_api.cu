@@ -7,6 +7,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <mutex>
@@ -58,6 +59,20 @@ extern "C" const char* rope_status_string(rope_status st) {
 }
 
 extern "C" const char* rope_last_error(void) { return g_last_error; }
+
+// Bound of every in-kernel wait: 2 s, or ROPE_WAIT_LIMIT_S seconds (clamped to
+// [0.05, 120]) for runs that slow kernels down on purpose, such as profilers
+// replaying a kernel under instrumentation.
+uint64_t rope::wait_limit_ns() {
+  static const uint64_t v = [] {
+    const char* e = getenv("ROPE_WAIT_LIMIT_S");
+    double s = e ? atof(e) : 2.0;
+    if (!(s >= 0.05)) s = 0.05;
+    if (s > 120.0) s = 120.0;
+    return (uint64_t)(s * 1e9);
+  }();
+  return v;
+}
 
 // ---------------------------------------------------------------- per-device context
 
@@ -286,6 +301,9 @@ void prof_mark(int slot, int which, cudaStream_t st) {
 
 }  // namespace
 
+int rope::host_prof_begin(cudaStream_t st) { return prof_begin(st); }
+void rope::host_prof_mark(int slot, int which, cudaStream_t st) { prof_mark(slot, which, st); }
+
 extern "C" rope_status rope_profile_enable(int32_t max_calls) {
   if (max_calls < 0) return fail(ROPE_ERR_INVALID_ARG, "max_calls < 0");
   std::lock_guard<std::mutex> lk(g_prof.mu);
@@ -376,8 +394,8 @@ extern "C" void rope_index_free(rope_index* idx) {
   delete idx;
 }
 
-extern "C" rope_status rope_encode_reference(const rope_params* p, const uint8_t* ref, int64_t len, rope_index** out,
-                                             cudaStream_t stream) {
+rope_status rope::encode_reference_impl(const rope_params* p, const uint8_t* ref, int64_t len,
+                                        const uint32_t* shared_packed, rope_index** out, cudaStream_t stream) {
   rope_status st = check_params(p);
   if (st != ROPE_OK) return st;
   if (!out) return fail(ROPE_ERR_INVALID_ARG, "out is NULL");
@@ -386,7 +404,8 @@ extern "C" rope_status rope_encode_reference(const rope_params* p, const uint8_t
   const int D = p->m << (2 * p->t);
   if (D > kMaxScanDim) return fail(ROPE_ERR_UNSUPPORTED, "index dimension %d > %d", D, kMaxScanDim);
   const int64_t W = (len - p->window_len) / p->stride + 1;
-  if (W >= (int64_t)0xFFFFFFFF) return fail(ROPE_ERR_UNSUPPORTED, "more than 2^32-1 windows");
+  // window numbers are 32-bit in the scans, with room for one super-tile past the end
+  if (W > (int64_t)0xFFFFFFFF - 65536) return fail(ROPE_ERR_UNSUPPORTED, "more than 2^32 - 2^16 windows");
   DeviceCtx* c;
   st = get_ctx(&c);
   if (st != ROPE_OK) return st;
@@ -414,8 +433,11 @@ extern "C" rope_status rope_encode_reference(const rope_params* p, const uint8_t
   uint16_t *map_lsb = nullptr, *map = nullptr;
   float2 *phase = nullptr, *rot = nullptr, *eout = nullptr, *ein = nullptr;
   double2 *phase64 = nullptr, *rot64 = nullptr, *eout64 = nullptr, *ein64 = nullptr;
-  if ((st = upload(idx->owned, std::vector<uint32_t>(), &packed, (size_t)(n_words + pad_words))) != ROPE_OK)
+  if (shared_packed) {
+    packed = const_cast<uint32_t*>(shared_packed);  // borrowed: another index owns it
+  } else if ((st = upload(idx->owned, std::vector<uint32_t>(), &packed, (size_t)(n_words + pad_words))) != ROPE_OK) {
     return cleanup(st);
+  }
   if ((st = upload(idx->owned, std::vector<float>(), &inv_norm, (size_t)W + 8192)) != ROPE_OK) return cleanup(st);
   if (p->score_mode == 1 &&
       (st = upload(idx->owned, std::vector<float>(), &band_norm, (size_t)W * p->m + 8192)) != ROPE_OK)
@@ -460,7 +482,7 @@ extern "C" rope_status rope_encode_reference(const rope_params* p, const uint8_t
   // clear stale status, pack, pre-pass
   int zero = 0;
   cudaError_t e = cudaMemcpy(c->status, &zero, sizeof(int), cudaMemcpyHostToDevice);
-  if (e == cudaSuccess) e = launch_pack(ref, len, packed, c->status, stream);
+  if (e == cudaSuccess && !shared_packed) e = launch_pack(ref, len, packed, c->status, stream);
   if (e == cudaSuccess) {
     PrepassTables pt{phase64, rot64, eout64, ein64};
     e = launch_prepass(ix, pt, anchors, inv_norm, band_norm, c->status, stream);
@@ -470,6 +492,11 @@ extern "C" rope_status rope_encode_reference(const rope_params* p, const uint8_t
   if (st != ROPE_OK) return cleanup(st);
   *out = idx;
   return ROPE_OK;
+}
+
+extern "C" rope_status rope_encode_reference(const rope_params* p, const uint8_t* ref, int64_t len, rope_index** out,
+                                             cudaStream_t stream) {
+  return encode_reference_impl(p, ref, len, nullptr, out, stream);
 }
 
 extern "C" rope_status rope_index_info(const rope_index* idx, int64_t* n_windows, int64_t* ref_len,
@@ -554,6 +581,8 @@ rope_status plan_scan(const rope_index* idx, int32_t precision, int64_t n_reads,
   const int64_t sup_per_range = (n_sup + nr - 1) / nr;
   a.range_len = sup_per_range * sup;
   a.n_ranges = (int32_t)((n_sup + sup_per_range - 1) / sup_per_range);
+  a.lists_per_range = pl.tc ? scan_tc_lists_per_range(ix.D) : 1;
+  a.wait_limit_ns = wait_limit_ns();
   *out = pl;
   return ROPE_OK;
 }
@@ -575,9 +604,9 @@ rope_status check_opts(const rope_score_opts* o, rope_score_opts* v) {
 
 }  // namespace
 
-static rope_status score_topk_impl(const rope_index* idx, const float* emb_f32, const uint16_t* emb_bf16,
-                                   const float* norms, int64_t n_reads, const rope_score_opts* opts,
-                                   int64_t* out_win, float* out_score, cudaStream_t stream, int prof_slot) {
+rope_status rope::score_topk_impl(const rope_index* idx, const float* emb_f32, const uint16_t* emb_bf16,
+                                  const float* norms, int64_t n_reads, const rope_score_opts* opts, int64_t* out_win,
+                                  float* out_score, cudaStream_t stream, int prof_slot, const int64_t* out_row) {
   if (!idx) return fail(ROPE_ERR_INVALID_ARG, "index is NULL");
   rope_score_opts o;
   rope_status st = check_opts(opts, &o);
@@ -595,10 +624,10 @@ static rope_status score_topk_impl(const rope_index* idx, const float* emb_f32, 
 
   ScanPlan pl;
   Candidate* cand = nullptr;
-  int32_t n_ranges = 1;
+  int32_t n_ranges = 1;  // candidate lists per read seen by the merge
   if (je > jb) {
     if ((st = plan_scan(idx, o.precision, n_reads, jb, je, o.n_ranges, c->num_sms, &pl)) != ROPE_OK) return st;
-    n_ranges = pl.a.n_ranges;
+    n_ranges = pl.a.n_ranges * pl.a.lists_per_range;
   }
   const size_t cand_bytes = (size_t)n_reads * n_ranges * o.cand_depth * sizeof(Candidate);
   if ((st = pool_alloc(c, (void**)&cand, cand_bytes, stream)) != ROPE_OK) return st;
@@ -634,6 +663,7 @@ static rope_status score_topk_impl(const rope_index* idx, const float* emb_f32, 
   m.norms = norms;
   m.out_win = out_win;
   m.out_score = out_score;
+  m.out_row = out_row;
   m.status = c->status;
   cudaError_t e = launch_merge(ix, m, stream);
   prof_mark(prof_slot, 3, stream);
@@ -648,7 +678,7 @@ extern "C" rope_status rope_score_topk(const rope_index* idx, const float* emb_f
   const int slot = prof_begin(stream);
   prof_mark(slot, 1, stream);
   const rope_status st = score_topk_impl(idx, emb_f32, emb_bf16, norms, n_reads, opts, out_win, out_score, stream,
-                                         slot);
+                                         slot, nullptr);
   if (slot >= 0 && st != ROPE_OK) {
     prof_mark(slot, 2, stream);
     prof_mark(slot, 3, stream);
@@ -716,7 +746,7 @@ extern "C" rope_status rope_map(const rope_index* idx, const uint8_t* seqs, cons
   if (st == ROPE_OK) {
     o.j_begin = 0;
     o.j_end = 0;
-    st = score_topk_impl(idx, emb, embh, norms, n_reads, &o, out_win, out_score, stream, slot);
+    st = score_topk_impl(idx, emb, embh, norms, n_reads, &o, out_win, out_score, stream, slot, nullptr);
   }
   if (slot >= 0 && st != ROPE_OK) {
     prof_mark(slot, 2, stream);
@@ -801,17 +831,22 @@ extern "C" rope_status rope_score_topk_noalloc(const rope_index* idx, const floa
                 (long long)n_reads, o.cand_depth, per_range, cap, cap / ((size_t)o.cand_depth * sizeof(Candidate)));
 
   ScanPlan pl;
-  int32_t n_ranges = 1;
+  int32_t n_ranges = 1;  // candidate lists per read seen by the merge
   if (je > jb) {
     if ((st = plan_scan(idx, o.precision, n_reads, jb, je, o.n_ranges, num_sms, &pl)) != ROPE_OK) return st;
-    if ((size_t)pl.a.n_ranges * per_range > cap) {
+    const size_t lpr = (size_t)pl.a.lists_per_range;
+    if ((size_t)pl.a.n_ranges * lpr * per_range > cap) {
       if (o.n_ranges > 0)
         return fail(ROPE_ERR_INVALID_ARG, "n_ranges=%d needs %zu bytes of scratch; the allocation-free scratch "
-                    "holds %zu", o.n_ranges, (size_t)pl.a.n_ranges * per_range, cap);
-      if ((st = plan_scan(idx, o.precision, n_reads, jb, je, (int32_t)(cap / per_range), num_sms, &pl)) != ROPE_OK)
+                    "holds %zu", o.n_ranges, (size_t)pl.a.n_ranges * lpr * per_range, cap);
+      if (lpr * per_range > cap)
+        return fail(ROPE_ERR_INVALID_ARG, "n_reads=%lld needs %zu bytes of candidates; the allocation-free scratch "
+                    "holds %zu", (long long)n_reads, lpr * per_range, cap);
+      if ((st = plan_scan(idx, o.precision, n_reads, jb, je, (int32_t)(cap / (lpr * per_range)), num_sms, &pl)) !=
+          ROPE_OK)
         return st;
     }
-    n_ranges = pl.a.n_ranges;
+    n_ranges = pl.a.n_ranges * pl.a.lists_per_range;
   }
   int* status = static_cast<int*>(base);
   Candidate* cand = reinterpret_cast<Candidate*>(static_cast<unsigned char*>(base) + kNoAllocHeadBytes);

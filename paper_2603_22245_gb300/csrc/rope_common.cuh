@@ -169,6 +169,21 @@ struct Chain : ChainB<4> {
   static constexpr int LPC = D / 4;
 };
 
+// ---------------------------------------------------------------- packed FP32 pairs
+
+// (re0^2 + im0^2, re1^2 + im1^2) with the FP32x2 instructions of sm_100+: one
+// packed multiply and one packed fma for two scores, each lane of the pair
+// rounded exactly as fmaf(re, re, im * im).
+__device__ __forceinline__ void abs2_pair(uint32_t re0, uint32_t re1, uint32_t im0, uint32_t im1, float& s0,
+                                          float& s1) {
+  uint64_t re, im, r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(re) : "r"(re0), "r"(re1));
+  asm("mov.b64 %0, {%1, %2};" : "=l"(im) : "r"(im0), "r"(im1));
+  asm("mul.rn.f32x2 %0, %1, %1;" : "=l"(r) : "l"(im));
+  asm("fma.rn.f32x2 %0, %1, %1, %2;" : "=l"(r) : "l"(re), "l"(r));
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(s0), "=f"(s1) : "l"(r));
+}
+
 // ---------------------------------------------------------------- PTX: mbarrier
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -197,16 +212,31 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   return ok != 0;
 }
 
+// try_wait that may park the thread until the phase completes or about
+// kSuspendHintNs pass, so a waiting warp takes no issue slots from the warps
+// doing the work.
+constexpr uint32_t kSuspendHintNs = 200000;
+__device__ __forceinline__ bool mbar_try_wait_suspend(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity), "n"(kSuspendHintNs)
+      : "memory");
+  return ok != 0;
+}
+
 // Bounded wait on a phase parity. Returns false (and sets the timeout bit and
 // the block's abort flag) if the phase did not complete within kWaitLimitNs,
 // or if another role of the block has already aborted.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag, int* status) {
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag, int* status,
+                                          uint64_t limit_ns = kWaitLimitNs) {
   if (mbar_try_wait(bar, parity)) return true;
   const uint64_t t0 = globaltimer_ns();
   for (;;) {
-    if (mbar_try_wait(bar, parity)) return true;
+    if (mbar_try_wait_suspend(bar, parity)) return true;
     if (*abort_flag) return false;
-    if (globaltimer_ns() - t0 > kWaitLimitNs) {
+    if (globaltimer_ns() - t0 > limit_ns) {
       *abort_flag = 1;
       set_status(status, kStatusTimeout);
       return false;
@@ -217,8 +247,8 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volati
 // Warp-uniform bounded wait: every lane waits, then the warp agrees (and
 // reconverges) before any .sync.aligned instruction that follows.
 __device__ __forceinline__ bool mbar_wait_warp(uint64_t* bar, uint32_t parity, volatile int* abort_flag,
-                                               int* status) {
-  const bool ok = mbar_wait(bar, parity, abort_flag, status);
+                                               int* status, uint64_t limit_ns = kWaitLimitNs) {
+  const bool ok = mbar_wait(bar, parity, abort_flag, status, limit_ns);
   return __all_sync(0xffffffffu, ok);
 }
 

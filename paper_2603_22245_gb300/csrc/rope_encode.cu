@@ -87,7 +87,8 @@ cudaError_t launch_mer_bins(const uint32_t* packed, int64_t len, int64_t n_words
 // sum of §2.1-§2.3 in FP32, deterministic).
 __global__ void encode_reads_kernel(EncTables tb, const uint8_t* __restrict__ seqs,
                                     const int64_t* __restrict__ offsets, int64_t n, float* __restrict__ emb_f32,
-                                    __nv_bfloat16* __restrict__ emb_bf16, float* __restrict__ norms, int* status) {
+                                    __nv_bfloat16* __restrict__ emb_bf16, float* __restrict__ norms, int* status,
+                                    const int64_t* __restrict__ perm) {
   extern __shared__ float2 enc_acc[];
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
@@ -95,8 +96,9 @@ __global__ void encode_reads_kernel(EncTables tb, const uint8_t* __restrict__ se
   float2* acc = enc_acc + (size_t)warp * tb.D;
   const int n_loc = tb.N - tb.s + 1;
   for (int64_t r = (int64_t)blockIdx.x * wpb + warp; r < n; r += (int64_t)gridDim.x * wpb) {
-    const int64_t start = offsets[r];
-    const int64_t len = offsets[r + 1] - start;
+    const int64_t src = perm ? perm[r] : r;
+    const int64_t start = offsets[src];
+    const int64_t len = offsets[src + 1] - start;
     const uint8_t* seq = seqs + start;
     for (int g = lane; g < tb.D; g += 32) acc[g] = make_float2(0.f, 0.f);
     bool ok = len >= tb.N;
@@ -165,7 +167,8 @@ __global__ void encode_reads_kernel(EncTables tb, const uint8_t* __restrict__ se
 }
 
 cudaError_t launch_encode_reads(const EncTables& tb, const uint8_t* seqs, const int64_t* offsets, int64_t n,
-                                float* emb_f32, uint16_t* emb_bf16, float* norms, int* status, cudaStream_t st) {
+                                float* emb_f32, uint16_t* emb_bf16, float* norms, int* status, cudaStream_t st,
+                                const int64_t* perm) {
   if (n <= 0) return cudaSuccess;
   int wpb = (int)(48 * 1024 / (tb.D * sizeof(float2)));
   if (wpb > 8) wpb = 8;
@@ -175,7 +178,7 @@ cudaError_t launch_encode_reads(const EncTables& tb, const uint8_t* seqs, const 
   if (blocks > 152 * 64) blocks = 152 * 64;
   encode_reads_kernel<<<(unsigned)blocks, wpb * 32, smem, st>>>(tb, seqs, offsets, n, emb_f32,
                                                                   reinterpret_cast<__nv_bfloat16*>(emb_bf16), norms,
-                                                                  status);
+                                                                  status, perm);
   return cudaGetLastError();
 }
 

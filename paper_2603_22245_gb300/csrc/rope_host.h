@@ -22,6 +22,19 @@ rope_status host_fail(rope_status st, const char* fmt, ...);
 rope_status host_ctx(DeviceCtx** out);
 // Stream-ordered scratch from the context's pool.
 rope_status host_pool_alloc(DeviceCtx* c, void** p, size_t bytes, cudaStream_t st);
+// Stage timing of one call (rope_profile_enable): a slot (or -1 when off or
+// full) and its marks 1..3.
+int host_prof_begin(cudaStream_t st);
+void host_prof_mark(int slot, int which, cudaStream_t st);
+// Index build; with shared_packed set, the index borrows that packed
+// reference (same letters, owned by another index) instead of packing ref.
+rope_status encode_reference_impl(const rope_params* p, const uint8_t* ref, int64_t len,
+                                  const uint32_t* shared_packed, rope_index** out, cudaStream_t stream);
+// Scan + merge for n_reads encoded reads; the result of read r goes to output
+// row out_row[r] (out_row null: row r). prof_slot < 0: no stage timing.
+rope_status score_topk_impl(const rope_index* idx, const float* emb_f32, const uint16_t* emb_bf16,
+                            const float* norms, int64_t n_reads, const rope_score_opts* opts, int64_t* out_win,
+                            float* out_score, cudaStream_t stream, int prof_slot, const int64_t* out_row);
 
 }  // namespace rope
 

@@ -35,9 +35,11 @@ struct ScanArgs {
   int32_t n_groups;
   int32_t cand_depth;        // candidates kept per read per range
   int32_t sep;
-  Candidate* cand;           // [n_reads, n_ranges, cand_depth]
+  Candidate* cand;           // [n_reads, n_ranges * lists_per_range, cand_depth]
   float* dense;              // [n_reads, je-jb] (dense mode)
   int* status;
+  int32_t lists_per_range;   // candidate lists a scan keeps per read and range
+  uint64_t wait_limit_ns;    // bound of every in-kernel wait
 };
 
 struct MergeArgs {
@@ -48,15 +50,30 @@ struct MergeArgs {
   const float* norms;
   int64_t* out_win;
   float* out_score;
+  const int64_t* out_row;  // output row of read r (null: row r)
   int* status;
 };
+
+// rope_ladder.cu
+constexpr int kLadderMaxBuckets = 64;
+// entries of the per-block histogram scratch (int64) for n_reads reads
+int64_t ladder_hist_entries(int64_t n_reads, int nbk);
+// bucket of each read (largest lens[j] <= length, -1 if none; out_len = that
+// length, may be null) and a stable sort of the bucketed reads by bucket:
+// perm[base[b] + i] = i-th read of bucket b, count[b] = size of bucket b
+cudaError_t launch_ladder_sort(const int64_t* offsets, int64_t n, const int32_t* lens, int nbk, int32_t* bucket,
+                               int32_t* out_len, int64_t* hist, int64_t* base, int64_t* count, int64_t* perm,
+                               cudaStream_t st);
+cudaError_t launch_fill_empty(int64_t* win, float* score, int64_t n, cudaStream_t st);
 
 // rope_encode.cu
 cudaError_t launch_pack(const uint8_t* seq, int64_t len, uint32_t* out, int* status, cudaStream_t st);
 cudaError_t launch_mer_bins(const uint32_t* packed, int64_t len, int64_t n_words, int s, const uint16_t* map_lsb,
                             uint16_t* out, cudaStream_t st);
+// Row r encodes read perm[r] (perm null: read r).
 cudaError_t launch_encode_reads(const EncTables& tb, const uint8_t* seqs, const int64_t* offsets, int64_t n,
-                                float* emb_f32, uint16_t* emb_bf16, float* norms, int* status, cudaStream_t st);
+                                float* emb_f32, uint16_t* emb_bf16, float* norms, int* status, cudaStream_t st,
+                                const int64_t* perm = nullptr);
 struct PrepassTables {
   const double2* phase;  // [m*(N-s+1)]
   const double2* rot;    // [m]
@@ -79,6 +96,8 @@ int scan_tc_supported(int D);
 int64_t scan_tc_super_tile(int D);
 int scan_tc_group(int D);
 int scan_tc_max_stride();
+int scan_tc_lists_per_range(int D);
+uint64_t wait_limit_ns();
 cudaError_t launch_scan_tc(const DevIndex& ix, const ScanArgs& a, bool dense, int num_sms, cudaStream_t st);
 
 // rope_merge.cu

@@ -160,8 +160,9 @@ __global__ void merge_kernel(DevIndex ix, MergeArgs a) {
         ow = (int64_t)(0xFFFFFFFFu - (uint32_t)my_key) * ix.stride;
         os = unord_float((uint32_t)(my_key >> 32));
       }
-      a.out_win[r * a.k + lane] = ow;
-      a.out_score[r * a.k + lane] = os;
+      const int64_t orow = a.out_row ? a.out_row[r] : r;
+      a.out_win[orow * a.k + lane] = ow;
+      a.out_score[orow * a.k + lane] = os;
     }
   }
 }

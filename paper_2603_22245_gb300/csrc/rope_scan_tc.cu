@@ -8,7 +8,7 @@
 //     once per work item by the epilogue warps.
 //   * B operand (shared memory, same layout): per stage T windows as 2T rows,
 //     row n = [cr | ci] and row T+n = [ci | -cr] of window n. The generator
-//     warps produce them: each chain of 8 lanes runs the §3.4 recurrence from
+//     warps produce them: each chain of LPC lanes runs the §3.4 recurrence from
 //     an exact anchor through 64 consecutive windows and emits one window per
 //     stage, scaled by the stored 1/sqrt(C_j) and rounded to BF16.
 //   * D (tensor memory): per stage and tile a 128 x 2T FP32 accumulator whose
@@ -16,10 +16,11 @@
 //   * One thread issues tcgen05.mma (M = 128, N = 2T = 128, K = 16 per
 //     instruction; an MMA costs at least ~45 cycles whatever N is, so N = 128
 //     keeps the tensor pipe saturated) and commits to mbarriers; a producer
-//     warp streams the 2-bit packed reference and the window norms of each
-//     super-tile into shared memory with bulk copies (TMA); epilogue warps
-//     (thread = read) load the accumulators with tcgen05.ld in 16-column
-//     chunks, form Re^2 + Im^2 and keep the read's best windows.
+//     warp streams the 2-bit packed reference of each super-tile into shared
+//     memory with bulk copies (TMA); epilogue warps (thread = read; HALVES
+//     warps split an accumulator's windows) load the accumulators with
+//     tcgen05.ld in 16-column chunks, form Re^2 + Im^2 and keep the read's best
+//     windows in a list per (read, half).
 // Every wait is bounded; a wait that runs out sets the timeout status bit and
 // the block drains its in-flight copies and MMAs, frees tensor memory and exits.
 #include <cuda_bf16.h>
@@ -29,15 +30,17 @@
 
 namespace rope {
 
-template <int D_, int NT_, int T_, int STAGES_, int NB_>
+template <int D_, int NT_, int T_, int STAGES_, int NB_, int LPC_, int HALVES_>
 struct TcShape {
-  static constexpr int D = D_, NT = NT_, T = T_, STAGES = STAGES_, NB = NB_;
+  static constexpr int D = D_, NT = NT_, T = T_, STAGES = STAGES_, NB = NB_;  // NB: most B ring slots
   static constexpr int A = kAnchorPeriod;
-  static constexpr int BPL = D / 8;              // complex entries per generator lane
-  static constexpr int LPC = 8;                  // lanes per chain
+  static constexpr int LPC = LPC_;               // lanes per chain
+  static constexpr int BPL = D / LPC;            // complex entries per generator lane
   static constexpr int CPW = 32 / LPC;           // chains per warp
   static constexpr int GEN_WARPS = T / CPW;
-  static constexpr int EPI_WARPS = 4 * NT;
+  static constexpr int HALVES = HALVES_;         // epilogue warps sharing one accumulator's columns
+  static constexpr int WPH = T / HALVES;         // windows per epilogue warp per stage
+  static constexpr int EPI_WARPS = 4 * NT * HALVES;
   static constexpr int WARP_MMA = EPI_WARPS;
   static constexpr int WARP_PROD = EPI_WARPS + 1;
   static constexpr int WARP_GEN0 = EPI_WARPS + 2;
@@ -56,15 +59,18 @@ struct TcShape {
   static_assert(D == 32 || D == 64, "complex dimension");
   static_assert(GEN_WARPS * CPW == T, "T must be a multiple of chains per warp");
   static_assert(STAGES * NT * 2 * T <= TMEM_COLS, "tensor memory budget");
-  static_assert(T % 16 == 0, "the epilogue loads 16-column chunks");
+  static_assert(WPH % 16 == 0, "the epilogue loads 16-column chunks");
+  static_assert(BPL == 4 || BPL % 8 == 0, "generator lanes write 8-byte or whole 16-byte pieces");
   static_assert((2 * T) % 16 == 0 && 2 * T <= 256, "MMA N");
   static_assert(NTHREADS <= 1024, "block size");
 };
 
 struct TcLaunch {
+  int32_t nb;              // B ring slots in use (1..NB, the most that fit in shared memory)
   int32_t words_per_slot;  // packed words staged per super-tile (multiple of 4)
   int32_t st_slot_bytes;   // bytes of one super-tile data slot
-  int32_t bins_bytes;      // bytes of the per-chain bin arrays (stride 1)
+  int32_t bins_bytes;      // bytes of the chain-interleaved bin arrays (stride 1)
+  int32_t inv_bytes;       // bytes of the chain-interleaved window norms
 };
 
 __device__ __forceinline__ float fmax3(float a, float b, float c) {
@@ -93,14 +99,19 @@ __global__ void __launch_bounds__(Sh::NTHREADS, 1) scan_tc_kernel(DevIndex ix, S
   __shared__ uint32_t tmem_base_s;
   __shared__ int abort_s;
 
-  // dynamic shared memory: [A tiles | B ring | 2 super-tile slots | chain bins | lists]
+  // dynamic shared memory:
+  //   [A tiles | B ring | 2 packed-word slots | window norms [A][T] | bins [2][A][T] | lists]
+  // (norms and bins are chain-interleaved: entry (step i, chain c) at i*T + c,
+  // so the chains of a warp read consecutive addresses)
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(tc_smem_raw) + 1023) & ~uintptr_t(1023));
   uint8_t* a_tiles = smem;
   uint8_t* b_ring = a_tiles + NT * Sh::A_TILE_BYTES;
-  uint8_t* st_slots = b_ring + NB * Sh::B_SLOT_BYTES;
-  uint8_t* chain_bins = st_slots + 2 * L.st_slot_bytes;
-  float* list_s = reinterpret_cast<float*>(chain_bins + L.bins_bytes);
-  uint32_t* list_w = reinterpret_cast<uint32_t*>(list_s + (size_t)a.cand_depth * Sh::GROUP);
+  uint8_t* st_slots = b_ring + L.nb * Sh::B_SLOT_BYTES;
+  float* inv_t = reinterpret_cast<float*>(st_slots + 2 * L.st_slot_bytes);
+  uint8_t* bins_t = reinterpret_cast<uint8_t*>(inv_t) + L.inv_bytes;
+  float* list_s = reinterpret_cast<float*>(bins_t + L.bins_bytes);
+  uint32_t* list_w = reinterpret_cast<uint32_t*>(list_s + (size_t)a.cand_depth * Sh::GROUP * Sh::HALVES);
+  const uint64_t wlim = a.wait_limit_ns;
 
   const int tid = threadIdx.x;
   const int warp = tid >> 5;
@@ -109,7 +120,7 @@ __global__ void __launch_bounds__(Sh::NTHREADS, 1) scan_tc_kernel(DevIndex ix, S
   volatile int* abort_flag = &abort_s;
 
   if (tid == 0) {
-    for (int i = 0; i < NB; ++i) {
+    for (int i = 0; i < L.nb; ++i) {
       mbar_init(&bar_bfull[i], Sh::GEN_WARPS);
       mbar_init(&bar_bempty[i], 1);
     }
@@ -138,15 +149,16 @@ __global__ void __launch_bounds__(Sh::NTHREADS, 1) scan_tc_kernel(DevIndex ix, S
 
   if (warp < Sh::EPI_WARPS) {
     // ================================================================ epilogue
+    // warp = (half h, tile, lane quarter q); h selects windows [h*WPH, (h+1)*WPH)
+    // of each stage. Each (read, half) keeps its own candidate list.
     const int q = warp & 3;
-    const int tile = warp >> 2;
+    const int tile = (warp >> 2) % NT;
+    const int h = warp / (4 * NT);
     const int rs = tile * 128 + 32 * q + lane;  // read slot in the group
     const int arow = 32 * q + lane;             // its row in the A tile
-    ThreadList lst;
-    lst.s = list_s + rs;
-    lst.w = list_w + rs;
-    lst.stride = Sh::GROUP;
-    lst.depth = a.cand_depth;
+    const int lstride = Sh::GROUP * Sh::HALVES;
+    float* ls = list_s + h * Sh::GROUP + rs;
+    uint32_t* lw = list_w + h * Sh::GROUP + rs;
     const uint32_t lane_base = (uint32_t)(32 * q) << 16;
     uint8_t* arow_base = a_tiles + tile * Sh::A_TILE_BYTES;
     uint32_t gs = 0;
@@ -159,10 +171,13 @@ __global__ void __launch_bounds__(Sh::NTHREADS, 1) scan_tc_kernel(DevIndex ix, S
       const int64_t j_lo = max(st_begin, a.jb);
       const int64_t j_hi = min(st_begin + a.range_len, a.je);
       const int64_t n_st = (j_hi - st_begin + Sh::SUP - 1) / Sh::SUP;
-      // A operand: this read's normalised BF16 row, 16-byte chunks into the
-      // swizzled tile. The previous item's MMAs have all completed: this
-      // thread consumed every accumulator they wrote.
-      {
+      // window numbers fit in 32 bits with room for a super-tile past the last
+      // window (the index refuses W > 2^32 - 2^16)
+      const uint32_t jlo = (uint32_t)j_lo, jhi = (uint32_t)j_hi;
+      // A operand (written by the h = 0 warps): this read's normalised BF16
+      // row, 16-byte chunks into the swizzled tile. The previous item's MMAs
+      // have all completed: this thread consumed every accumulator they wrote.
+      if (h == 0) {
         const uint4* src = reinterpret_cast<const uint4*>(a.emb_bf16 + (have_read ? r : 0) * 2 * D);
 #pragma unroll
         for (int c = 0; c < 2 * D / 8; ++c) {
@@ -172,67 +187,76 @@ __global__ void __launch_bounds__(Sh::NTHREADS, 1) scan_tc_kernel(DevIndex ix, S
                                     sw128_offset((uint32_t)arow, (uint32_t)((c & 7) * 16))) = v;
         }
         fence_proxy_async_smem();
-        __syncwarp();
-        if (lane == 0) mbar_arrive(&bar_aready);
       }
-      if (!kDense) lst.reset();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&bar_aready);
+      // empty list; thr = the worst kept score, kept in a register
+      float thr = -INFINITY;
+      int worst = 0;
+      if (!kDense) {
+        for (int e = 0; e < a.cand_depth; ++e) {
+          ls[e * lstride] = -INFINITY;
+          lw[e * lstride] = kEmptyWin;
+        }
+      }
       for (int64_t sti = 0; sti < n_st; ++sti) {
-        const int64_t st = st_begin + sti * Sh::SUP;
+        const uint32_t st = (uint32_t)(st_begin + sti * Sh::SUP);
         for (int i = 0; i < A; ++i, ++gs) {
           const uint32_t s = gs % STAGES;
-          if (!mbar_wait_warp(&bar_afull[s], (gs / STAGES) & 1, abort_flag, a.status)) goto epi_done;
+          if (!mbar_wait_warp(&bar_afull[s], (gs / STAGES) & 1, abort_flag, a.status, wlim)) goto epi_done;
           tc_fence_after();
           const uint32_t col = (uint32_t)(((int)s * NT + tile) * 2 * T);
-          const int64_t jbase = st + i;  // column n holds window jbase + n*A
-          const bool full = jbase >= j_lo && jbase + (int64_t)(T - 1) * A < j_hi;
+          const uint32_t jbase = st + (uint32_t)i;  // column n holds window jbase + n*A
+          const bool full = jbase >= jlo && jbase + (uint32_t)((T - 1) * A) < jhi;
 #pragma unroll
-          for (int c0 = 0; c0 < T; c0 += 16) {
+          for (int c0 = h * Sh::WPH; c0 < (h + 1) * Sh::WPH; c0 += 16) {
             uint32_t vr[16], vi[16];
             tmem_ld16(tbase + lane_base + col + c0, vr);
             tmem_ld16(tbase + lane_base + col + T + c0, vi);
             tc_wait_ld();
-            if (c0 + 16 == T) {
-              // the last chunk is in registers: hand the accumulator back
+            if (c0 + 16 == (h + 1) * Sh::WPH) {
+              // this warp's last chunk is in registers: hand the accumulator back
               tc_fence_before();
               __syncwarp();
               if (lane == 0) mbar_arrive(&bar_aempty[s]);
             }
             float sc[16];
 #pragma unroll
-            for (int n = 0; n < 16; ++n) {
-              const float re = __uint_as_float(vr[n]);
-              const float im = __uint_as_float(vi[n]);
-              sc[n] = fmaf(re, re, im * im);
-            }
-            const int64_t jc = jbase + (int64_t)c0 * A;
+            for (int n = 0; n < 16; n += 2) abs2_pair(vr[n], vr[n + 1], vi[n], vi[n + 1], sc[n], sc[n + 1]);
+            const uint32_t jc = jbase + (uint32_t)(c0 * A);
             if (kDense) {
               if (have_read) {
 #pragma unroll
                 for (int n = 0; n < 16; ++n) {
-                  const int64_t j = jc + (int64_t)n * A;
-                  if (j >= j_lo && j < j_hi) a.dense[r * (a.je - a.jb) + (j - a.jb)] = sc[n];
+                  const uint32_t j = jc + (uint32_t)(n * A);
+                  if (j >= jlo && j < jhi) a.dense[r * (a.je - a.jb) + ((int64_t)j - a.jb)] = sc[n];
                 }
               }
             } else {
               float mx;
               if (full) {
-                mx = fmax3(sc[0], sc[1], sc[2]);
-#pragma unroll
-                for (int n = 3; n + 1 < 16; n += 2) mx = fmax3(mx, sc[n], sc[n + 1]);
-                mx = fmaxf(mx, sc[15]);
+                // depth-3 tree of 3-input maxima
+                const float m0 = fmax3(sc[0], sc[1], sc[2]), m1 = fmax3(sc[3], sc[4], sc[5]);
+                const float m2 = fmax3(sc[6], sc[7], sc[8]), m3 = fmax3(sc[9], sc[10], sc[11]);
+                const float m4 = fmax3(sc[12], sc[13], sc[14]);
+                mx = fmaxf(fmax3(m0, m1, m2), fmax3(m3, m4, sc[15]));
               } else {
                 mx = -INFINITY;
 #pragma unroll
                 for (int n = 0; n < 16; ++n) {
-                  const int64_t j = jc + (int64_t)n * A;
-                  if (j >= j_lo && j < j_hi) mx = fmaxf(mx, sc[n]);
+                  const uint32_t j = jc + (uint32_t)(n * A);
+                  if (j >= jlo && j < jhi) mx = fmaxf(mx, sc[n]);
                 }
               }
-              if (have_read && mx >= lst.thr) {
+              if (have_read && mx >= thr) {
 #pragma unroll
                 for (int n = 0; n < 16; ++n) {
-                  const int64_t j = jc + (int64_t)n * A;
-                  if (j >= j_lo && j < j_hi && sc[n] >= lst.thr) lst.insert(sc[n], (uint32_t)j, a.sep, S);
+                  const uint32_t j = jc + (uint32_t)(n * A);
+                  if (j >= jlo && j < jhi && sc[n] >= thr) {
+                    const ListState ns = list_insert(ls, lw, lstride, a.cand_depth, worst, sc[n], j, a.sep, S);
+                    thr = ns.thr;
+                    worst = ns.worst;
+                  }
                 }
               }
             }
@@ -240,15 +264,15 @@ __global__ void __launch_bounds__(Sh::NTHREADS, 1) scan_tc_kernel(DevIndex ix, S
         }
       }
       if (!kDense && have_read) {
-        Candidate* out = a.cand + ((size_t)r * a.n_ranges + rng) * a.cand_depth;
-        for (int e = 0; e < a.cand_depth; ++e) out[e] = Candidate{lst.S(e), lst.Wn(e)};
+        Candidate* out = a.cand + (((size_t)r * a.n_ranges + rng) * Sh::HALVES + h) * a.cand_depth;
+        for (int e = 0; e < a.cand_depth; ++e) out[e] = Candidate{ls[e * lstride], lw[e * lstride]};
       }
     }
   epi_done:;
   } else if (warp == Sh::WARP_MMA) {
     // ================================================================ MMA issue
     if (lane == 0) {
-      uint32_t gs = 0, gb = 0, it = 0;
+      uint32_t gs = 0, it = 0, bslot = 0, bphase = 0;
       bool ok = true;
       const uint64_t a_desc0 = smem_desc_sw128(smem_u32(a_tiles));
       const uint64_t b_desc0 = smem_desc_sw128(smem_u32(b_ring));
@@ -257,12 +281,12 @@ __global__ void __launch_bounds__(Sh::NTHREADS, 1) scan_tc_kernel(DevIndex ix, S
         const int64_t st_begin = a.st0 + (int64_t)rng * a.range_len;
         const int64_t j_hi = min(st_begin + a.range_len, a.je);
         const int64_t n_stage = (j_hi - st_begin + Sh::SUP - 1) / Sh::SUP * A;
-        if (!mbar_wait(&bar_aready, it & 1, abort_flag, a.status)) break;
-        for (int64_t k = 0; k < n_stage; ++k, ++gs, ++gb) {
-          const uint32_t slot = gb % NB;
+        if (!mbar_wait(&bar_aready, it & 1, abort_flag, a.status, wlim)) break;
+        for (int64_t k = 0; k < n_stage; ++k, ++gs) {
+          const uint32_t slot = bslot;
           const uint32_t s = gs % STAGES;
-          if (!mbar_wait(&bar_bfull[slot], (gb / NB) & 1, abort_flag, a.status)) { ok = false; break; }
-          if (!mbar_wait(&bar_aempty[s], ((gs / STAGES) & 1) ^ 1, abort_flag, a.status)) { ok = false; break; }
+          if (!mbar_wait(&bar_bfull[slot], bphase, abort_flag, a.status, wlim)) { ok = false; break; }
+          if (!mbar_wait(&bar_aempty[s], ((gs / STAGES) & 1) ^ 1, abort_flag, a.status, wlim)) { ok = false; break; }
           tc_fence_after();
           // descriptors differ only in the start-address field (16-byte units)
           const uint64_t slot_desc = b_desc0 + (uint64_t)((slot * Sh::B_SLOT_BYTES) >> 4);
@@ -280,11 +304,15 @@ __global__ void __launch_bounds__(Sh::NTHREADS, 1) scan_tc_kernel(DevIndex ix, S
           }
           tc_commit(&bar_bempty[slot]);
           tc_commit(&bar_afull[s]);
+          if (++bslot == (uint32_t)L.nb) {
+            bslot = 0;
+            bphase ^= 1u;
+          }
         }
       }
       // drain: every MMA issued by this thread has completed
       tc_commit(&bar_drain);
-      mbar_wait(&bar_drain, 0, abort_flag, a.status);
+      mbar_wait(&bar_drain, 0, abort_flag, a.status, wlim);
     }
   } else if (warp == Sh::WARP_PROD) {
     // ================================================================ bulk-copy producer
@@ -299,44 +327,45 @@ __global__ void __launch_bounds__(Sh::NTHREADS, 1) scan_tc_kernel(DevIndex ix, S
         for (int64_t sti = 0; sti < n_st; ++sti, ++g) {
           const int64_t st = st_begin + sti * Sh::SUP;
           const uint32_t slot = g & 1;
-          if (!mbar_wait(&bar_stempty[slot], ((g >> 1) & 1) ^ 1, abort_flag, a.status)) { ok = false; break; }
+          if (!mbar_wait(&bar_stempty[slot], ((g >> 1) & 1) ^ 1, abort_flag, a.status, wlim)) { ok = false; break; }
           uint8_t* dst = st_slots + slot * L.st_slot_bytes;
           const int64_t word0 = ((st * S) >> 4) & ~int64_t(3);
           const uint32_t wbytes = (uint32_t)L.words_per_slot * 4u;
-          const uint32_t nbytes = (uint32_t)Sh::SUP * 4u;
-          mbar_expect_tx(&bar_stfull[slot], wbytes + nbytes);
+          mbar_expect_tx(&bar_stfull[slot], wbytes);
           bulk_g2s(dst, ix.packed + word0, wbytes, &bar_stfull[slot]);
-          bulk_g2s(dst + wbytes, ix.inv_norm + st, nbytes, &bar_stfull[slot]);
         }
         if (!ok) break;
       }
       // wait for the copies still in flight into either slot (the latest phase of each)
       for (uint32_t h = (g >= 2 ? g - 2 : 0); h < g; ++h)
-        mbar_wait(&bar_stfull[h & 1], (h >> 1) & 1, abort_flag, a.status);
+        mbar_wait(&bar_stfull[h & 1], (h >> 1) & 1, abort_flag, a.status, wlim);
     }
   } else {
     // ================================================================ window generators
     const int gw = warp - Sh::WARP_GEN0;
     const int chain = gw * Sh::CPW + lane / Sh::LPC;  // B row (Re) and column of its windows
     const int lic = lane % Sh::LPC;
-    uint8_t* bins_out = chain_bins + (size_t)chain * 2 * A;
-    uint8_t* bins_in = bins_out + A;
     ChainB<BPL> ch;
     ch.setup(ix, lic);
     // byte offsets of this lane's pieces in a B slot: row chain = [cr | ci],
-    // row T+chain = [ci | -cr]; BPL bf16 (2*BPL bytes) each
-    uint32_t off_re_cr, off_re_ci, off_im_ci, off_im_cr;
+    // row T+chain = [ci | -cr]; BPL bf16 = 2*BPL bytes each, written as one
+    // 8-byte piece (BPL = 4) or 16-byte pieces
+    constexpr int NPC = BPL == 4 ? 1 : BPL / 8;  // pieces per half-row
+    uint32_t off_re_cr[NPC], off_re_ci[NPC], off_im_ci[NPC], off_im_cr[NPC];
     {
-      const int e_lo = BPL * lic, e_hi = D + BPL * lic;
       auto off = [&](int row, int e) -> uint32_t {
         return (uint32_t)((e >> 6) * Sh::B_KBLK_BYTES) + sw128_offset((uint32_t)row, (uint32_t)((e & 63) * 2));
       };
-      off_re_cr = off(chain, e_lo);
-      off_re_ci = off(chain, e_hi);
-      off_im_ci = off(T + chain, e_lo);
-      off_im_cr = off(T + chain, e_hi);
+#pragma unroll
+      for (int pc = 0; pc < NPC; ++pc) {
+        const int e_lo = BPL * lic + 8 * pc, e_hi = D + BPL * lic + 8 * pc;
+        off_re_cr[pc] = off(chain, e_lo);
+        off_re_ci[pc] = off(chain, e_hi);
+        off_im_ci[pc] = off(T + chain, e_lo);
+        off_im_cr[pc] = off(T + chain, e_hi);
+      }
     }
-    uint32_t g = 0, gb = 0;
+    uint32_t g = 0, bslot = 0, bphase = 0;
     for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
       const int rng = item / a.n_groups;
       const int64_t st_begin = a.st0 + (int64_t)rng * a.range_len;
@@ -345,55 +374,62 @@ __global__ void __launch_bounds__(Sh::NTHREADS, 1) scan_tc_kernel(DevIndex ix, S
       for (int64_t sti = 0; sti < n_st; ++sti, ++g) {
         const int64_t st = st_begin + sti * Sh::SUP;
         const uint32_t slot = g & 1;
-        if (!mbar_wait_warp(&bar_stfull[slot], (g >> 1) & 1, abort_flag, a.status)) goto gen_done;
-        const uint8_t* src = st_slots + slot * L.st_slot_bytes;
-        const uint32_t* words = reinterpret_cast<const uint32_t*>(src);
-        const float* inv = reinterpret_cast<const float*>(src + (size_t)L.words_per_slot * 4);
+        if (!mbar_wait_warp(&bar_stfull[slot], (g >> 1) & 1, abort_flag, a.status, wlim)) goto gen_done;
+        const uint32_t* words = reinterpret_cast<const uint32_t*>(st_slots + slot * L.st_slot_bytes);
         const int64_t word0 = ((st * S) >> 4) & ~int64_t(3);
         const int64_t a_idx = st / A + chain;  // this chain's anchor (padded past the last window)
         const int64_t p_out0 = (st + (int64_t)chain * A) * S;
         const int64_t p_in0 = p_out0 + ix.N - ix.s + 1;
-        if (S == 1) {
-          for (int u = lic; u < 2 * A; u += Sh::LPC) {
-            const int64_t p = u < A ? p_out0 + u : p_in0 + (u - A);
-            bins_out[u] = (uint8_t)bin_staged(words, word0, p, ix.s, ix.map_lsb);
+        // this chain's window norms and (stride 1) bins, chain-interleaved
+        for (int u = lic; u < A; u += Sh::LPC) {
+          inv_t[u * T + chain] = __ldg(ix.inv_norm + st + (int64_t)chain * A + u);
+          if (S == 1) {
+            bins_t[u * T + chain] = (uint8_t)bin_staged(words, word0, p_out0 + u, ix.s, ix.map_lsb);
+            bins_t[(A + u) * T + chain] = (uint8_t)bin_staged(words, word0, p_in0 + u, ix.s, ix.map_lsb);
           }
         }
         ch.load(ix.anchors + a_idx * D, lic);
         __syncwarp();
-        for (int i = 0; i < A; ++i, ++gb) {
-          const uint32_t bslot = gb % NB;
-          const float nv = inv[chain * A + i];
-          if (!mbar_wait_warp(&bar_bempty[bslot], ((gb / NB) & 1) ^ 1, abort_flag, a.status)) goto gen_done;
+        for (int i = 0; i < A; ++i) {
+          const float nv = inv_t[i * T + chain];
+          if (!mbar_wait_warp(&bar_bempty[bslot], bphase ^ 1u, abort_flag, a.status, wlim)) goto gen_done;
           {
             uint8_t* bt = b_ring + bslot * Sh::B_SLOT_BYTES;
             uint32_t pr[BPL / 2], pi[BPL / 2], pn[BPL / 2];
 #pragma unroll
-            for (int h = 0; h < BPL / 2; ++h) {
-              const __nv_bfloat162 rr = __floats2bfloat162_rn(ch.cr[2 * h] * nv, ch.cr[2 * h + 1] * nv);
-              const __nv_bfloat162 ii = __floats2bfloat162_rn(ch.ci[2 * h] * nv, ch.ci[2 * h + 1] * nv);
-              pr[h] = *reinterpret_cast<const uint32_t*>(&rr);
-              pi[h] = *reinterpret_cast<const uint32_t*>(&ii);
-              pn[h] = pr[h] ^ 0x80008000u;
+            for (int hh = 0; hh < BPL / 2; ++hh) {
+              const __nv_bfloat162 rr = __floats2bfloat162_rn(ch.cr[2 * hh] * nv, ch.cr[2 * hh + 1] * nv);
+              const __nv_bfloat162 ii = __floats2bfloat162_rn(ch.ci[2 * hh] * nv, ch.ci[2 * hh + 1] * nv);
+              pr[hh] = *reinterpret_cast<const uint32_t*>(&rr);
+              pi[hh] = *reinterpret_cast<const uint32_t*>(&ii);
+              pn[hh] = pr[hh] ^ 0x80008000u;
             }
             if constexpr (BPL == 4) {
-              *reinterpret_cast<uint2*>(bt + off_re_cr) = make_uint2(pr[0], pr[1]);
-              *reinterpret_cast<uint2*>(bt + off_re_ci) = make_uint2(pi[0], pi[1]);
-              *reinterpret_cast<uint2*>(bt + off_im_ci) = make_uint2(pi[0], pi[1]);
-              *reinterpret_cast<uint2*>(bt + off_im_cr) = make_uint2(pn[0], pn[1]);
+              *reinterpret_cast<uint2*>(bt + off_re_cr[0]) = make_uint2(pr[0], pr[1]);
+              *reinterpret_cast<uint2*>(bt + off_re_ci[0]) = make_uint2(pi[0], pi[1]);
+              *reinterpret_cast<uint2*>(bt + off_im_ci[0]) = make_uint2(pi[0], pi[1]);
+              *reinterpret_cast<uint2*>(bt + off_im_cr[0]) = make_uint2(pn[0], pn[1]);
             } else {
-              *reinterpret_cast<uint4*>(bt + off_re_cr) = make_uint4(pr[0], pr[1], pr[2], pr[3]);
-              *reinterpret_cast<uint4*>(bt + off_re_ci) = make_uint4(pi[0], pi[1], pi[2], pi[3]);
-              *reinterpret_cast<uint4*>(bt + off_im_ci) = make_uint4(pi[0], pi[1], pi[2], pi[3]);
-              *reinterpret_cast<uint4*>(bt + off_im_cr) = make_uint4(pn[0], pn[1], pn[2], pn[3]);
+#pragma unroll
+              for (int pc = 0; pc < NPC; ++pc) {
+                const int o = 4 * pc;
+                *reinterpret_cast<uint4*>(bt + off_re_cr[pc]) = make_uint4(pr[o], pr[o + 1], pr[o + 2], pr[o + 3]);
+                *reinterpret_cast<uint4*>(bt + off_re_ci[pc]) = make_uint4(pi[o], pi[o + 1], pi[o + 2], pi[o + 3]);
+                *reinterpret_cast<uint4*>(bt + off_im_ci[pc]) = make_uint4(pi[o], pi[o + 1], pi[o + 2], pi[o + 3]);
+                *reinterpret_cast<uint4*>(bt + off_im_cr[pc]) = make_uint4(pn[o], pn[o + 1], pn[o + 2], pn[o + 3]);
+              }
             }
           }
           fence_proxy_async_smem();
           __syncwarp();
           if (lane == 0) mbar_arrive(&bar_bfull[bslot]);
+          if (++bslot == (uint32_t)L.nb) {
+            bslot = 0;
+            bphase ^= 1u;
+          }
           // advance the recurrence to the next window
           if (S == 1) {
-            ch.step1(bins_out[i], bins_in[i]);
+            ch.step1(bins_t[i * T + chain], bins_t[(A + i) * T + chain]);
           } else {
             const int64_t po = p_out0 + (int64_t)i * S;
             for (int u = 0; u < S; ++u) {
@@ -422,8 +458,14 @@ __global__ void __launch_bounds__(Sh::NTHREADS, 1) scan_tc_kernel(DevIndex ix, S
 
 // ---------------------------------------------------------------- configurations
 
-using TcShape32 = TcShape<32, 2, 64, 2, 4>;  // d = 64:  256 reads x 64 windows per stage, MMA N = 128
-using TcShape64 = TcShape<64, 2, 64, 2, 2>;  // d = 128: 256 reads x 64 windows per stage, MMA N = 128
+// d = 64:  256 reads x 64 windows per stage, MMA N = 128; 16 epilogue warps (two
+//          per accumulator quarter), 8 generator warps (chains of 4 lanes x 8 entries)
+using TcShape32 = TcShape<32, 2, 64, 2, 4, 4, 2>;
+// d = 128: 256 reads x 64 windows per stage, MMA N = 128 (twice the tensor time
+//          per stage); 8 epilogue warps, 16 generator warps (chains of 8 lanes x 8 entries)
+using TcShape64 = TcShape<64, 2, 64, 2, 2, 8, 1>;
+
+constexpr size_t kTcSmemLimit = 227 * 1024;
 
 int scan_tc_supported(int D) { return D == 32 || D == 64; }
 
@@ -433,28 +475,38 @@ int scan_tc_group(int D) { return D == 32 ? TcShape32::GROUP : D == 64 ? TcShape
 
 int scan_tc_max_stride() { return 8; }
 
+int scan_tc_lists_per_range(int D) {
+  return D == 32 ? TcShape32::HALVES : D == 64 ? TcShape64::HALVES : 1;
+}
+
 template <class Sh>
-static size_t tc_smem_bytes(const DevIndex& ix, int cand_depth, bool dense, TcLaunch* Lout) {
+static size_t tc_smem_bytes(const DevIndex& ix, int cand_depth, bool dense, int nb, TcLaunch* Lout) {
   TcLaunch L;
+  L.nb = nb;
   const int S = ix.stride;
   int64_t words = ((int64_t)Sh::SUP * S + ix.N + 64) / 16 + 8;
   words = (words + 3) & ~int64_t(3);
   L.words_per_slot = (int32_t)words;
-  int64_t slot = words * 4 + (int64_t)Sh::SUP * 4;
+  int64_t slot = words * 4;
   slot = (slot + 127) & ~int64_t(127);
   L.st_slot_bytes = (int32_t)slot;
+  L.inv_bytes = Sh::A * Sh::T * 4;
   L.bins_bytes = S == 1 ? (int32_t)(Sh::T * 2 * Sh::A) : 0;
-  const size_t lists = dense ? 0 : (size_t)cand_depth * Sh::GROUP * 8;
+  const size_t lists = dense ? 0 : (size_t)cand_depth * Sh::GROUP * Sh::HALVES * 8;
   if (Lout) *Lout = L;
-  return 1024 + (size_t)Sh::NT * Sh::A_TILE_BYTES + (size_t)Sh::NB * Sh::B_SLOT_BYTES + 2 * (size_t)L.st_slot_bytes +
-         L.bins_bytes + lists;
+  return 1024 + (size_t)Sh::NT * Sh::A_TILE_BYTES + (size_t)nb * Sh::B_SLOT_BYTES + 2 * (size_t)L.st_slot_bytes +
+         L.inv_bytes + L.bins_bytes + lists;
 }
 
 template <class Sh, bool kDense>
 static cudaError_t launch_tc(const DevIndex& ix, const ScanArgs& a, int num_sms, cudaStream_t st) {
+  // the deepest B ring that fits (long windows at large strides and deep
+  // candidate lists leave room for fewer slots)
   TcLaunch L;
-  const size_t smem = tc_smem_bytes<Sh>(ix, a.cand_depth, kDense, &L);
-  if (smem > 227 * 1024) return cudaErrorInvalidValue;
+  int nb = Sh::NB;
+  size_t smem = tc_smem_bytes<Sh>(ix, a.cand_depth, kDense, nb, &L);
+  while (smem > kTcSmemLimit && nb > 1) smem = tc_smem_bytes<Sh>(ix, a.cand_depth, kDense, nb >>= 1, &L);
+  if (smem > kTcSmemLimit) return cudaErrorInvalidValue;
   auto kern = scan_tc_kernel<Sh, kDense>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;

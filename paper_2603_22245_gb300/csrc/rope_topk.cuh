@@ -55,9 +55,7 @@ struct ThreadList {
   }
 
   // window number j starts at j*stride_pos; buckets are floor(start / sep).
-  // Out of line: the scans call it rarely, and inlining it at every score
-  // position would bloat the instruction stream of the hot loop.
-  __device__ __noinline__ void insert(float sc, uint32_t j, int sep, int stride_pos) {
+  __device__ __forceinline__ void insert(float sc, uint32_t j, int sep, int stride_pos) {
     if (sep > 0) {
       const int64_t bucket = (int64_t)j * stride_pos / sep;
       for (int e = 0; e < depth; ++e) {
@@ -78,5 +76,27 @@ struct ThreadList {
     rescan();
   }
 };
+
+// The same list update as a free function for the tensor-core epilogue: it is
+// out of line (called rarely; inlining it at every score position would bloat
+// the hot loop's instruction stream) and returns the new worst entry and its
+// score by value, so the caller keeps the filter threshold in a register.
+struct ListState {
+  float thr;
+  int worst;
+};
+
+static __device__ __noinline__ ListState list_insert(float* ls, uint32_t* lw, int stride, int depth, int worst, float sc,
+                                             uint32_t j, int sep, int stride_pos) {
+  ThreadList t;
+  t.s = ls;
+  t.w = lw;
+  t.stride = stride;
+  t.depth = depth;
+  t.worst = worst;
+  t.thr = ls[worst * stride];
+  t.insert(sc, j, sep, stride_pos);
+  return ListState{t.thr, t.worst};
+}
 
 }  // namespace rope

@@ -8,6 +8,7 @@ Loading fails loudly when the library has not been built.
 from __future__ import annotations
 
 import ctypes
+import dataclasses
 import os
 from dataclasses import dataclass
 
@@ -74,6 +75,12 @@ EXPORTS = {
     "rope_rerank_features": ([_P, _P, _P, _P, _P, _I64, _I32, _P, _P], ctypes.c_int),
     "rope_rerank_prune": ([_P, _P, _P, _I64, _I32, _I32, _P, _P, _P, _P], ctypes.c_int),
     "rope_map_rerank": ([_P, _P, _P, _I64, _P, _P, _I32, _P, _P, _P, _P], ctypes.c_int),
+    "rope_ladder_lengths": ([_I32, _I32, _I32, _P, _I32], _I32),
+    "rope_ladder_create": ([_P, _P, _I64, _I32, _I32, _I32, _P, _P], ctypes.c_int),
+    "rope_ladder_free": ([_P], None),
+    "rope_ladder_size": ([_P], _I32),
+    "rope_ladder_bucket": ([_P, _I32], _P),
+    "rope_ladder_map": ([_P, _P, _P, _I64, _P, _P, _P, _P, _P], ctypes.c_int),
     "rope_merge_shards_host": ([_P, _P, _I32, _I64, _I32, _I32, _I32, _P, _P], ctypes.c_int),
     "rope_profile_enable": ([_I32], ctypes.c_int),
     "rope_profile_read": ([_P, _I32, _P], ctypes.c_int),
@@ -168,11 +175,13 @@ def _device_view(ptr: int, n: int, typestr: str, dtype) -> torch.Tensor:
 
 
 class Index:
-    """Owner of a ``rope_index`` (freed with rope_index_free)."""
+    """Owner of a ``rope_index`` (freed with rope_index_free), or a borrowed
+    view of one that another object owns (``owner`` set; free() is a no-op)."""
 
-    def __init__(self, handle: int, params: Params):
+    def __init__(self, handle: int, params: Params, owner=None):
         self.handle = handle
         self.params = params
+        self.owner = owner
 
     def info(self) -> dict:
         nw, rl, ap = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int32()
@@ -197,9 +206,9 @@ class Index:
         return _device_view(inf["packed"], (inf["ref_len"] + 15) // 16, "<u4", torch.int32)
 
     def free(self):
-        if self.handle:
+        if self.handle and self.owner is None:
             load().rope_index_free(self.handle)
-            self.handle = None
+        self.handle = None
 
     def __del__(self):
         try:
@@ -321,3 +330,68 @@ def rope_merge_shards_host(wins: np.ndarray, scores: np.ndarray, k_out: int, sep
     _check(load().rope_merge_shards_host(wins.ctypes.data, scores.ctypes.data, n_shards, n_reads, k_in, k_out, sep,
                                          ow.ctypes.data, os_.ctypes.data))
     return ow, os_
+
+
+# ---------------------------------------------------------------- length ladder
+
+def rope_ladder_lengths(n_min: int = 100, n_max: int = 10000, steps_per_octave: int = 8) -> list[int]:
+    """Window lengths floor(n_min * 2^(j/steps)) up to n_max, repeats dropped (host only)."""
+    lib = load()
+    n = lib.rope_ladder_lengths(n_min, n_max, steps_per_octave, None, 0)
+    if n < 0:
+        raise ValueError("bad ladder parameters")
+    buf = (ctypes.c_int32 * max(n, 1))()
+    lib.rope_ladder_lengths(n_min, n_max, steps_per_octave, buf, n)
+    return list(buf[:n])
+
+
+class Ladder:
+    """Owner of a ``rope_ladder``: one index per window length over one packed reference."""
+
+    def __init__(self, handle: int, params: Params, lengths: list[int]):
+        self.handle = handle
+        self.params = params
+        self.lengths = lengths
+
+    def bucket(self, j: int) -> Index:
+        h = load().rope_ladder_bucket(self.handle, j)
+        if not h:
+            raise IndexError(j)
+        return Index(h, dataclasses.replace(self.params, window_len=self.lengths[j]), owner=self)
+
+    def free(self):
+        if self.handle:
+            load().rope_ladder_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def rope_ladder_create(p: Params, ref: torch.Tensor, n_min: int = 100, n_max: int = 10000, steps_per_octave: int = 8,
+                       stream=None) -> Ladder:
+    h = ctypes.c_void_p()
+    pc = p.c()
+    _check(load().rope_ladder_create(ctypes.byref(pc), _ptr(ref), ref.numel(), n_min, n_max, steps_per_octave,
+                                     ctypes.byref(h), _stream(stream)))
+    n = load().rope_ladder_size(h.value)
+    lens = rope_ladder_lengths(n_min, min(n_max, ref.numel()), steps_per_octave)[:n]
+    return Ladder(h.value, p, lens)
+
+
+def rope_ladder_map(lad: Ladder, seqs: torch.Tensor, offsets: torch.Tensor, k: int = 8, sep: int = 0,
+                    precision="bf16", rescore=None, cand_depth: int = 0, rescore_depth: int = 0, n_ranges: int = 0,
+                    out=None, stream=None):
+    """Reads of any length: (starts [n, k], fidelities [n, k], window length used [n] (-1: too short))."""
+    n = offsets.numel() - 1
+    if out is None:
+        out = (torch.empty((n, k), dtype=torch.int64, device=seqs.device),
+               torch.empty((n, k), dtype=torch.float32, device=seqs.device),
+               torch.empty((n,), dtype=torch.int32, device=seqs.device))
+    o = _opts(k, sep, precision, rescore, cand_depth, rescore_depth, n_ranges, 0, 0)
+    _check(load().rope_ladder_map(lad.handle, _ptr(seqs), _ptr(offsets), n, ctypes.byref(o), _ptr(out[0]),
+                                  _ptr(out[1]), _ptr(out[2]), _stream(stream)))
+    return out
