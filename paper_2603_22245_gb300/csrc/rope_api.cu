@@ -627,6 +627,10 @@ rope_status rope::score_topk_impl(const rope_index* idx, const float* emb_f32, c
   int32_t n_ranges = 1;  // candidate lists per read seen by the merge
   if (je > jb) {
     if ((st = plan_scan(idx, o.precision, n_reads, jb, je, o.n_ranges, c->num_sms, &pl)) != ROPE_OK) return st;
+    if (pl.tc && !scan_tc_fits(ix, o.cand_depth))
+      return fail(ROPE_ERR_UNSUPPORTED, "cand_depth=%d: the tensor-core scan's candidate lists at complex "
+                  "dimension %d and stride %d do not fit in shared memory; use a smaller cand_depth",
+                  o.cand_depth, ix.D, ix.stride);
     n_ranges = pl.a.n_ranges * pl.a.lists_per_range;
   }
   const size_t cand_bytes = (size_t)n_reads * n_ranges * o.cand_depth * sizeof(Candidate);
@@ -834,6 +838,10 @@ extern "C" rope_status rope_score_topk_noalloc(const rope_index* idx, const floa
   int32_t n_ranges = 1;  // candidate lists per read seen by the merge
   if (je > jb) {
     if ((st = plan_scan(idx, o.precision, n_reads, jb, je, o.n_ranges, num_sms, &pl)) != ROPE_OK) return st;
+    if (pl.tc && !scan_tc_fits(idx->ix, o.cand_depth))
+      return fail(ROPE_ERR_UNSUPPORTED, "cand_depth=%d: the tensor-core scan's candidate lists at complex "
+                  "dimension %d and stride %d do not fit in shared memory; use a smaller cand_depth",
+                  o.cand_depth, idx->ix.D, idx->ix.stride);
     const size_t lpr = (size_t)pl.a.lists_per_range;
     if ((size_t)pl.a.n_ranges * lpr * per_range > cap) {
       if (o.n_ranges > 0)

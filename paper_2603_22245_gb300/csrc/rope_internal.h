@@ -99,6 +99,8 @@ int scan_tc_max_stride();
 int scan_tc_lists_per_range(int D);
 uint64_t wait_limit_ns();
 cudaError_t launch_scan_tc(const DevIndex& ix, const ScanArgs& a, bool dense, int num_sms, cudaStream_t st);
+// whether the tensor-core scan's shared memory holds candidate lists of this depth
+int scan_tc_fits(const DevIndex& ix, int cand_depth);
 
 // rope_merge.cu
 cudaError_t launch_merge(const DevIndex& ix, const MergeArgs& a, cudaStream_t st);

@@ -55,7 +55,8 @@ __global__ void merge_kernel(DevIndex ix, MergeArgs a) {
       uint64_t best = 0;
       for (int e = lane; e < total; e += 32) {
         const Candidate c = cands[e];
-        if (c.win == kEmptyWin) continue;
+        if (c.win >= kUnusedWin) continue;  // empty entry, or the mark of an unused slot
+        if (cands[e - e % a.cand_depth].win == kUnusedWin) continue;  // rest of an unused slot
         const uint64_t key = cand_key(c.score, c.win);
         if (key < last && key > best) best = key;
       }

@@ -30,7 +30,7 @@
 
 namespace rope {
 
-template <int D_, int NT_, int T_, int STAGES_, int NB_, int LPC_, int HALVES_>
+template <int D_, int NT_, int T_, int STAGES_, int NB_, int LPC_, int HALVES_, bool ISOLATE_MMA_>
 struct TcShape {
   static constexpr int D = D_, NT = NT_, T = T_, STAGES = STAGES_, NB = NB_;  // NB: most B ring slots
   static constexpr int A = kAnchorPeriod;
@@ -41,10 +41,17 @@ struct TcShape {
   static constexpr int HALVES = HALVES_;         // epilogue warps sharing one accumulator's columns
   static constexpr int WPH = T / HALVES;         // windows per epilogue warp per stage
   static constexpr int EPI_WARPS = 4 * NT * HALVES;
-  static constexpr int WARP_MMA = EPI_WARPS;
+  static constexpr int EPI_THREADS = 32 * EPI_WARPS;
+  static constexpr int WARP_MMA = EPI_WARPS;      // on scheduler 0 (EPI_WARPS is a multiple of 4)
   static constexpr int WARP_PROD = EPI_WARPS + 1;
   static constexpr int WARP_GEN0 = EPI_WARPS + 2;
-  static constexpr int NWARPS = EPI_WARPS + 2 + GEN_WARPS;
+  // With ISOLATE_MMA the warps after the producer whose number is a multiple
+  // of 4 stay idle, so that the single MMA-issuing thread shares scheduler 0
+  // with the epilogue warps only and gets its instructions issued promptly.
+  static constexpr bool ISOLATE_MMA = ISOLATE_MMA_;
+  __host__ __device__ static constexpr int idle_before(int w) { return ISOLATE_MMA ? (w - 1) / 4 - (WARP_GEN0 - 1) / 4 : 0; }
+  __host__ __device__ static constexpr int nwarps_for(int w) { return (w - WARP_GEN0) - idle_before(w) >= GEN_WARPS ? w : nwarps_for(w + 1); }
+  static constexpr int NWARPS = nwarps_for(WARP_GEN0);
   static constexpr int NTHREADS = 32 * NWARPS;
   static constexpr int SUP = T * A;                   // windows per super-tile
   static constexpr int GROUP = NT * 128;              // reads per work item
@@ -145,7 +152,12 @@ __global__ void __launch_bounds__(Sh::NTHREADS, 1) scan_tc_kernel(DevIndex ix, S
   __syncthreads();
   tc_fence_after();
   const uint32_t tbase = tmem_base_s;
-  const int n_items = a.n_groups * a.n_ranges;
+  // items (read group, window range) in group-major order; each block takes a
+  // contiguous run, so consecutive items of one group reuse the A operand and
+  // keep one candidate list per read across their ranges
+  const int64_t n_items = (int64_t)a.n_groups * a.n_ranges;
+  const int64_t it_lo = n_items * blockIdx.x / gridDim.x;
+  const int64_t it_hi = n_items * (blockIdx.x + 1) / gridDim.x;
 
   if (warp < Sh::EPI_WARPS) {
     // ================================================================ epilogue
@@ -162,9 +174,18 @@ __global__ void __launch_bounds__(Sh::NTHREADS, 1) scan_tc_kernel(DevIndex ix, S
     const uint32_t lane_base = (uint32_t)(32 * q) << 16;
     uint8_t* arow_base = a_tiles + tile * Sh::A_TILE_BYTES;
     uint32_t gs = 0;
-    for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
-      const int grp = item % a.n_groups;
-      const int rng = item / a.n_groups;
+    int prev_grp = -1;     // read group of the list being kept
+    int seg_rng = 0;       // range whose slot receives that list
+    float thr = -INFINITY;  // worst kept score, kept in a register
+    int worst = 0;
+    // writes the kept list of read r to the slot of range rng
+    auto flush = [&](int64_t r, int rng) {
+      Candidate* out = a.cand + (((size_t)r * a.n_ranges + rng) * Sh::HALVES + h) * a.cand_depth;
+      for (int e = 0; e < a.cand_depth; ++e) out[e] = Candidate{ls[e * lstride], lw[e * lstride]};
+    };
+    for (int64_t item = it_lo; item < it_hi; ++item) {
+      const int grp = (int)(item / a.n_ranges);
+      const int rng = (int)(item % a.n_ranges);
       const int64_t r = (int64_t)grp * Sh::GROUP + rs;
       const bool have_read = r < a.n_reads;
       const int64_t st_begin = a.st0 + (int64_t)rng * a.range_len;
@@ -174,31 +195,42 @@ __global__ void __launch_bounds__(Sh::NTHREADS, 1) scan_tc_kernel(DevIndex ix, S
       // window numbers fit in 32 bits with room for a super-tile past the last
       // window (the index refuses W > 2^32 - 2^16)
       const uint32_t jlo = (uint32_t)j_lo, jhi = (uint32_t)j_hi;
-      // A operand (written by the h = 0 warps): this read's normalised BF16
-      // row, 16-byte chunks into the swizzled tile. The previous item's MMAs
-      // have all completed: this thread consumed every accumulator they wrote.
-      if (h == 0) {
-        const uint4* src = reinterpret_cast<const uint4*>(a.emb_bf16 + (have_read ? r : 0) * 2 * D);
-#pragma unroll
-        for (int c = 0; c < 2 * D / 8; ++c) {
-          const uint4 v = have_read ? __ldg(src + c) : make_uint4(0, 0, 0, 0);
-          const int kb = c >> 3;
-          *reinterpret_cast<uint4*>(arow_base + kb * Sh::A_KBLK_BYTES +
-                                    sw128_offset((uint32_t)arow, (uint32_t)((c & 7) * 16))) = v;
+      if (grp != prev_grp) {
+        // a new read group: hand over the previous group's list, load the A
+        // operand and start an empty list. The previous item's MMAs have all
+        // completed: this thread consumed every accumulator they wrote.
+        if (!kDense && prev_grp >= 0) {
+          const int64_t pr = (int64_t)prev_grp * Sh::GROUP + rs;
+          if (pr < a.n_reads) flush(pr, seg_rng);
         }
-        fence_proxy_async_smem();
+        if (h == 0) {
+          // this read's normalised BF16 row, 16-byte chunks into the swizzled tile
+          const uint4* src = reinterpret_cast<const uint4*>(a.emb_bf16 + (have_read ? r : 0) * 2 * D);
+#pragma unroll
+          for (int c = 0; c < 2 * D / 8; ++c) {
+            const uint4 v = have_read ? __ldg(src + c) : make_uint4(0, 0, 0, 0);
+            const int kb = c >> 3;
+            *reinterpret_cast<uint4*>(arow_base + kb * Sh::A_KBLK_BYTES +
+                                      sw128_offset((uint32_t)arow, (uint32_t)((c & 7) * 16))) = v;
+          }
+          fence_proxy_async_smem();
+        }
+        thr = -INFINITY;
+        worst = 0;
+        if (!kDense) {
+          for (int e = 0; e < a.cand_depth; ++e) {
+            ls[e * lstride] = -INFINITY;
+            lw[e * lstride] = kEmptyWin;
+          }
+        }
+        prev_grp = grp;
+        seg_rng = rng;
+      } else if (!kDense && have_read) {
+        // the list carries on: this range's own slot holds no list
+        a.cand[(((size_t)r * a.n_ranges + rng) * Sh::HALVES + h) * a.cand_depth].win = kUnusedWin;
       }
       __syncwarp();
       if (lane == 0) mbar_arrive(&bar_aready);
-      // empty list; thr = the worst kept score, kept in a register
-      float thr = -INFINITY;
-      int worst = 0;
-      if (!kDense) {
-        for (int e = 0; e < a.cand_depth; ++e) {
-          ls[e * lstride] = -INFINITY;
-          lw[e * lstride] = kEmptyWin;
-        }
-      }
       for (int64_t sti = 0; sti < n_st; ++sti) {
         const uint32_t st = (uint32_t)(st_begin + sti * Sh::SUP);
         for (int i = 0; i < A; ++i, ++gs) {
@@ -210,9 +242,10 @@ __global__ void __launch_bounds__(Sh::NTHREADS, 1) scan_tc_kernel(DevIndex ix, S
           const bool full = jbase >= jlo && jbase + (uint32_t)((T - 1) * A) < jhi;
 #pragma unroll
           for (int c0 = h * Sh::WPH; c0 < (h + 1) * Sh::WPH; c0 += 16) {
+            const uint32_t taddr = tbase + lane_base + col + c0;
             uint32_t vr[16], vi[16];
-            tmem_ld16(tbase + lane_base + col + c0, vr);
-            tmem_ld16(tbase + lane_base + col + T + c0, vi);
+            tmem_ld16(taddr, vr);
+            tmem_ld16(taddr + T, vi);
             tc_wait_ld();
             if (c0 + 16 == (h + 1) * Sh::WPH) {
               // this warp's last chunk is in registers: hand the accumulator back
@@ -249,11 +282,23 @@ __global__ void __launch_bounds__(Sh::NTHREADS, 1) scan_tc_kernel(DevIndex ix, S
                 }
               }
               if (have_read && mx >= thr) {
+                // rare: the windows of this chunk at or above the threshold, in
+                // column order, each offered to the out-of-line list update
+                uint32_t pass = 0;
 #pragma unroll
                 for (int n = 0; n < 16; ++n) {
                   const uint32_t j = jc + (uint32_t)(n * A);
-                  if (j >= jlo && j < jhi && sc[n] >= thr) {
-                    const ListState ns = list_insert(ls, lw, lstride, a.cand_depth, worst, sc[n], j, a.sep, S);
+                  pass |= (j >= jlo && j < jhi && sc[n] >= thr) ? (1u << n) : 0u;
+                }
+                while (pass) {
+                  const int n = __ffs(pass) - 1;
+                  pass &= pass - 1;
+                  float v = sc[0];
+#pragma unroll
+                  for (int k2 = 1; k2 < 16; ++k2) v = n == k2 ? sc[k2] : v;
+                  if (v >= thr) {
+                    const ListState ns =
+                        list_insert(ls, lw, lstride, a.cand_depth, worst, v, jc + (uint32_t)(n * A), a.sep, S);
                     thr = ns.thr;
                     worst = ns.worst;
                   }
@@ -263,10 +308,10 @@ __global__ void __launch_bounds__(Sh::NTHREADS, 1) scan_tc_kernel(DevIndex ix, S
           }
         }
       }
-      if (!kDense && have_read) {
-        Candidate* out = a.cand + (((size_t)r * a.n_ranges + rng) * Sh::HALVES + h) * a.cand_depth;
-        for (int e = 0; e < a.cand_depth; ++e) out[e] = Candidate{ls[e * lstride], lw[e * lstride]};
-      }
+    }
+    if (!kDense && prev_grp >= 0) {
+      const int64_t pr = (int64_t)prev_grp * Sh::GROUP + rs;
+      if (pr < a.n_reads) flush(pr, seg_rng);
     }
   epi_done:;
   } else if (warp == Sh::WARP_MMA) {
@@ -276,8 +321,8 @@ __global__ void __launch_bounds__(Sh::NTHREADS, 1) scan_tc_kernel(DevIndex ix, S
       bool ok = true;
       const uint64_t a_desc0 = smem_desc_sw128(smem_u32(a_tiles));
       const uint64_t b_desc0 = smem_desc_sw128(smem_u32(b_ring));
-      for (int item = blockIdx.x; item < n_items && ok; item += gridDim.x, ++it) {
-        const int rng = item / a.n_groups;
+      for (int64_t item = it_lo; item < it_hi && ok; ++item, ++it) {
+        const int rng = (int)(item % a.n_ranges);
         const int64_t st_begin = a.st0 + (int64_t)rng * a.range_len;
         const int64_t j_hi = min(st_begin + a.range_len, a.je);
         const int64_t n_stage = (j_hi - st_begin + Sh::SUP - 1) / Sh::SUP * A;
@@ -318,8 +363,8 @@ __global__ void __launch_bounds__(Sh::NTHREADS, 1) scan_tc_kernel(DevIndex ix, S
     // ================================================================ bulk-copy producer
     if (lane == 0) {
       uint32_t g = 0;
-      for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
-        const int rng = item / a.n_groups;
+      for (int64_t item = it_lo; item < it_hi; ++item) {
+        const int rng = (int)(item % a.n_ranges);
         const int64_t st_begin = a.st0 + (int64_t)rng * a.range_len;
         const int64_t j_hi = min(st_begin + a.range_len, a.je);
         const int64_t n_st = (j_hi - st_begin + Sh::SUP - 1) / Sh::SUP;
@@ -340,9 +385,9 @@ __global__ void __launch_bounds__(Sh::NTHREADS, 1) scan_tc_kernel(DevIndex ix, S
       for (uint32_t h = (g >= 2 ? g - 2 : 0); h < g; ++h)
         mbar_wait(&bar_stfull[h & 1], (h >> 1) & 1, abort_flag, a.status, wlim);
     }
-  } else {
+  } else if (!Sh::ISOLATE_MMA || (warp & 3) != 0) {
     // ================================================================ window generators
-    const int gw = warp - Sh::WARP_GEN0;
+    const int gw = warp - Sh::WARP_GEN0 - Sh::idle_before(warp);
     const int chain = gw * Sh::CPW + lane / Sh::LPC;  // B row (Re) and column of its windows
     const int lic = lane % Sh::LPC;
     ChainB<BPL> ch;
@@ -366,8 +411,8 @@ __global__ void __launch_bounds__(Sh::NTHREADS, 1) scan_tc_kernel(DevIndex ix, S
       }
     }
     uint32_t g = 0, bslot = 0, bphase = 0;
-    for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
-      const int rng = item / a.n_groups;
+    for (int64_t item = it_lo; item < it_hi; ++item) {
+      const int rng = (int)(item % a.n_ranges);
       const int64_t st_begin = a.st0 + (int64_t)rng * a.range_len;
       const int64_t j_hi = min(st_begin + a.range_len, a.je);
       const int64_t n_st = (j_hi - st_begin + Sh::SUP - 1) / Sh::SUP;
@@ -459,11 +504,12 @@ __global__ void __launch_bounds__(Sh::NTHREADS, 1) scan_tc_kernel(DevIndex ix, S
 // ---------------------------------------------------------------- configurations
 
 // d = 64:  256 reads x 64 windows per stage, MMA N = 128; 16 epilogue warps (two
-//          per accumulator quarter), 8 generator warps (chains of 4 lanes x 8 entries)
-using TcShape32 = TcShape<32, 2, 64, 2, 4, 4, 2>;
+//          per accumulator quarter), 8 generator warps (chains of 4 lanes x 8
+//          entries), the MMA warp alone with epilogue warps on its scheduler.
+using TcShape32 = TcShape<32, 2, 64, 2, 4, 4, 2, true>;
 // d = 128: 256 reads x 64 windows per stage, MMA N = 128 (twice the tensor time
 //          per stage); 8 epilogue warps, 16 generator warps (chains of 8 lanes x 8 entries)
-using TcShape64 = TcShape<64, 2, 64, 2, 2, 8, 1>;
+using TcShape64 = TcShape<64, 2, 64, 2, 2, 8, 1, false>;
 
 constexpr size_t kTcSmemLimit = 227 * 1024;
 
@@ -498,6 +544,13 @@ static size_t tc_smem_bytes(const DevIndex& ix, int cand_depth, bool dense, int 
          L.inv_bytes + L.bins_bytes + lists;
 }
 
+int scan_tc_fits(const DevIndex& ix, int cand_depth) {
+  TcLaunch L;
+  if (ix.D == 32) return tc_smem_bytes<TcShape32>(ix, cand_depth, false, 1, &L) <= kTcSmemLimit;
+  if (ix.D == 64) return tc_smem_bytes<TcShape64>(ix, cand_depth, false, 1, &L) <= kTcSmemLimit;
+  return 0;
+}
+
 template <class Sh, bool kDense>
 static cudaError_t launch_tc(const DevIndex& ix, const ScanArgs& a, int num_sms, cudaStream_t st) {
   // the deepest B ring that fits (long windows at large strides and deep
@@ -510,8 +563,8 @@ static cudaError_t launch_tc(const DevIndex& ix, const ScanArgs& a, int num_sms,
   auto kern = scan_tc_kernel<Sh, kDense>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  const int n_items = a.n_groups * a.n_ranges;
-  int grid = num_sms < n_items ? num_sms : n_items;
+  const int64_t n_items = (int64_t)a.n_groups * a.n_ranges;
+  const int grid = (int)(num_sms < n_items ? num_sms : n_items);
   if (grid < 1) return cudaSuccess;
   kern<<<grid, Sh::NTHREADS, smem, st>>>(ix, a, L);
   return cudaGetLastError();

@@ -12,6 +12,10 @@
 namespace rope {
 
 constexpr uint32_t kEmptyWin = 0xFFFFFFFFu;
+// First entry of a candidate slot that holds no list: the tensor-core scan
+// keeps one list across consecutive ranges of a read group and writes it to
+// the slot of the first range; the later ranges' slots carry this mark.
+constexpr uint32_t kUnusedWin = 0xFFFFFFFEu;
 
 __device__ __forceinline__ bool cand_better(float s1, uint32_t j1, float s2, uint32_t j2) {
   return s1 > s2 || (s1 == s2 && j1 < j2);
@@ -37,17 +41,25 @@ struct ThreadList {
     thr = -INFINITY;
   }
 
+  // new worst entry: the lowest score, the highest window among equal scores;
+  // scores read 8 at a time so the loads' latencies overlap
   __device__ __forceinline__ void rescan() {
     int wi = 0;
-    float ws = S(0);
-    uint32_t ww = Wn(0);
-    for (int e = 1; e < depth; ++e) {
-      const float se = S(e);
-      const uint32_t we = Wn(e);
-      if (cand_better(ws, ww, se, we)) {
-        wi = e;
-        ws = se;
-        ww = we;
+    float ws = INFINITY;
+    uint32_t ww = 0;
+    for (int e0 = 0; e0 < depth; e0 += 8) {
+      float se[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) se[u] = e0 + u < depth ? S(e0 + u) : INFINITY;
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        if (se[u] > ws) continue;
+        const uint32_t we = Wn(e0 + u);
+        if (se[u] < ws || we > ww) {
+          wi = e0 + u;
+          ws = se[u];
+          ww = we;
+        }
       }
     }
     worst = wi;
