@@ -72,11 +72,13 @@ struct TcShape {
   static_assert(NTHREADS <= 1024, "block size");
 };
 
+constexpr int kMaxPhaseTab = 16 * 8;  // m * stride <= 16 * 8 (D <= 64 complex, t >= 1)
+
 struct TcLaunch {
   int32_t nb;              // B ring slots in use (1..NB, the most that fit in shared memory)
   int32_t words_per_slot;  // packed words staged per super-tile (multiple of 4)
   int32_t st_slot_bytes;   // bytes of one super-tile data slot
-  int32_t bins_bytes;      // bytes of the chain-interleaved bin arrays (stride 1)
+  int32_t bins_bytes;      // bytes of the bin arrays (per chain at stride 1, per location otherwise)
   int32_t inv_bytes;       // bytes of the chain-interleaved window norms
 };
 
@@ -103,6 +105,8 @@ __global__ void __launch_bounds__(Sh::NTHREADS, 1) scan_tc_kernel(DevIndex ix, S
   __shared__ __align__(8) uint64_t bar_afull[STAGES], bar_aempty[STAGES];
   __shared__ __align__(8) uint64_t bar_stfull[2], bar_stempty[2];
   __shared__ __align__(8) uint64_t bar_aready, bar_drain;
+  __shared__ __align__(8) uint64_t bar_gsync;  // generator warps, stride > 1 super-tile bins
+  __shared__ float2 e_tab[2][kMaxPhaseTab];     // leaving / entering phases [band * S + u]
   __shared__ uint32_t tmem_base_s;
   __shared__ int abort_s;
 
@@ -140,9 +144,14 @@ __global__ void __launch_bounds__(Sh::NTHREADS, 1) scan_tc_kernel(DevIndex ix, S
       mbar_init(&bar_stempty[i], Sh::GEN_WARPS);
     }
     mbar_init(&bar_aready, Sh::EPI_WARPS);
+    mbar_init(&bar_gsync, Sh::GEN_WARPS * 32);
     mbar_init(&bar_drain, 1);
     abort_s = 0;
     fence_barrier_init();
+  }
+  for (int q = tid; q < ix.m * S; q += Sh::NTHREADS) {
+    e_tab[0][q] = ix.eout[q];
+    e_tab[1][q] = ix.ein[q];
   }
   if (warp == Sh::WARP_MMA) {
     tmem_alloc(&tmem_base_s, Sh::TMEM_COLS);
@@ -410,7 +419,13 @@ __global__ void __launch_bounds__(Sh::NTHREADS, 1) scan_tc_kernel(DevIndex ix, S
         off_im_cr[pc] = off(T + chain, e_hi);
       }
     }
-    uint32_t g = 0, bslot = 0, bphase = 0;
+    uint32_t g = 0, bslot = 0, bphase = 0, gsp = 0;
+    // all generator threads meet (bounded wait) around the stride > 1 bin fill
+    auto gen_sync = [&]() -> bool {
+      mbar_arrive(&bar_gsync);
+      return mbar_wait_warp(&bar_gsync, (gsp++) & 1, abort_flag, a.status, wlim);
+    };
+    const int in_off = ix.N - ix.s + 1;  // entering location relative to the leaving one
     for (int64_t item = it_lo; item < it_hi; ++item) {
       const int rng = (int)(item % a.n_ranges);
       const int64_t st_begin = a.st0 + (int64_t)rng * a.range_len;
@@ -432,6 +447,16 @@ __global__ void __launch_bounds__(Sh::NTHREADS, 1) scan_tc_kernel(DevIndex ix, S
             bins_t[u * T + chain] = (uint8_t)bin_staged(words, word0, p_out0 + u, ix.s, ix.map_lsb);
             bins_t[(A + u) * T + chain] = (uint8_t)bin_staged(words, word0, p_in0 + u, ix.s, ix.map_lsb);
           }
+        }
+        if (S > 1) {
+          // the bins of every location of the super-tile, each computed once
+          // and shared by all chains (the previous super-tile's are all used)
+          if (!gen_sync()) goto gen_done;
+          const int n_pos = Sh::SUP * S + in_off;
+          const int64_t pos0 = st * S;
+          for (int t = gw * 32 + lane; t < n_pos; t += Sh::GEN_WARPS * 32)
+            bins_t[t] = (uint8_t)bin_staged(words, word0, pos0 + t, ix.s, ix.map_lsb);
+          if (!gen_sync()) goto gen_done;
         }
         ch.load(ix.anchors + a_idx * D, lic);
         __syncwarp();
@@ -476,11 +501,12 @@ __global__ void __launch_bounds__(Sh::NTHREADS, 1) scan_tc_kernel(DevIndex ix, S
           if (S == 1) {
             ch.step1(bins_t[i * T + chain], bins_t[(A + i) * T + chain]);
           } else {
-            const int64_t po = p_out0 + (int64_t)i * S;
+            const int base = (chain * A + i) * S;
+            const float2* eo = e_tab[0] + ch.band * S;
+            const float2* ei = e_tab[1] + ch.band * S;
             for (int u = 0; u < S; ++u) {
-              ch.sub_at(bin_staged(words, word0, po + u, ix.s, ix.map_lsb), ix.eout[ch.band * S + u]);
-              ch.add_at(bin_staged(words, word0, po + ix.N - ix.s + 1 + u, ix.s, ix.map_lsb),
-                        ix.ein[ch.band * S + u]);
+              ch.sub_at(bins_t[base + u], eo[u]);
+              ch.add_at(bins_t[base + in_off + u], ei[u]);
             }
             ch.rotate();
           }
@@ -511,7 +537,21 @@ using TcShape32 = TcShape<32, 2, 64, 2, 4, 4, 2, true>;
 //          per stage); 8 epilogue warps, 16 generator warps (chains of 8 lanes x 8 entries)
 using TcShape64 = TcShape<64, 2, 64, 2, 2, 8, 1, false>;
 
-constexpr size_t kTcSmemLimit = 227 * 1024;
+// Dynamic shared memory one block of this kernel may take: the device's
+// opt-in maximum per block less the kernel's static shared memory (barriers,
+// phase tables). 0 if the attributes cannot be read.
+template <class Sh, bool kDense>
+static size_t tc_dyn_limit() {
+  int dev = 0, optin = 0;
+  cudaFuncAttributes fa{};
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess ||
+      cudaFuncGetAttributes(&fa, scan_tc_kernel<Sh, kDense>) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return optin > (int)fa.sharedSizeBytes ? (size_t)optin - fa.sharedSizeBytes : 0;
+}
 
 int scan_tc_supported(int D) { return D == 32 || D == 64; }
 
@@ -537,7 +577,9 @@ static size_t tc_smem_bytes(const DevIndex& ix, int cand_depth, bool dense, int 
   slot = (slot + 127) & ~int64_t(127);
   L.st_slot_bytes = (int32_t)slot;
   L.inv_bytes = Sh::A * Sh::T * 4;
-  L.bins_bytes = S == 1 ? (int32_t)(Sh::T * 2 * Sh::A) : 0;
+  // stride 1: per-chain bins, chain-interleaved; stride > 1: one bin per
+  // location of the super-tile, shared by the chains
+  L.bins_bytes = S == 1 ? (int32_t)(Sh::T * 2 * Sh::A) : (int32_t)((Sh::SUP * S + ix.N - ix.s + 1 + 15) & ~15);
   const size_t lists = dense ? 0 : (size_t)cand_depth * Sh::GROUP * Sh::HALVES * 8;
   if (Lout) *Lout = L;
   return 1024 + (size_t)Sh::NT * Sh::A_TILE_BYTES + (size_t)nb * Sh::B_SLOT_BYTES + 2 * (size_t)L.st_slot_bytes +
@@ -546,8 +588,8 @@ static size_t tc_smem_bytes(const DevIndex& ix, int cand_depth, bool dense, int 
 
 int scan_tc_fits(const DevIndex& ix, int cand_depth) {
   TcLaunch L;
-  if (ix.D == 32) return tc_smem_bytes<TcShape32>(ix, cand_depth, false, 1, &L) <= kTcSmemLimit;
-  if (ix.D == 64) return tc_smem_bytes<TcShape64>(ix, cand_depth, false, 1, &L) <= kTcSmemLimit;
+  if (ix.D == 32) return tc_smem_bytes<TcShape32>(ix, cand_depth, false, 1, &L) <= tc_dyn_limit<TcShape32, false>();
+  if (ix.D == 64) return tc_smem_bytes<TcShape64>(ix, cand_depth, false, 1, &L) <= tc_dyn_limit<TcShape64, false>();
   return 0;
 }
 
@@ -556,13 +598,17 @@ static cudaError_t launch_tc(const DevIndex& ix, const ScanArgs& a, int num_sms,
   // the deepest B ring that fits (long windows at large strides and deep
   // candidate lists leave room for fewer slots)
   TcLaunch L;
+  const size_t limit = tc_dyn_limit<Sh, kDense>();
   int nb = Sh::NB;
   size_t smem = tc_smem_bytes<Sh>(ix, a.cand_depth, kDense, nb, &L);
-  while (smem > kTcSmemLimit && nb > 1) smem = tc_smem_bytes<Sh>(ix, a.cand_depth, kDense, nb >>= 1, &L);
-  if (smem > kTcSmemLimit) return cudaErrorInvalidValue;
+  while (smem > limit && nb > 1) smem = tc_smem_bytes<Sh>(ix, a.cand_depth, kDense, nb >>= 1, &L);
+  if (smem > limit) return cudaErrorInvalidValue;
   auto kern = scan_tc_kernel<Sh, kDense>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
+  if (e != cudaSuccess) {
+    cudaGetLastError();  // not sticky: leave no pending error for later launches
+    return e;
+  }
   const int64_t n_items = (int64_t)a.n_groups * a.n_ranges;
   const int grid = (int)(num_sms < n_items ? num_sms : n_items);
   if (grid < 1) return cudaSuccess;
