@@ -264,14 +264,18 @@ rope_status rope_levenshtein(const rope_index* idx, const uint8_t* seqs, const i
                              const int64_t* read_idx, const int64_t* win_start, int64_t n_pairs, int32_t* out_ld,
                              float* out_frac, cudaStream_t stream);
 
-/* Feature rows X [n_reads * K, F], F = K + 2 + m, for each read's K candidates
+/* Feature rows X [n_reads * K, F], F = K + 6 + m, for each read's K candidates
  * (cand_win/cand_score [n_reads, K] from rope_score_topk, best first):
  * the read's K scores (missing = 0), the candidate's fidelity, its m per-band
- * fidelities (§2.5, FP32 direct sums), and rank / K. Rows of missing
- * candidates (start -1) are zero. */
-rope_status rope_rerank_features(const rope_index* idx, const float* emb_f32, const float* norms,
-                                 const int64_t* cand_win, const float* cand_score, int64_t n_reads, int32_t K,
-                                 float* X, cudaStream_t stream);
+ * fidelities (§2.5, FP32 direct sums), rank / K, and four Hamming fingerprint
+ * fidelities ((n - d)/n)^2 (§1) of the read head (seqs/offsets, the reads the
+ * embeddings were made from): against the window, the best against the
+ * windows shifted by -4..4 letters (letters outside the reference mismatch),
+ * and of the head's first and second halves against the window's. Rows of
+ * missing candidates (start -1) are zero. */
+rope_status rope_rerank_features(const rope_index* idx, const uint8_t* seqs, const int64_t* offsets,
+                                 const float* emb_f32, const float* norms, const int64_t* cand_win,
+                                 const float* cand_score, int64_t n_reads, int32_t K, float* X, cudaStream_t stream);
 
 /* Per read, the `keep` of its K candidates with the smallest pred (ties: higher
  * score, then lower start); out_* [n_reads, keep], missing (-1, -inf, +inf). */

@@ -291,3 +291,69 @@ def adamw(p, g, m, v, step, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, wd=0.01):
         assert a.dtype == np.float64 and a.flags.c_contiguous
     g = np.ascontiguousarray(g, dtype=np.float64)
     _load().oracle_adamw(_p(p), _p(g), _p(m), _p(v), len(p), step, lr, beta1, beta2, eps, wd)
+
+
+# ------------------------------------------------------------ reranker features
+
+RERANK_SHIFT = 4  # largest letter shift of the shifted Hamming feature
+
+
+def rerank_features(ref, seqs, offsets, cand_win, cand_score, p: Params) -> np.ndarray:
+    """Feature rows [n*K, K + 6 + m] of the learned reranker for each read's K
+    candidates, straight from the definitions (small inputs only):
+
+      [0, K)      the read's K candidate scores as given (0 where missing)
+      K           the candidate's own score as given
+      K+1 .. K+m  the fidelity of band k alone (§2.4 restricted to band k, §2.5)
+                  between the read head and the window, FP64 direct sums
+      K+1+m       rank / K
+      K+2+m       Hamming fingerprint fidelity ((n - d)/n)^2 (§1) of the read
+                  head against the window
+      K+3+m       its maximum over the windows starting -4..4 letters away
+                  (letters outside the reference count as mismatches)
+      K+4+m,K+5+m the same fidelity of the head's first floor(N/2) letters and
+                  of the remaining letters against the window's
+
+    Rows of missing candidates (start -1) are zero. The network these rows
+    feed has no counterpart in the paper; the fidelities it is built from do.
+    """
+    ref = _u8(ref)
+    seqs = _u8(seqs)
+    cand_win = np.asarray(cand_win)
+    cand_score = np.asarray(cand_score, dtype=np.float64)
+    n, K = cand_win.shape
+    m, N, nb = p.m, p.N, p.dim // p.m
+    F = K + 6 + m
+    L = len(ref)
+    X = np.zeros((n * K, F))
+    for r in range(n):
+        head = seqs[offsets[r]:offsets[r] + N]
+        x = embed(head, p)
+        for c in range(K):
+            w = int(cand_win[r, c])
+            if w < 0:
+                continue
+            row = X[r * K + c]
+            for f in range(K):
+                row[f] = cand_score[r, f] if cand_win[r, f] >= 0 else 0.0
+            row[K] = cand_score[r, c]
+            y = embed(ref[w:w + N], p)
+            for k in range(m):
+                row[K + 1 + k] = fidelity(x[k * nb:(k + 1) * nb], y[k * nb:(k + 1) * nb])
+            row[K + 1 + m] = c / K
+
+            def window(start):
+                out = np.full(N, ord("N"), dtype=np.uint8)
+                lo, hi = max(start, 0), min(start + N, L)
+                if hi > lo:
+                    out[lo - start:hi - start] = ref[lo:hi]
+                return out
+
+            win = window(w)
+            row[K + 2 + m] = hamming_fingerprint_fidelity(head, win)
+            row[K + 3 + m] = max(hamming_fingerprint_fidelity(head, window(w + d))
+                                 for d in range(-RERANK_SHIFT, RERANK_SHIFT + 1))
+            n1 = N // 2
+            row[K + 4 + m] = hamming_fingerprint_fidelity(head[:n1], win[:n1])
+            row[K + 5 + m] = hamming_fingerprint_fidelity(head[n1:], win[n1:])
+    return X

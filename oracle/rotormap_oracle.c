@@ -236,17 +236,20 @@ double oracle_fidelity_per_band(const double* xr, const double* xi, const double
 }
 
 /* Hamming quantum fingerprint (§1): |Q(S)> = n^{-1/2} sum_i |i>|S_i>, built
- * explicitly as an (n*4)-dimensional real vector; returns |<Q(S)|Q(T)>|^2. */
+ * explicitly as an (n*5)-dimensional real vector over the alphabet
+ * {A, C, G, T, other}: any letter outside ACGT takes the fifth slot; returns
+ * |<Q(S)|Q(T)>|^2. */
 double oracle_hamming_fingerprint_fidelity(const uint8_t* S, const uint8_t* T, int n) {
-  double* qs = (double*)calloc((size_t)n * 4, sizeof(double));
-  double* qt = (double*)calloc((size_t)n * 4, sizeof(double));
+  double* qs = (double*)calloc((size_t)n * 5, sizeof(double));
+  double* qt = (double*)calloc((size_t)n * 5, sizeof(double));
   double norm = 1.0 / sqrt((double)n);
   for (int i = 0; i < n; ++i) {
-    qs[i * 4 + oracle_base(S[i])] = norm;
-    qt[i * 4 + oracle_base(T[i])] = norm;
+    const int a = oracle_base(S[i]), b = oracle_base(T[i]);
+    qs[i * 5 + (a < 0 ? 4 : a)] = norm;
+    qt[i * 5 + (b < 0 ? 4 : b)] = norm;
   }
   double ip = 0;
-  for (int i = 0; i < n * 4; ++i) ip += qs[i] * qt[i];
+  for (int i = 0; i < n * 5; ++i) ip += qs[i] * qt[i];
   free(qs);
   free(qt);
   return ip * ip;

@@ -117,8 +117,11 @@ struct MlpWeights {
 cudaError_t launch_levenshtein(const uint32_t* packed, const uint8_t* seqs, const int64_t* offsets,
                                const int64_t* read_idx, const int64_t* win_start, int64_t n_pairs, int N, int32_t* out,
                                cudaStream_t st);
-cudaError_t launch_features(const DevIndex& ix, const float* emb_f32, const float* norms, const int64_t* cand_win,
-                            const float* cand_score, int64_t n_reads, int K, int F, float* X, cudaStream_t st);
+// kShift: largest letter shift of the Hamming features
+constexpr int kShift = 4;
+cudaError_t launch_features(const DevIndex& ix, const uint8_t* seqs, const int64_t* offsets, const float* emb_f32,
+                            const float* norms, const int64_t* cand_win, const float* cand_score, int64_t n_reads,
+                            int K, int F, float* X, cudaStream_t st);
 cudaError_t launch_mlp_forward(const MlpWeights& w, const float* X, const int64_t* idx, int64_t B, float* y, float* pre,
                                const float* t, float* dy, float* sq, cudaStream_t st);
 cudaError_t launch_mlp_backward(const MlpWeights& w, const float* X, const int64_t* idx, int64_t B, const float* pre,

@@ -107,7 +107,13 @@ cudaError_t launch_levenshtein(const uint32_t* packed, const uint8_t* seqs, cons
 //   K+m+1        rank / K
 // One warp per read; each candidate window is summed directly in FP32
 // (location order), as the re-scoring does. Missing candidates get a zero row.
-__global__ void features_kernel(DevIndex ix, const float* __restrict__ emb_f32, const float* __restrict__ norms,
+// letter (0..3) at reference position p, or 4 outside [0, L)
+__device__ __forceinline__ uint32_t ref_letter(const uint32_t* __restrict__ packed, int64_t L, int64_t p) {
+  return (p >= 0 && p < L) ? (packed[p >> 4] >> ((p & 15) * 2)) & 3u : 4u;
+}
+
+__global__ void features_kernel(DevIndex ix, const uint8_t* __restrict__ seqs, const int64_t* __restrict__ offsets,
+                                const float* __restrict__ emb_f32, const float* __restrict__ norms,
                                 const int64_t* __restrict__ cand_win, const float* __restrict__ cand_score,
                                 int64_t n_reads, int K, int F, float* __restrict__ X) {
   extern __shared__ float2 feat_acc[];
@@ -167,24 +173,59 @@ __global__ void features_kernel(DevIndex ix, const float* __restrict__ emb_f32, 
         const float sc = cand_score[r * K + f];
         row[f] = cand_win[r * K + f] >= 0 ? sc : 0.f;
       }
-      if (lane == 0) {
-        row[K] = cand_score[r * K + c];
-        row[K + 1 + ix.m] = (float)c / (float)K;
+      // Hamming fingerprint fidelities ((n - d) / n)^2 (§1) of the read head
+      // against the window and the windows shifted by up to kShift letters
+      // (letters outside the reference count as mismatches), and of the two
+      // halves of the head at no shift
+      {
+        const uint8_t* head = seqs + offsets[r];
+        const int N = ix.N, n1 = N / 2;
+        int mm[2 * kShift + 1], mm1 = 0;
+#pragma unroll
+        for (int d = 0; d <= 2 * kShift; ++d) mm[d] = 0;
+        for (int i = lane; i < N; i += 32) {
+          const uint32_t q = letter_code(head[i]);
+#pragma unroll
+          for (int d = 0; d <= 2 * kShift; ++d) mm[d] += q != ref_letter(ix.packed, ix.L, w0 + i + d - kShift);
+          if (i < n1) mm1 += q != ref_letter(ix.packed, ix.L, w0 + i);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+          for (int d = 0; d <= 2 * kShift; ++d) mm[d] += __shfl_xor_sync(0xffffffffu, mm[d], o);
+          mm1 += __shfl_xor_sync(0xffffffffu, mm1, o);
+        }
+        if (lane == 0) {
+          auto hf = [](int n, int d) {
+            const float v = (float)(n - d) / (float)n;
+            return v * v;
+          };
+          float best = 0.f;
+#pragma unroll
+          for (int d = 0; d <= 2 * kShift; ++d) best = fmaxf(best, hf(N, mm[d]));
+          row[K] = cand_score[r * K + c];
+          row[K + 1 + ix.m] = (float)c / (float)K;
+          row[K + 2 + ix.m] = hf(N, mm[kShift]);
+          row[K + 3 + ix.m] = best;
+          row[K + 4 + ix.m] = hf(n1, mm1);
+          row[K + 5 + ix.m] = hf(N - n1, mm[kShift] - mm1);
+        }
       }
-      for (int f = K + 2 + ix.m + lane; f < F; f += 32) row[f] = 0.f;
+      for (int f = K + 6 + ix.m + lane; f < F; f += 32) row[f] = 0.f;
       __syncwarp();
     }
   }
 }
 
-cudaError_t launch_features(const DevIndex& ix, const float* emb_f32, const float* norms, const int64_t* cand_win,
-                            const float* cand_score, int64_t n_reads, int K, int F, float* X, cudaStream_t st) {
+cudaError_t launch_features(const DevIndex& ix, const uint8_t* seqs, const int64_t* offsets, const float* emb_f32,
+                            const float* norms, const int64_t* cand_win, const float* cand_score, int64_t n_reads,
+                            int K, int F, float* X, cudaStream_t st) {
   if (n_reads <= 0) return cudaSuccess;
   const int wpb = 8;
   int64_t blocks = (n_reads + wpb - 1) / wpb;
   if (blocks > 152 * 32) blocks = 152 * 32;
   features_kernel<<<(unsigned)blocks, wpb * 32, (size_t)wpb * ix.D * sizeof(float2), st>>>(
-      ix, emb_f32, norms, cand_win, cand_score, n_reads, K, F, X);
+      ix, seqs, offsets, emb_f32, norms, cand_win, cand_score, n_reads, K, F, X);
   return cudaGetLastError();
 }
 

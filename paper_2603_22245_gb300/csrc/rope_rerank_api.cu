@@ -251,15 +251,18 @@ extern "C" rope_status rope_levenshtein(const rope_index* idx, const uint8_t* se
   return ROPE_OK;
 }
 
-extern "C" rope_status rope_rerank_features(const rope_index* idx, const float* emb_f32, const float* norms,
-                                            const int64_t* cand_win, const float* cand_score, int64_t n_reads,
-                                            int32_t K, float* X, cudaStream_t stream) {
+extern "C" rope_status rope_rerank_features(const rope_index* idx, const uint8_t* seqs, const int64_t* offsets,
+                                            const float* emb_f32, const float* norms, const int64_t* cand_win,
+                                            const float* cand_score, int64_t n_reads, int32_t K, float* X,
+                                            cudaStream_t stream) {
   if (!idx || n_reads < 0 || K < 1) return host_fail(ROPE_ERR_INVALID_ARG, "bad arguments");
   if (n_reads == 0) return ROPE_OK;
-  const int F = K + 2 + idx->ix.m;
-  if (F > kMaxFeatures) return host_fail(ROPE_ERR_INVALID_ARG, "K + 2 + m = %d > %d features", F, kMaxFeatures);
-  if (!emb_f32 || !norms || !cand_win || !cand_score || !X) return host_fail(ROPE_ERR_INVALID_ARG, "NULL pointer");
-  ROPE_HOST_CUDA(launch_features(idx->ix, emb_f32, norms, cand_win, cand_score, n_reads, K, F, X, stream));
+  const int F = K + 6 + idx->ix.m;
+  if (F > kMaxFeatures) return host_fail(ROPE_ERR_INVALID_ARG, "K + 6 + m = %d > %d features", F, kMaxFeatures);
+  if (!seqs || !offsets || !emb_f32 || !norms || !cand_win || !cand_score || !X)
+    return host_fail(ROPE_ERR_INVALID_ARG, "NULL pointer");
+  ROPE_HOST_CUDA(launch_features(idx->ix, seqs, offsets, emb_f32, norms, cand_win, cand_score, n_reads, K, F, X,
+                                 stream));
   return ROPE_OK;
 }
 
@@ -284,7 +287,7 @@ extern "C" rope_status rope_map_rerank(const rope_index* idx, const uint8_t* seq
   if (n_reads == 0) return ROPE_OK;
   if (!seqs || !offsets || !out_win || !out_score) return host_fail(ROPE_ERR_INVALID_ARG, "NULL pointer");
   const int D = idx->ix.D, m = idx->ix.m;
-  const int F = K + 2 + m;
+  const int F = K + 6 + m;
   if (rr && rr->F != F) return host_fail(ROPE_ERR_INVALID_ARG, "reranker takes %d features, k=%d gives %d", rr->F, K, F);
   DeviceCtx* c;
   rope_status st = host_ctx(&c);
@@ -307,7 +310,7 @@ extern "C" rope_status rope_map_rerank(const rope_index* idx, const uint8_t* seq
     st = rope_score_topk(idx, emb, embh, norms, n_reads, &o, cw, cs, stream);
   }
   if (st == ROPE_OK && rr) {
-    cudaError_t e = launch_features(idx->ix, emb, norms, cw, cs, n_reads, K, F, X, stream);
+    cudaError_t e = launch_features(idx->ix, seqs, offsets, emb, norms, cw, cs, n_reads, K, F, X, stream);
     if (e == cudaSuccess) e = launch_mlp_forward(rr->w, X, nullptr, n * K, pred, nullptr, nullptr, nullptr, nullptr, stream);
     if (e != cudaSuccess) st = host_fail(ROPE_ERR_CUDA, "rerank launch: %s", cudaGetErrorString(e));
   }

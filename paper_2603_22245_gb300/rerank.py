@@ -22,8 +22,8 @@ from . import rotormap as rm
 
 
 def n_features(K: int, m: int) -> int:
-    """Feature row width: K scores, own score, m per-band fidelities, rank."""
-    return K + 2 + m
+    """Feature row width: K scores, own score, m per-band fidelities, rank, 4 Hamming fidelities."""
+    return K + 6 + m
 
 
 class Reranker:
@@ -103,14 +103,15 @@ def rope_levenshtein(idx: rm.Index, seqs: torch.Tensor, offsets: torch.Tensor, r
     return ld, frac
 
 
-def rope_rerank_features(idx: rm.Index, emb_f32: torch.Tensor, norms: torch.Tensor, cand_win: torch.Tensor,
-                         cand_score: torch.Tensor) -> torch.Tensor:
-    """Feature rows [n_reads * K, K + 2 + m] of every (read, candidate)."""
+def rope_rerank_features(idx: rm.Index, seqs: torch.Tensor, offsets: torch.Tensor, emb_f32: torch.Tensor,
+                         norms: torch.Tensor, cand_win: torch.Tensor, cand_score: torch.Tensor) -> torch.Tensor:
+    """Feature rows [n_reads * K, K + 6 + m] of every (read, candidate)."""
     n, K = cand_win.shape
     F = n_features(K, idx.params.m)
     X = torch.empty((n * K, F), dtype=torch.float32, device="cuda")
-    rm._check(rm.load().rope_rerank_features(idx.handle, rm._ptr(emb_f32), rm._ptr(norms), rm._ptr(cand_win),
-                                             rm._ptr(cand_score), n, K, rm._ptr(X), rm._stream()))
+    rm._check(rm.load().rope_rerank_features(idx.handle, rm._ptr(seqs), rm._ptr(offsets), rm._ptr(emb_f32),
+                                             rm._ptr(norms), rm._ptr(cand_win), rm._ptr(cand_score), n, K,
+                                             rm._ptr(X), rm._stream()))
     return X
 
 
@@ -138,7 +139,7 @@ def training_set(idx: rm.Index, seqs: torch.Tensor, offsets: torch.Tensor, k: in
     p = idx.params
     f32, bf16, norms = rm.rope_encode_reads(p, seqs, offsets)
     win, score = rm.rope_score_topk(idx, f32, bf16, norms, k=k, sep=p.window_len, precision=precision)
-    X = rope_rerank_features(idx, f32, norms, win, score)
+    X = rope_rerank_features(idx, seqs, offsets, f32, norms, win, score)
     w_h = win.reshape(-1).cpu().numpy()
     vi = np.nonzero(w_h >= 0)[0].astype(np.int64)
     read_idx = torch.from_numpy(vi // k).cuda()

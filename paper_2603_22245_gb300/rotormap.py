@@ -72,7 +72,7 @@ EXPORTS = {
     "rope_reranker_save": ([_P, ctypes.c_char_p], ctypes.c_int),
     "rope_reranker_load": ([_P, ctypes.c_char_p], ctypes.c_int),
     "rope_levenshtein": ([_P, _P, _P, _P, _P, _I64, _P, _P, _P], ctypes.c_int),
-    "rope_rerank_features": ([_P, _P, _P, _P, _P, _I64, _I32, _P, _P], ctypes.c_int),
+    "rope_rerank_features": ([_P, _P, _P, _P, _P, _P, _P, _I64, _I32, _P, _P], ctypes.c_int),
     "rope_rerank_prune": ([_P, _P, _P, _I64, _I32, _I32, _P, _P, _P, _P], ctypes.c_int),
     "rope_map_rerank": ([_P, _P, _P, _I64, _P, _P, _I32, _P, _P, _P, _P], ctypes.c_int),
     "rope_ladder_lengths": ([_I32, _I32, _I32, _P, _I32], _I32),

@@ -490,3 +490,49 @@ def test_adamw_first_step_closed_form():
     oracle.adamw(p, g, m, v, 1, lr=1e-2, wd=0.1)
     assert np.allclose(p, p0 * (1 - 1e-3) - 1e-2 * np.sign(g), rtol=0, atol=1e-9)
     assert np.allclose(m, 0.1 * g) and np.allclose(v, 0.001 * g * g)
+
+
+# ---------------------------------------------------------------- reranker features (oracle)
+
+def test_rerank_features_pins():
+    """Feature rows: the Hamming fingerprint fidelities of §1 are 1 for an exact
+    copy, find a copy shifted by up to 4 letters, split into halves at N/2; the
+    band fidelities average to the per-band score of §2.5; missing rows are 0."""
+    ref = synth.uniform_ref(4000, 11)
+    p = oracle.Params(s=4, m=2, t=2, variant=1, N=150)
+    w = 1000
+    head_exact = ref[w:w + 150]
+    head_shift = ref[w + 3:w + 153]  # the window 3 letters further on
+    mut = head_exact.copy()
+    mut[10] = ord("A") if mut[10] != ord("A") else ord("C")  # one substitution in the first half
+    seqs = np.concatenate([head_exact, head_shift, mut])
+    offs = np.array([0, 150, 300, 450])
+    cw = np.array([[w, -1], [w, 200], [w, 3000]])
+    cs = np.array([[0.8, -np.inf], [0.7, 0.2], [0.6, 0.5]])
+    X = oracle.rerank_features(ref, seqs, offs, cw, cs, p)
+    K, m = 2, 2
+    assert X.shape == (6, K + 6 + m)
+    r0 = X[0]
+    one = pytest.approx(1.0, abs=1e-12)
+    assert r0[K + 2 + m] == one and r0[K + 3 + m] == one and r0[K + 4 + m] == one and r0[K + 5 + m] == one
+    assert np.all(r0[K + 1:K + 1 + m] == pytest.approx(1.0))
+    assert np.all(X[1] == 0)                                  # missing candidate
+    assert X[0, 1] == 0 and X[0, 0] == 0.8 and X[0, K] == 0.8  # scores, missing = 0
+    assert X[3, K + 1 + m] == 0.5                              # rank / K
+    r2 = X[2]
+    assert r2[K + 3 + m] == one and r2[K + 2 + m] < 0.7       # the shifted copy is found at d = +3
+    r4 = X[4]
+    assert r4[K + 2 + m] == pytest.approx((149 / 150) ** 2)
+    assert r4[K + 4 + m] == pytest.approx((74 / 75) ** 2) and r4[K + 5 + m] == one
+    # band fidelities average to the per-band score of the C oracle
+    x = oracle.embed(mut, p)
+    y = oracle.embed(ref[3000:3150], p)
+    assert X[5, K + 1:K + 1 + m].mean() == pytest.approx(oracle.fidelity_per_band(x, y, m), rel=1e-12)
+
+
+def test_hamming_fingerprint_other_letters():
+    """§1 fingerprint over {A, C, G, T, other}: a letter outside ACGT is one
+    more alphabet letter, so it mismatches every base."""
+    assert oracle.hamming_fingerprint_fidelity(b"ACGT", b"ACGN") == pytest.approx((3 / 4) ** 2)
+    assert oracle.hamming_fingerprint_fidelity(b"NNAC", b"GTAC") == pytest.approx((2 / 4) ** 2)
+    assert oracle.hamming_fingerprint_fidelity(b"ACGTACGT", b"TGCATGCA") == pytest.approx(0.0, abs=1e-15)

@@ -45,6 +45,41 @@ def test_levenshtein_bit_exact(lib, rr_mod, N):
     idx.free()
 
 
+# ---------------------------------------------------------------- feature rows
+
+@pytest.mark.parametrize("m", [2, 4])
+def test_features_match_oracle(lib, rr_mod, m):
+    """Feature rows against the FP64 oracle on seeded candidates (planted
+    loci, loci a few letters off, random loci, reference ends, missing)."""
+    ref = synth.markov_ref(60_000, 0.41, 7, 0.05, 0.05)
+    rd = synth.reads(ref, 40, seed=8, sub_rate=0.03, indel_rate=0.02)
+    p = lib.Params(s=4, m=m, t=2, variant=1, window_len=150)
+    op = oracle.Params(s=4, m=m, t=2, variant=1, N=150)
+    idx = lib.rope_encode_reference(p, torch.from_numpy(ref).cuda())
+    rng = np.random.default_rng(9)
+    K = 6
+    W = len(ref) - 150 + 1
+    cw = np.stack([rd.true_pos, rd.true_pos + rng.integers(-3, 4, rd.n), rng.integers(0, W, rd.n),
+                   np.zeros(rd.n, np.int64), np.full(rd.n, W - 1), np.full(rd.n, -1)], axis=1)
+    cw[:, 1] = np.clip(cw[:, 1], 0, W - 1)
+    cs = np.sort(rng.uniform(0, 1, (rd.n, K)), axis=1)[:, ::-1].copy()
+    cs[:, -1] = -np.inf
+    sd, od = torch.from_numpy(rd.seqs).cuda(), torch.from_numpy(rd.offsets).cuda()
+    f32, _, norms = lib.rope_encode_reads(p, sd, od, want_bf16=False)
+    X = rr_mod.rope_rerank_features(idx, sd, od, f32, norms, torch.from_numpy(cw).cuda(),
+                                    torch.from_numpy(cs.astype(np.float32)).cuda())
+    lib.rope_sync_status()
+    got = X.cpu().numpy().astype(np.float64)
+    want = oracle.rerank_features(ref, rd.seqs, rd.offsets, cw, cs.astype(np.float32), op)
+    assert got.shape == want.shape == (rd.n * K, K + 6 + m)
+    bands = slice(K + 1, K + 1 + m)
+    assert np.allclose(got[:, bands], want[:, bands], rtol=1e-5, atol=1e-6)
+    rest = np.ones(got.shape[1], bool)
+    rest[bands] = False
+    assert np.allclose(got[:, rest], want[:, rest], rtol=0, atol=1e-6)
+    idx.free()
+
+
 # ---------------------------------------------------------------- network parity
 
 def _random_net(rr_mod, F=20, H=128, seed=0):
@@ -149,7 +184,9 @@ def test_reranker_trains_and_prunes(lib, rr_mod):
     hit = lambda w: (np.abs(w.cpu().numpy() - tp[:, None]) < 150).any(axis=1).mean()
     r_rr, r_sc, r8 = hit(w_rr), hit(w_sc), hit(w8)
     print(f"true-locus recall: reranked top-2 {r_rr:.4f}, score top-2 {r_sc:.4f}, score top-8 {r8:.4f}")
-    assert r_rr >= r_sc - 0.005
+    # the network, given the Hamming fingerprint fidelities next to the RoPE
+    # fidelities, keeps the true locus more often than the score ranking
+    assert r_rr > r_sc + 0.005
     assert r8 >= r_sc
     rr.free()
     idx.free()
