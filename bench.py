@@ -64,6 +64,13 @@ WORKLOADS = {
         L=10_000_000, gc=0.41, tandem=0.025, segdup=0.025, inter=0.0, ref_seed=5,
         n_reads=200_000, read_len=2000, sigma=0.7, len_min=100, len_max=10000, sub=0.032, indel=0.048,
         read_seed=6, s=4, m=4, t=2, variant=1, N=100, stride=8, k=8, ladder=(100, 10000, 8)),
+    "markov20M": dict(
+        desc="20 Mbp order-2 Markov reference (GC 41%, 2.5% tandem repeats, 2.5% segmental duplicates), "
+             "32768 x 150 bp planted reads (1% sub, 0.5% indel geom p=0.7), d=64, N=150, stride 1, top-8 "
+             "(a one-batch case small enough for a full ncu capture of the scan)",
+        L=20_000_000, gc=0.41, tandem=0.025, segdup=0.025, inter=0.0, ref_seed=3,
+        n_reads=32768, read_len=150, sub=0.01, indel=0.005, read_seed=4,
+        s=4, m=2, t=2, variant=1, N=150, stride=1, k=8),
     "uniform100k": dict(
         desc="100 kbp uniform reference, 256 x 150 bp planted reads (1% sub, 0.5% indel), d=64, stride 1, top-8",
         L=100_000, gc=None, ref_seed=1, n_reads=256, read_len=150, sub=0.01, indel=0.005, read_seed=2,
