@@ -146,7 +146,7 @@ int oracle_embed(const uint8_t* seq, int N, int s, int m, int t, int variant, co
 }
 
 /*
- * The same vector in the matrix form of §2.11: sum over loc of
+ * The same vector in the matrix form of §2.10: sum over loc of
  *     D^loc (ones(m) (x) onehot(bin(mer(loc)))),
  * D = diag((w^{f_1},...,w^{f_m}) (x) ones(4^t)), w = exp(2 pi i / N).
  * D^loc is formed by repeated multiplication by D (loc matrix products of a
