@@ -418,6 +418,7 @@ def main():
     for i in range(args.warmup):
         step(i)
     rm.rope_sync_status()
+    tuned = rm.rope_autotune_query(idx, B, k=k)  # chosen during the first warm-up step
     rm.rope_profile_enable(args.steps)
     step_outs = [(torch.empty((B, k), dtype=torch.int64, device="cuda"),
                   torch.empty((B, k), dtype=torch.float32, device="cuda")) for _ in range(args.steps)]
@@ -536,7 +537,9 @@ def main():
         "config": {"workload": args.workload + ": " + wl["desc"], "reads_per_step_per_gpu": B, "n_windows": W,
                    "scores_per_step_per_gpu": scores_step, "l2": "inputs larger than L2 (0.8 GB index streamed "
                    "per scan pass; reads 20 MB/step)", "index_build_s": index_s, "parallelism": f"replicated index, "
-                   f"reads sharded over {ws} GPU(s)"},
+                   f"reads sharded over {ws} GPU(s)",
+                   "scan_tiles": None if tuned is None else {"variant": tuned[0], "items_per_sm": tuned[1],
+                                                              "tuning_sample_ms": tuned[2]}},
         "reads_per_s": reads_s, "top1_acc": acc_bf16, "fp32_plain": fp32,
         "speedup_vs_fp32_plain": value / ws / fp32["value"],
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "reranker": reranker, "gpu_launches": 3 * args.steps, "clocks": clocks,

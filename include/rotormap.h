@@ -203,6 +203,27 @@ rope_status rope_score_topk_noalloc(const rope_index* idx, const float* emb_f32,
                                     const float* norms, int64_t n_reads, const rope_score_opts* opts,
                                     int64_t* out_win, float* out_score, cudaStream_t stream);
 
+/* ---- tuner (no counterpart in the paper) --------------------------------
+ * The BF16 scan has tile variants and a free split of the work into
+ * (read group, window range) items. On the first BF16 rope_score_topk /
+ * rope_map call of a shape class (device, complex dimension, stride, window
+ * length and read groups rounded up to powers of two, cand_depth, sep on/off)
+ * with opts->n_ranges == 0, the library times each variant with 8, 16 and 32
+ * items per SM on a sample of that call's windows and reads (a few scans on
+ * at most a few hundred thousand windows) and keeps the fastest for the class;
+ * later calls of the class use it. Results do not depend on the choice.
+ * Tuning is on unless the environment sets ROPE_AUTOTUNE=0; the
+ * allocation-free entry point only reads earlier choices. */
+rope_status rope_autotune_enable(int32_t enabled);  /* 0 also forgets earlier choices */
+/* Records (variant, items per SM) for the class of (idx, n_reads, opts), as if
+ * tuned: later calls of the class use it. variant < 2 at d = 64, 0 at d = 128. */
+rope_status rope_autotune_set(const rope_index* idx, int64_t n_reads, const rope_score_opts* opts, int32_t variant,
+                              int32_t items_per_sm);
+/* The choice recorded for the class of (idx, n_reads, opts): tile variant,
+ * items per SM and the sample scan's time; ROPE_ERR_INVALID_ARG if none yet. */
+rope_status rope_autotune_query(const rope_index* idx, int64_t n_reads, const rope_score_opts* opts,
+                                int32_t* variant, int32_t* items_per_sm, float* sample_ms);
+
 /* Every score of every read against windows [j_begin, j_begin+count), as
  * n_reads x count floats, computed by the same scan kernel as rope_score_topk
  * (FP32 or BF16 tensor-core path) with its top-k stage replaced by a store.

@@ -7,6 +7,8 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <algorithm>
+#include <tuple>
 #include <cstdlib>
 #include <cstring>
 #include <map>
@@ -545,7 +547,7 @@ struct ScanPlan {
 };
 
 rope_status plan_scan(const rope_index* idx, int32_t precision, int64_t n_reads, int64_t jb, int64_t je,
-                      int32_t n_ranges_req, int num_sms, ScanPlan* out) {
+                      int32_t n_ranges_req, int num_sms, ScanPlan* out, int32_t tc_variant = 0) {
   const DevIndex& ix = idx->ix;
   ScanPlan pl;
   pl.tc = precision == ROPE_PREC_BF16;
@@ -581,7 +583,8 @@ rope_status plan_scan(const rope_index* idx, int32_t precision, int64_t n_reads,
   const int64_t sup_per_range = (n_sup + nr - 1) / nr;
   a.range_len = sup_per_range * sup;
   a.n_ranges = (int32_t)((n_sup + sup_per_range - 1) / sup_per_range);
-  a.lists_per_range = pl.tc ? scan_tc_lists_per_range(ix.D) : 1;
+  a.tc_variant = pl.tc ? tc_variant : 0;
+  a.lists_per_range = pl.tc ? scan_tc_lists_per_range(ix.D, a.tc_variant) : 1;
   a.wait_limit_ns = wait_limit_ns();
   *out = pl;
   return ROPE_OK;
@@ -599,6 +602,157 @@ rope_status check_opts(const rope_score_opts* o, rope_score_opts* v) {
   if (v->rescore_depth < v->k) v->rescore_depth = v->k;
   if (v->rescore_depth > 32) return fail(ROPE_ERR_INVALID_ARG, "rescore_depth > 32");
   if (v->rescore != 0 && v->rescore != 1) return fail(ROPE_ERR_INVALID_ARG, "rescore must be 0 or 1");
+  return ROPE_OK;
+}
+
+// ---------------------------------------------------------------- tuner
+//
+// The tensor-core scan has tile variants (scan_tc_variants) and a free work
+// split (read-group x window-range items per SM). On the first BF16 call for
+// a shape class (device, complex dimension, stride, window length and read
+// groups to the nearest power of two, candidate depth, sep on/off) the tuner
+// times every (variant, items per SM) pair on a sample of the call's own
+// windows with the call's own reads and keeps the fastest for that class. The
+// results of a scan do not depend on these choices (each window's score is
+// the same product; the merge takes the best entries of all lists), only its
+// speed does. ROPE_AUTOTUNE=0 (or rope_autotune_enable(0)) keeps the defaults.
+
+struct TuneKey {
+  int dev, D, stride, n_log2, g_log2, cand_depth, sep_on;
+  bool operator<(const TuneKey& o) const {
+    return std::tie(dev, D, stride, n_log2, g_log2, cand_depth, sep_on) <
+           std::tie(o.dev, o.D, o.stride, o.n_log2, o.g_log2, o.cand_depth, o.sep_on);
+  }
+};
+struct TuneVal {
+  int32_t variant = 0;
+  int32_t items_per_sm = 16;
+  float sample_ms = 0.f;
+};
+std::mutex g_tune_mu;
+std::map<TuneKey, TuneVal> g_tune;
+int g_autotune = -1;  // -1: from the environment on first use
+
+bool autotune_on() {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  if (g_autotune < 0) {
+    const char* e = getenv("ROPE_AUTOTUNE");
+    g_autotune = (e && e[0] == '0') ? 0 : 1;
+  }
+  return g_autotune == 1;
+}
+
+int ilog2_ceil(int64_t v) {
+  int r = 0;
+  while ((int64_t(1) << r) < v) ++r;
+  return r;
+}
+
+TuneKey tune_key(const rope_index* idx, int64_t n_reads, const rope_score_opts& o) {
+  const DevIndex& ix = idx->ix;
+  const int64_t groups = (n_reads + scan_tc_group(ix.D) - 1) / scan_tc_group(ix.D);
+  return TuneKey{idx->device, ix.D, ix.stride, ilog2_ceil(ix.N), ilog2_ceil(groups), o.cand_depth, o.sep > 0};
+}
+
+int32_t ranges_for(int items_per_sm, int num_sms, int64_t n_groups) {
+  const int64_t nr = ((int64_t)items_per_sm * num_sms + n_groups - 1) / n_groups;
+  return (int32_t)(nr < 1 ? 1 : nr > 4096 ? 4096 : nr);
+}
+
+// Times the candidates on windows [jb, jb + sample) and records the fastest.
+rope_status tune_tc(const rope_index* idx, const uint16_t* emb_bf16, const float* emb_f32, const float* norms,
+                    int64_t n_reads, int64_t jb, int64_t je, const rope_score_opts& o, DeviceCtx* c,
+                    cudaStream_t stream, TuneVal* best) {
+  const DevIndex& ix = idx->ix;
+  const int64_t sup = scan_tc_super_tile(ix.D);
+  const int64_t n_groups = (n_reads + scan_tc_group(ix.D) - 1) / scan_tc_group(ix.D);
+  static const int kItems[] = {8, 16, 32};
+  // enough super-tiles for the finest split to give every range one
+  const int64_t want_sup = std::max<int64_t>(64, ((int64_t)32 * c->num_sms + n_groups - 1) / n_groups);
+  const int64_t sample = std::min<int64_t>(je - jb, want_sup * sup);
+  size_t cand_bytes = 0;
+  for (int v = 0; v < scan_tc_variants(ix.D); ++v)
+    for (int items : kItems) {
+      const size_t b = (size_t)n_reads * ranges_for(items, c->num_sms, n_groups) * scan_tc_lists_per_range(ix.D, v) *
+                       o.cand_depth * sizeof(Candidate);
+      cand_bytes = std::max(cand_bytes, b);
+    }
+  Candidate* cand = nullptr;
+  rope_status st = pool_alloc(c, (void**)&cand, cand_bytes, stream);
+  if (st != ROPE_OK) return st;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  TuneVal b{0, 16, 1e30f};
+  bool any = false;
+  for (int v = 0; v < scan_tc_variants(ix.D) && st == ROPE_OK; ++v) {
+    if (!scan_tc_fits(ix, o.cand_depth, v)) continue;
+    for (int items : kItems) {
+      ScanPlan pl;
+      st = plan_scan(idx, ROPE_PREC_BF16, n_reads, jb, jb + sample, ranges_for(items, c->num_sms, n_groups),
+                     c->num_sms, &pl, v);
+      if (st != ROPE_OK) break;
+      pl.a.emb_f32 = emb_f32;
+      pl.a.emb_bf16 = emb_bf16;
+      pl.a.norms = norms;
+      pl.a.cand_depth = o.cand_depth;
+      pl.a.sep = o.sep;
+      pl.a.cand = cand;
+      pl.a.status = c->status;
+      float ms = 0.f;
+      cudaError_t e = cudaSuccess;
+      for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep) {  // the second launch is timed
+        cudaEventRecord(e0, stream);
+        e = launch_scan_tc(ix, pl.a, false, c->num_sms, stream);
+        cudaEventRecord(e1, stream);
+      }
+      if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+      if (e != cudaSuccess) {
+        st = fail(ROPE_ERR_CUDA, "tuning launch: %s", cudaGetErrorString(e));
+        break;
+      }
+      if (ms < b.sample_ms) b = TuneVal{v, items, ms};
+      any = true;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFreeAsync(cand, stream);
+  if (st == ROPE_OK && any) *best = b;
+  return st;
+}
+
+// The variant and range split of a BF16 scan: the tuned ones for its class
+// (tuned now if new and the call's n_ranges is 0), else the defaults.
+rope_status choose_tc(const rope_index* idx, const uint16_t* emb_bf16, const float* emb_f32, const float* norms,
+                      int64_t n_reads, int64_t jb, int64_t je, const rope_score_opts& o, DeviceCtx* c,
+                      cudaStream_t stream, bool may_tune, int32_t* variant, int32_t* n_ranges) {
+  *variant = 0;
+  *n_ranges = o.n_ranges;
+  if (!scan_tc_supported(idx->ix.D) || idx->ix.score_mode != 0 || idx->ix.stride > scan_tc_max_stride())
+    return ROPE_OK;  // plan_scan reports why
+  const TuneKey key = tune_key(idx, n_reads, o);
+  const int64_t n_groups = (n_reads + scan_tc_group(idx->ix.D) - 1) / scan_tc_group(idx->ix.D);
+  TuneVal val;
+  bool found;
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune.find(key);
+    found = it != g_tune.end();
+    if (found) val = it->second;
+  }
+  if (!found && may_tune && o.n_ranges == 0 && autotune_on()) {
+    rope_status st = tune_tc(idx, emb_bf16, emb_f32, norms, n_reads, jb, je, o, c, stream, &val);
+    if (st != ROPE_OK) return st;
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune[key] = val;
+    found = true;
+  }
+  if (found) {
+    *variant = val.variant;
+    if (o.n_ranges == 0) *n_ranges = ranges_for(val.items_per_sm, c->num_sms, n_groups);
+  }
   return ROPE_OK;
 }
 
@@ -626,8 +780,13 @@ rope_status rope::score_topk_impl(const rope_index* idx, const float* emb_f32, c
   Candidate* cand = nullptr;
   int32_t n_ranges = 1;  // candidate lists per read seen by the merge
   if (je > jb) {
-    if ((st = plan_scan(idx, o.precision, n_reads, jb, je, o.n_ranges, c->num_sms, &pl)) != ROPE_OK) return st;
-    if (pl.tc && !scan_tc_fits(ix, o.cand_depth))
+    int32_t variant = 0, nr_req = o.n_ranges;
+    if (o.precision == ROPE_PREC_BF16 &&
+        (st = choose_tc(idx, emb_bf16, emb_f32, norms, n_reads, jb, je, o, c, stream, true, &variant, &nr_req)) !=
+            ROPE_OK)
+      return st;
+    if ((st = plan_scan(idx, o.precision, n_reads, jb, je, nr_req, c->num_sms, &pl, variant)) != ROPE_OK) return st;
+    if (pl.tc && !scan_tc_fits(ix, o.cand_depth, variant))
       return fail(ROPE_ERR_UNSUPPORTED, "cand_depth=%d: the tensor-core scan's candidate lists at complex "
                   "dimension %d and stride %d do not fit in shared memory; use a smaller cand_depth",
                   o.cand_depth, ix.D, ix.stride);
@@ -673,6 +832,46 @@ rope_status rope::score_topk_impl(const rope_index* idx, const float* emb_f32, c
   prof_mark(prof_slot, 3, stream);
   cudaFreeAsync(cand, stream);
   if (e != cudaSuccess) return fail(ROPE_ERR_CUDA, "merge launch: %s", cudaGetErrorString(e));
+  return ROPE_OK;
+}
+
+extern "C" rope_status rope_autotune_enable(int32_t enabled) {
+  if (enabled != 0 && enabled != 1) return fail(ROPE_ERR_INVALID_ARG, "enabled must be 0 or 1");
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_autotune = enabled;
+  if (!enabled) g_tune.clear();
+  return ROPE_OK;
+}
+
+extern "C" rope_status rope_autotune_set(const rope_index* idx, int64_t n_reads, const rope_score_opts* opts,
+                                         int32_t variant, int32_t items_per_sm) {
+  if (!idx || !opts || n_reads < 1) return fail(ROPE_ERR_INVALID_ARG, "bad arguments");
+  rope_score_opts o;
+  rope_status st = check_opts(opts, &o);
+  if (st != ROPE_OK) return st;
+  if (!scan_tc_supported(idx->ix.D)) return fail(ROPE_ERR_UNSUPPORTED, "no tensor-core scan at this dimension");
+  if (variant < 0 || variant >= scan_tc_variants(idx->ix.D))
+    return fail(ROPE_ERR_INVALID_ARG, "variant %d outside [0, %d)", variant, scan_tc_variants(idx->ix.D));
+  if (items_per_sm < 1 || items_per_sm > 256) return fail(ROPE_ERR_INVALID_ARG, "items_per_sm outside [1, 256]");
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tune[tune_key(idx, n_reads, o)] = TuneVal{variant, items_per_sm, 0.f};
+  return ROPE_OK;
+}
+
+extern "C" rope_status rope_autotune_query(const rope_index* idx, int64_t n_reads, const rope_score_opts* opts,
+                                           int32_t* variant, int32_t* items_per_sm, float* sample_ms) {
+  if (!idx || !opts || n_reads < 1) return fail(ROPE_ERR_INVALID_ARG, "bad arguments");
+  rope_score_opts o;
+  rope_status st = check_opts(opts, &o);
+  if (st != ROPE_OK) return st;
+  if (!scan_tc_supported(idx->ix.D)) return fail(ROPE_ERR_UNSUPPORTED, "no tensor-core scan at this dimension");
+  const TuneKey key = tune_key(idx, n_reads, o);
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  auto it = g_tune.find(key);
+  if (it == g_tune.end()) return fail(ROPE_ERR_INVALID_ARG, "no tuned configuration for this shape class yet");
+  if (variant) *variant = it->second.variant;
+  if (items_per_sm) *items_per_sm = it->second.items_per_sm;
+  if (sample_ms) *sample_ms = it->second.sample_ms;
   return ROPE_OK;
 }
 
@@ -837,8 +1036,18 @@ extern "C" rope_status rope_score_topk_noalloc(const rope_index* idx, const floa
   ScanPlan pl;
   int32_t n_ranges = 1;  // candidate lists per read seen by the merge
   if (je > jb) {
-    if ((st = plan_scan(idx, o.precision, n_reads, jb, je, o.n_ranges, num_sms, &pl)) != ROPE_OK) return st;
-    if (pl.tc && !scan_tc_fits(idx->ix, o.cand_depth))
+    int32_t variant = 0, nr_req = o.n_ranges;
+    if (o.precision == ROPE_PREC_BF16) {
+      // an earlier tuned choice for this shape class, if any (never tunes here:
+      // tuning allocates)
+      DeviceCtx tmp{};
+      tmp.num_sms = num_sms;
+      if ((st = choose_tc(idx, emb_bf16, emb_f32, norms, n_reads, jb, je, o, &tmp, stream, false, &variant,
+                          &nr_req)) != ROPE_OK)
+        return st;
+    }
+    if ((st = plan_scan(idx, o.precision, n_reads, jb, je, nr_req, num_sms, &pl, variant)) != ROPE_OK) return st;
+    if (pl.tc && !scan_tc_fits(idx->ix, o.cand_depth, variant))
       return fail(ROPE_ERR_UNSUPPORTED, "cand_depth=%d: the tensor-core scan's candidate lists at complex "
                   "dimension %d and stride %d do not fit in shared memory; use a smaller cand_depth",
                   o.cand_depth, idx->ix.D, idx->ix.stride);
@@ -850,8 +1059,8 @@ extern "C" rope_status rope_score_topk_noalloc(const rope_index* idx, const floa
       if (lpr * per_range > cap)
         return fail(ROPE_ERR_INVALID_ARG, "n_reads=%lld needs %zu bytes of candidates; the allocation-free scratch "
                     "holds %zu", (long long)n_reads, lpr * per_range, cap);
-      if ((st = plan_scan(idx, o.precision, n_reads, jb, je, (int32_t)(cap / (lpr * per_range)), num_sms, &pl)) !=
-          ROPE_OK)
+      if ((st = plan_scan(idx, o.precision, n_reads, jb, je, (int32_t)(cap / (lpr * per_range)), num_sms, &pl,
+                          variant)) != ROPE_OK)
         return st;
     }
     n_ranges = pl.a.n_ranges * pl.a.lists_per_range;

@@ -533,6 +533,10 @@ __global__ void __launch_bounds__(Sh::NTHREADS, 1) scan_tc_kernel(DevIndex ix, S
 //          per accumulator quarter), 8 generator warps (chains of 4 lanes x 8
 //          entries), the MMA warp alone with epilogue warps on its scheduler.
 using TcShape32 = TcShape<32, 2, 64, 2, 4, 4, 2, true>;
+// d = 64, second tile variant: one epilogue warp per accumulator quarter and
+//          tile (8 warps, each reading all 64 windows of a stage; one candidate
+//          list per read), more registers per thread. Faster at large strides.
+using TcShape32b = TcShape<32, 2, 64, 2, 4, 4, 1, true>;
 // d = 128: 256 reads x 64 windows per stage, MMA N = 128 (twice the tensor time
 //          per stage); 8 epilogue warps, 16 generator warps (chains of 8 lanes x 8 entries)
 using TcShape64 = TcShape<64, 2, 64, 2, 2, 8, 1, false>;
@@ -561,8 +565,11 @@ int scan_tc_group(int D) { return D == 32 ? TcShape32::GROUP : D == 64 ? TcShape
 
 int scan_tc_max_stride() { return 8; }
 
-int scan_tc_lists_per_range(int D) {
-  return D == 32 ? TcShape32::HALVES : D == 64 ? TcShape64::HALVES : 1;
+int scan_tc_variants(int D) { return D == 32 ? 2 : D == 64 ? 1 : 0; }
+
+int scan_tc_lists_per_range(int D, int variant) {
+  if (D == 32) return variant == 1 ? TcShape32b::HALVES : TcShape32::HALVES;
+  return D == 64 ? TcShape64::HALVES : 1;
 }
 
 template <class Sh>
@@ -586,8 +593,10 @@ static size_t tc_smem_bytes(const DevIndex& ix, int cand_depth, bool dense, int 
          L.inv_bytes + L.bins_bytes + lists;
 }
 
-int scan_tc_fits(const DevIndex& ix, int cand_depth) {
+int scan_tc_fits(const DevIndex& ix, int cand_depth, int variant) {
   TcLaunch L;
+  if (ix.D == 32 && variant == 1)
+    return tc_smem_bytes<TcShape32b>(ix, cand_depth, false, 1, &L) <= tc_dyn_limit<TcShape32b, false>();
   if (ix.D == 32) return tc_smem_bytes<TcShape32>(ix, cand_depth, false, 1, &L) <= tc_dyn_limit<TcShape32, false>();
   if (ix.D == 64) return tc_smem_bytes<TcShape64>(ix, cand_depth, false, 1, &L) <= tc_dyn_limit<TcShape64, false>();
   return 0;
@@ -618,6 +627,8 @@ static cudaError_t launch_tc(const DevIndex& ix, const ScanArgs& a, int num_sms,
 
 cudaError_t launch_scan_tc(const DevIndex& ix, const ScanArgs& a, bool dense, int num_sms, cudaStream_t st) {
   if (ix.stride > scan_tc_max_stride()) return cudaErrorInvalidValue;
+  if (ix.D == 32 && a.tc_variant == 1)
+    return dense ? launch_tc<TcShape32b, true>(ix, a, num_sms, st) : launch_tc<TcShape32b, false>(ix, a, num_sms, st);
   if (ix.D == 32)
     return dense ? launch_tc<TcShape32, true>(ix, a, num_sms, st) : launch_tc<TcShape32, false>(ix, a, num_sms, st);
   if (ix.D == 64)

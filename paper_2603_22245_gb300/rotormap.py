@@ -75,6 +75,9 @@ EXPORTS = {
     "rope_rerank_features": ([_P, _P, _P, _P, _P, _P, _P, _I64, _I32, _P, _P], ctypes.c_int),
     "rope_rerank_prune": ([_P, _P, _P, _I64, _I32, _I32, _P, _P, _P, _P], ctypes.c_int),
     "rope_map_rerank": ([_P, _P, _P, _I64, _P, _P, _I32, _P, _P, _P, _P], ctypes.c_int),
+    "rope_autotune_enable": ([_I32], ctypes.c_int),
+    "rope_autotune_query": ([_P, _I64, _P, _P, _P, _P], ctypes.c_int),
+    "rope_autotune_set": ([_P, _I64, _P, _I32, _I32], ctypes.c_int),
     "rope_ladder_lengths": ([_I32, _I32, _I32, _P, _I32], _I32),
     "rope_ladder_create": ([_P, _P, _I64, _I32, _I32, _I32, _P, _P], ctypes.c_int),
     "rope_ladder_free": ([_P], None),
@@ -395,3 +398,25 @@ def rope_ladder_map(lad: Ladder, seqs: torch.Tensor, offsets: torch.Tensor, k: i
     _check(load().rope_ladder_map(lad.handle, _ptr(seqs), _ptr(offsets), n, ctypes.byref(o), _ptr(out[0]),
                                   _ptr(out[1]), _ptr(out[2]), _stream(stream)))
     return out
+
+
+# ---------------------------------------------------------------- tuner
+
+def rope_autotune_enable(enabled: bool):
+    _check(load().rope_autotune_enable(1 if enabled else 0))
+
+
+def rope_autotune_query(idx: Index, n_reads: int, k: int = 8, sep: int = 0, cand_depth: int = 0):
+    """(tile variant, items per SM, sample ms) chosen for this shape class, or None."""
+    o = _opts(k, sep, "bf16", None, cand_depth, 0, 0, 0, 0)
+    v, it, ms = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_float()
+    st = load().rope_autotune_query(idx.handle, n_reads, ctypes.byref(o), ctypes.byref(v), ctypes.byref(it),
+                                    ctypes.byref(ms))
+    return (v.value, it.value, ms.value) if st == 0 else None
+
+
+def rope_autotune_set(idx: Index, n_reads: int, variant: int, items_per_sm: int, k: int = 8, sep: int = 0,
+                      cand_depth: int = 0):
+    """Pin the scan configuration of this shape class."""
+    o = _opts(k, sep, "bf16", None, cand_depth, 0, 0, 0, 0)
+    _check(load().rope_autotune_set(idx.handle, n_reads, ctypes.byref(o), variant, items_per_sm))
