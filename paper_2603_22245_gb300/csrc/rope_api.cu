@@ -659,7 +659,40 @@ int32_t ranges_for(int items_per_sm, int num_sms, int64_t n_groups) {
   return (int32_t)(nr < 1 ? 1 : nr > 4096 ? 4096 : nr);
 }
 
-// Times the candidates on windows [jb, jb + sample) and records the fastest.
+// Times one candidate (variant, n_ranges) on windows [jb, jb + len).
+rope_status time_candidate(const rope_index* idx, const uint16_t* emb_bf16, const float* emb_f32, const float* norms,
+                           int64_t n_reads, int64_t jb, int64_t len, int32_t n_ranges, int variant,
+                           const rope_score_opts& o, Candidate* cand, DeviceCtx* c, cudaStream_t stream,
+                           cudaEvent_t e0, cudaEvent_t e1, int reps, float* ms) {
+  ScanPlan pl;
+  rope_status st = plan_scan(idx, ROPE_PREC_BF16, n_reads, jb, jb + len, n_ranges, c->num_sms, &pl, variant);
+  if (st != ROPE_OK) return st;
+  pl.a.emb_f32 = emb_f32;
+  pl.a.emb_bf16 = emb_bf16;
+  pl.a.norms = norms;
+  pl.a.cand_depth = o.cand_depth;
+  pl.a.sep = o.sep;
+  pl.a.cand = cand;
+  pl.a.status = c->status;
+  cudaError_t e = cudaSuccess;
+  for (int rep = 0; rep < reps && e == cudaSuccess; ++rep) {  // only the last launch is timed
+    cudaEventRecord(e0, stream);
+    e = launch_scan_tc(idx->ix, pl.a, false, c->num_sms, stream);
+    cudaEventRecord(e1, stream);
+  }
+  if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+  if (e == cudaSuccess) e = cudaEventElapsedTime(ms, e0, e1);
+  if (e != cudaSuccess) return fail(ROPE_ERR_CUDA, "tuning launch: %s", cudaGetErrorString(e));
+  return ROPE_OK;
+}
+
+// Predicts each candidate's time over the call's windows [jb, je) and
+// records the fastest. A scan's time is its lists' warm-up (a list of depth k
+// takes about k*ln(n/k) updates over n windows, most of them early) plus a
+// cost per window; a short sample alone would overweight the warm-up. So each
+// candidate is timed on windows [jb, jb + W1) and [jb, jb + 2*W1) with the
+// same number of ranges, and the line through the two points is evaluated
+// at je - jb (measured directly when that is at most 2*W1).
 rope_status tune_tc(const rope_index* idx, const uint16_t* emb_bf16, const float* emb_f32, const float* norms,
                     int64_t n_reads, int64_t jb, int64_t je, const rope_score_opts& o, DeviceCtx* c,
                     cudaStream_t stream, TuneVal* best) {
@@ -667,9 +700,13 @@ rope_status tune_tc(const rope_index* idx, const uint16_t* emb_bf16, const float
   const int64_t sup = scan_tc_super_tile(ix.D);
   const int64_t n_groups = (n_reads + scan_tc_group(ix.D) - 1) / scan_tc_group(ix.D);
   static const int kItems[] = {8, 16, 32};
-  // enough super-tiles for the finest split to give every range one
-  const int64_t want_sup = std::max<int64_t>(64, ((int64_t)32 * c->num_sms + n_groups - 1) / n_groups);
-  const int64_t sample = std::min<int64_t>(je - jb, want_sup * sup);
+  // W1: about 2^20 windows, and enough super-tiles for the finest split to
+  // give every range one
+  const int64_t w1_sup =
+      std::max<int64_t>(((int64_t)1 << 20) / sup, ((int64_t)32 * c->num_sms + n_groups - 1) / n_groups);
+  const int64_t total = je - jb;
+  const int64_t w1 = w1_sup * sup;
+  const bool direct = total <= 2 * w1;
   size_t cand_bytes = 0;
   for (int v = 0; v < scan_tc_variants(ix.D); ++v)
     for (int items : kItems) {
@@ -688,31 +725,24 @@ rope_status tune_tc(const rope_index* idx, const uint16_t* emb_bf16, const float
   for (int v = 0; v < scan_tc_variants(ix.D) && st == ROPE_OK; ++v) {
     if (!scan_tc_fits(ix, o.cand_depth, v)) continue;
     for (int items : kItems) {
-      ScanPlan pl;
-      st = plan_scan(idx, ROPE_PREC_BF16, n_reads, jb, jb + sample, ranges_for(items, c->num_sms, n_groups),
-                     c->num_sms, &pl, v);
+      const int32_t nr = ranges_for(items, c->num_sms, n_groups);
+      const int reps = any ? 1 : 2;  // the very first launch warms up, untimed
+      float pred = 0.f;
+      if (direct) {
+        st = time_candidate(idx, emb_bf16, emb_f32, norms, n_reads, jb, total, nr, v, o, cand, c, stream, e0, e1,
+                            reps, &pred);
+      } else {
+        float t1 = 0.f, t2 = 0.f;
+        st = time_candidate(idx, emb_bf16, emb_f32, norms, n_reads, jb, w1, nr, v, o, cand, c, stream, e0, e1, reps,
+                            &t1);
+        if (st == ROPE_OK)
+          st = time_candidate(idx, emb_bf16, emb_f32, norms, n_reads, jb, 2 * w1, nr, v, o, cand, c, stream, e0, e1,
+                              1, &t2);
+        const double per_window = ((double)t2 - t1) / (double)w1;
+        pred = (float)(t1 + per_window * (double)(total - w1));
+      }
       if (st != ROPE_OK) break;
-      pl.a.emb_f32 = emb_f32;
-      pl.a.emb_bf16 = emb_bf16;
-      pl.a.norms = norms;
-      pl.a.cand_depth = o.cand_depth;
-      pl.a.sep = o.sep;
-      pl.a.cand = cand;
-      pl.a.status = c->status;
-      float ms = 0.f;
-      cudaError_t e = cudaSuccess;
-      for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep) {  // the second launch is timed
-        cudaEventRecord(e0, stream);
-        e = launch_scan_tc(ix, pl.a, false, c->num_sms, stream);
-        cudaEventRecord(e1, stream);
-      }
-      if (e == cudaSuccess) e = cudaEventSynchronize(e1);
-      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
-      if (e != cudaSuccess) {
-        st = fail(ROPE_ERR_CUDA, "tuning launch: %s", cudaGetErrorString(e));
-        break;
-      }
-      if (ms < b.sample_ms) b = TuneVal{v, items, ms};
+      if (pred < b.sample_ms) b = TuneVal{v, items, pred};
       any = true;
     }
   }
