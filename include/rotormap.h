@@ -241,6 +241,16 @@ rope_status rope_score_dense(const rope_index* idx, const float* emb_f32, const 
 rope_status rope_map(const rope_index* idx, const uint8_t* seqs, const int64_t* offsets, int64_t n_reads,
                      const rope_score_opts* opts, int64_t* out_win, float* out_score, cudaStream_t stream);
 
+/* Both strands (§3.5 maps reads in both directions): each read is mapped by
+ * its head and by the head of its reverse complement (the complement of its
+ * last N letters, read backwards), both against the forward reference, and
+ * the best k of the two candidate lists are kept by (score descending, the
+ * forward strand first on equal scores, start ascending). out_strand int8
+ * [n_reads, k]: 0 forward, 1 reverse complement, -1 for a missing entry. */
+rope_status rope_map_strands(const rope_index* idx, const uint8_t* seqs, const int64_t* offsets, int64_t n_reads,
+                             const rope_score_opts* opts, int64_t* out_win, float* out_score, int8_t* out_strand,
+                             cudaStream_t stream);
+
 /* ---- learned reranker (steps a8, a9) -------------------------------------
  * The paper relates fidelity to Levenshtein distance (§1, §2.4) and keeps
  * candidate loci by score or per-fragment thresholds (§3.3, §3.5). This

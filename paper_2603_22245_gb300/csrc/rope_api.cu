@@ -991,6 +991,57 @@ extern "C" rope_status rope_map(const rope_index* idx, const uint8_t* seqs, cons
   return st;
 }
 
+extern "C" rope_status rope_map_strands(const rope_index* idx, const uint8_t* seqs, const int64_t* offsets,
+                                        int64_t n_reads, const rope_score_opts* opts, int64_t* out_win,
+                                        float* out_score, int8_t* out_strand, cudaStream_t stream) {
+  if (!idx) return fail(ROPE_ERR_INVALID_ARG, "index is NULL");
+  rope_score_opts o;
+  rope_status st = check_opts(opts, &o);
+  if (st != ROPE_OK) return st;
+  if (n_reads < 0) return fail(ROPE_ERR_INVALID_ARG, "n_reads < 0");
+  if (n_reads == 0) return ROPE_OK;
+  if (!seqs || !offsets || !out_win || !out_score || !out_strand) return fail(ROPE_ERR_INVALID_ARG, "NULL pointer");
+  DeviceCtx* c;
+  if ((st = get_ctx(&c)) != ROPE_OK) return st;
+  const int D = idx->ix.D, m = idx->ix.m, k = o.k;
+  const size_t n2 = 2 * (size_t)n_reads;
+  // one scratch block: emb_f32 | norms | win2 | score2 | emb_bf16 (rows n..2n-1: reverse strand)
+  auto al = [](size_t b) { return (b + 255) & ~size_t(255); };
+  const size_t b_f32 = al(n2 * 2 * D * sizeof(float)), b_norm = al(n2 * (1 + m) * sizeof(float));
+  const size_t b_win = al(n2 * k * sizeof(int64_t)), b_sc = al(n2 * k * sizeof(float));
+  const size_t b_bf16 = al(n2 * 2 * D * sizeof(uint16_t));
+  uint8_t* scratch = nullptr;
+  if ((st = pool_alloc(c, (void**)&scratch, b_f32 + b_norm + b_win + b_sc + b_bf16, stream)) != ROPE_OK) return st;
+  float* emb = reinterpret_cast<float*>(scratch);
+  float* norms = reinterpret_cast<float*>(scratch + b_f32);
+  int64_t* win2 = reinterpret_cast<int64_t*>(scratch + b_f32 + b_norm);
+  float* score2 = reinterpret_cast<float*>(scratch + b_f32 + b_norm + b_win);
+  uint16_t* embh = reinterpret_cast<uint16_t*>(scratch + b_f32 + b_norm + b_win + b_sc);
+  const int slot = prof_begin(stream);
+  cudaError_t e = launch_encode_reads(idx->enc, seqs, offsets, n_reads, emb, embh, norms, c->status, stream);
+  if (e == cudaSuccess)
+    e = launch_encode_reads(idx->enc, seqs, offsets, n_reads, emb + (size_t)n_reads * 2 * D,
+                            embh + (size_t)n_reads * 2 * D, norms + (size_t)n_reads * (1 + m), c->status, stream,
+                            nullptr, true);
+  prof_mark(slot, 1, stream);
+  if (e != cudaSuccess) st = fail(ROPE_ERR_CUDA, "encode launch: %s", cudaGetErrorString(e));
+  if (st == ROPE_OK) {
+    o.j_begin = 0;
+    o.j_end = 0;
+    st = score_topk_impl(idx, emb, embh, norms, (int64_t)n2, &o, win2, score2, stream, slot, nullptr);
+  }
+  if (st == ROPE_OK) {
+    e = launch_strand_merge(win2, score2, n_reads, k, out_win, out_score, out_strand, stream);
+    if (e != cudaSuccess) st = fail(ROPE_ERR_CUDA, "strand merge launch: %s", cudaGetErrorString(e));
+  }
+  if (slot >= 0 && st != ROPE_OK) {
+    prof_mark(slot, 2, stream);
+    prof_mark(slot, 3, stream);
+  }
+  cudaFreeAsync(scratch, stream);
+  return st;
+}
+
 // ---------------------------------------------------------------- allocation-free scan
 //
 // rope_score_topk_noalloc: the same scan, merge and re-scoring as

@@ -85,10 +85,19 @@ cudaError_t launch_mer_bins(const uint32_t* packed, int64_t len, int64_t n_words
 // lanes k < m add exp(2 pi i f_k loc / N) to entry (k, bin) of a per-warp
 // shared accumulator, so every entry is summed in location order (the direct
 // sum of §2.1-§2.3 in FP32, deterministic).
+// Letter q (0..3, 4 if not ACGT) of the head of a read of length len: the read
+// itself, or (rc) its reverse complement, whose head is the complement of the
+// read's last letters read backwards.
+__device__ __forceinline__ uint32_t head_letter(const uint8_t* seq, int64_t len, int q, bool rc) {
+  if (!rc) return letter_code(seq[q]);
+  const uint32_t c = letter_code(seq[len - 1 - q]);
+  return c > 3 ? c : 3u - c;  // A<->T, C<->G
+}
+
 __global__ void encode_reads_kernel(EncTables tb, const uint8_t* __restrict__ seqs,
                                     const int64_t* __restrict__ offsets, int64_t n, float* __restrict__ emb_f32,
                                     __nv_bfloat16* __restrict__ emb_bf16, float* __restrict__ norms, int* status,
-                                    const int64_t* __restrict__ perm) {
+                                    const int64_t* __restrict__ perm, bool rc) {
   extern __shared__ float2 enc_acc[];
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
@@ -106,7 +115,7 @@ __global__ void encode_reads_kernel(EncTables tb, const uint8_t* __restrict__ se
       if (lane == 0) set_status(status, kStatusShortRead);
     } else {
       int bad = 0;
-      for (int i = lane; i < tb.N; i += 32) bad |= letter_code(seq[i]) > 3;
+      for (int i = lane; i < tb.N; i += 32) bad |= head_letter(seq, len, i, rc) > 3;
       if (__any_sync(0xffffffffu, bad)) {
         ok = false;
         if (lane == 0) set_status(status, kStatusBadBase);
@@ -119,7 +128,7 @@ __global__ void encode_reads_kernel(EncTables tb, const uint8_t* __restrict__ se
         uint32_t b = 0;
         if (loc < n_loc) {
           uint32_t code = 0;
-          for (int i = 0; i < tb.s; ++i) code = code * 4u + (letter_code(seq[loc + i]) & 3u);
+          for (int i = 0; i < tb.s; ++i) code = code * 4u + (head_letter(seq, len, loc + i, rc) & 3u);
           b = tb.map[code];
         }
         const int cnt = min(32, n_loc - loc0);
@@ -168,7 +177,7 @@ __global__ void encode_reads_kernel(EncTables tb, const uint8_t* __restrict__ se
 
 cudaError_t launch_encode_reads(const EncTables& tb, const uint8_t* seqs, const int64_t* offsets, int64_t n,
                                 float* emb_f32, uint16_t* emb_bf16, float* norms, int* status, cudaStream_t st,
-                                const int64_t* perm) {
+                                const int64_t* perm, bool rc) {
   if (n <= 0) return cudaSuccess;
   int wpb = (int)(48 * 1024 / (tb.D * sizeof(float2)));
   if (wpb > 8) wpb = 8;
@@ -178,7 +187,7 @@ cudaError_t launch_encode_reads(const EncTables& tb, const uint8_t* seqs, const 
   if (blocks > 152 * 64) blocks = 152 * 64;
   encode_reads_kernel<<<(unsigned)blocks, wpb * 32, smem, st>>>(tb, seqs, offsets, n, emb_f32,
                                                                   reinterpret_cast<__nv_bfloat16*>(emb_bf16), norms,
-                                                                  status, perm);
+                                                                  status, perm, rc);
   return cudaGetLastError();
 }
 

@@ -71,10 +71,16 @@ cudaError_t launch_fill_empty(int64_t* win, float* score, int64_t n, cudaStream_
 cudaError_t launch_pack(const uint8_t* seq, int64_t len, uint32_t* out, int* status, cudaStream_t st);
 cudaError_t launch_mer_bins(const uint32_t* packed, int64_t len, int64_t n_words, int s, const uint16_t* map_lsb,
                             uint16_t* out, cudaStream_t st);
-// Row r encodes read perm[r] (perm null: read r).
+// Row r encodes read perm[r] (perm null: read r); with rc, the head of the
+// read's reverse complement.
 cudaError_t launch_encode_reads(const EncTables& tb, const uint8_t* seqs, const int64_t* offsets, int64_t n,
                                 float* emb_f32, uint16_t* emb_bf16, float* norms, int* status, cudaStream_t st,
-                                const int64_t* perm = nullptr);
+                                const int64_t* perm = nullptr, bool rc = false);
+// Per read, the best k of its forward-strand row r and reverse-strand row
+// n + r of (win, score) [2n, k] by (score desc, forward first, start asc);
+// strand 0 forward, 1 reverse, -1 for a missing entry.
+cudaError_t launch_strand_merge(const int64_t* win2, const float* score2, int64_t n, int k, int64_t* out_win,
+                                float* out_score, int8_t* out_strand, cudaStream_t st);
 struct PrepassTables {
   const double2* phase;  // [m*(N-s+1)]
   const double2* rot;    // [m]

@@ -179,3 +179,55 @@ cudaError_t launch_merge(const DevIndex& ix, const MergeArgs& a, cudaStream_t st
 }
 
 }  // namespace rope
+
+namespace rope {
+
+// Two sorted top-k lists per read (forward row r, reverse row n + r, each by
+// score descending and start ascending, missing entries (-1, -inf) last)
+// merged into one: score descending, the forward strand first on equal
+// scores, then the lower start.
+__global__ void strand_merge_kernel(const int64_t* __restrict__ win2, const float* __restrict__ score2, int64_t n,
+                                    int k, int64_t* __restrict__ out_win, float* __restrict__ out_score,
+                                    int8_t* __restrict__ out_strand) {
+  for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t* wf = win2 + r * k;
+    const int64_t* wr = win2 + (n + r) * k;
+    const float* sf = score2 + r * k;
+    const float* sr = score2 + (n + r) * k;
+    int i = 0, j = 0;
+    for (int o = 0; o < k; ++o) {
+      const bool okf = i < k && wf[i] >= 0, okr = j < k && wr[j] >= 0;
+      int8_t strand = -1;
+      if (okf && okr) {
+        strand = sr[j] > sf[i] ? 1 : 0;  // equal scores: forward first
+      } else if (okf) {
+        strand = 0;
+      } else if (okr) {
+        strand = 1;
+      }
+      int64_t w = -1;
+      float sc = -INFINITY;
+      if (strand == 0) {
+        w = wf[i];
+        sc = sf[i++];
+      } else if (strand == 1) {
+        w = wr[j];
+        sc = sr[j++];
+      }
+      out_win[r * k + o] = w;
+      out_score[r * k + o] = sc;
+      out_strand[r * k + o] = strand;
+    }
+  }
+}
+
+cudaError_t launch_strand_merge(const int64_t* win2, const float* score2, int64_t n, int k, int64_t* out_win,
+                                float* out_score, int8_t* out_strand, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  int64_t blocks = (n + 255) / 256;
+  if (blocks > 152 * 16) blocks = 152 * 16;
+  strand_merge_kernel<<<(unsigned)blocks, 256, 0, st>>>(win2, score2, n, k, out_win, out_score, out_strand);
+  return cudaGetLastError();
+}
+
+}  // namespace rope

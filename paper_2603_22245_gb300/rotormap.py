@@ -62,6 +62,7 @@ EXPORTS = {
     "rope_score_topk_noalloc": ([_P, _P, _P, _P, _I64, _P, _P, _P, _P], ctypes.c_int),
     "rope_score_dense": ([_P, _P, _P, _P, _I64, _I32, _I64, _I64, _P, _P], ctypes.c_int),
     "rope_map": ([_P, _P, _P, _I64, _P, _P, _P, _P], ctypes.c_int),
+    "rope_map_strands": ([_P, _P, _P, _I64, _P, _P, _P, _P, _P], ctypes.c_int),
     "rope_reranker_create": ([_I32, _I32, ctypes.c_uint64, _P], ctypes.c_int),
     "rope_reranker_free": ([_P], None),
     "rope_reranker_get": ([_P, _P, _P], ctypes.c_int),
@@ -307,6 +308,20 @@ def rope_map(idx: Index, seqs: torch.Tensor, offsets: torch.Tensor, k: int = 8, 
     o = _opts(k, sep, precision, rescore, cand_depth, rescore_depth, n_ranges, 0, 0)
     _check(load().rope_map(idx.handle, _ptr(seqs), _ptr(offsets), n, ctypes.byref(o), _ptr(out[0]), _ptr(out[1]),
                            _stream(stream)))
+    return out
+
+
+def rope_map_strands(idx: Index, seqs: torch.Tensor, offsets: torch.Tensor, k: int = 8, sep: int = 0,
+                     precision="bf16", rescore=None, cand_depth: int = 0, rescore_depth: int = 0, n_ranges: int = 0,
+                     stream=None):
+    """Both strands: (starts [n, k], fidelities [n, k], strand int8 [n, k]: 0 forward, 1 reverse, -1 missing)."""
+    n = offsets.numel() - 1
+    out = (torch.empty((n, k), dtype=torch.int64, device=seqs.device),
+           torch.empty((n, k), dtype=torch.float32, device=seqs.device),
+           torch.empty((n, k), dtype=torch.int8, device=seqs.device))
+    o = _opts(k, sep, precision, rescore, cand_depth, rescore_depth, n_ranges, 0, 0)
+    _check(load().rope_map_strands(idx.handle, _ptr(seqs), _ptr(offsets), n, ctypes.byref(o), _ptr(out[0]),
+                                   _ptr(out[1]), _ptr(out[2]), _stream(stream)))
     return out
 
 
