@@ -357,3 +357,38 @@ def rerank_features(ref, seqs, offsets, cand_win, cand_score, p: Params) -> np.n
             row[K + 4 + m] = hamming_fingerprint_fidelity(head[:n1], win[:n1])
             row[K + 5 + m] = hamming_fingerprint_fidelity(head[n1:], win[n1:])
     return X
+
+
+# ------------------------------------------------------------ both strands
+
+_COMPLEMENT = np.arange(256, dtype=np.uint8)
+for _a, _b in (("A", "T"), ("C", "G"), ("a", "t"), ("c", "g")):
+    _COMPLEMENT[ord(_a)], _COMPLEMENT[ord(_b)] = ord(_b), ord(_a)
+
+
+def reverse_complement(seq) -> np.ndarray:
+    """The other strand of a DNA string read 5'->3': letters reversed, A<->T, C<->G."""
+    return _COMPLEMENT[_u8(seq)[::-1]].copy()
+
+
+def score_topk_strands(ref, seqs, offsets, p: Params, k: int = 8, sep: int = 0):
+    """Top-k over both strands (§3.5 maps reads in both directions): each read
+    by its head and by the head of its reverse complement, both against the
+    forward reference, merged by (score descending, forward first, start
+    ascending). Returns (starts, scores, strand 0/1, -1 where missing)."""
+    seqs = _u8(seqs)
+    offsets = np.asarray(offsets, dtype=np.int64)
+    n = len(offsets) - 1
+    rc = np.concatenate([reverse_complement(seqs[offsets[i]:offsets[i + 1]]) for i in range(n)]) if n else seqs
+    wf, sf = score_topk(ref, seqs, offsets, p, k=k, sep=sep)
+    wr, sr = score_topk(ref, rc, offsets, p, k=k, sep=sep)
+    out_w = np.full((n, k), -1, dtype=np.int64)
+    out_s = np.full((n, k), -np.inf)
+    out_t = np.full((n, k), -1, dtype=np.int8)
+    for i in range(n):
+        cands = [(-sf[i, j], 0, wf[i, j]) for j in range(k) if wf[i, j] >= 0]
+        cands += [(-sr[i, j], 1, wr[i, j]) for j in range(k) if wr[i, j] >= 0]
+        cands.sort()
+        for j, (ns, t, w) in enumerate(cands[:k]):
+            out_w[i, j], out_s[i, j], out_t[i, j] = w, -ns, t
+    return out_w, out_s, out_t

@@ -536,3 +536,21 @@ def test_hamming_fingerprint_other_letters():
     assert oracle.hamming_fingerprint_fidelity(b"ACGT", b"ACGN") == pytest.approx((3 / 4) ** 2)
     assert oracle.hamming_fingerprint_fidelity(b"NNAC", b"GTAC") == pytest.approx((2 / 4) ** 2)
     assert oracle.hamming_fingerprint_fidelity(b"ACGTACGT", b"TGCATGCA") == pytest.approx(0.0, abs=1e-15)
+
+
+def test_reverse_complement_and_strands():
+    """The other strand: reversal with A<->T, C<->G, an involution; a read that
+    is the reverse complement of a window is found there on strand 1 with
+    fidelity 1, and a forward copy on strand 0."""
+    assert bytes(oracle.reverse_complement(b"ACGTTG")) == b"CAACGT"
+    s = synth.uniform_ref(500, 3)
+    assert np.array_equal(oracle.reverse_complement(oracle.reverse_complement(s)), s)
+    ref = synth.uniform_ref(3000, 4)
+    p = oracle.Params(s=4, m=2, t=2, variant=1, N=150)
+    fwd = ref[700:850]
+    rev = oracle.reverse_complement(ref[1900:2050])
+    seqs = np.concatenate([fwd, rev])
+    w, sc, t = oracle.score_topk_strands(ref, seqs, np.array([0, 150, 300]), p, k=3)
+    assert w[0, 0] == 700 and t[0, 0] == 0 and sc[0, 0] == pytest.approx(1.0, abs=1e-9)
+    assert w[1, 0] == 1900 and t[1, 0] == 1 and sc[1, 0] == pytest.approx(1.0, abs=1e-9)
+    assert np.all(np.diff(sc, axis=1) <= 0)
