@@ -539,7 +539,7 @@ def main():
                    "per scan pass; reads 20 MB/step)", "index_build_s": index_s, "parallelism": f"replicated index, "
                    f"reads sharded over {ws} GPU(s)",
                    "scan_tiles": None if tuned is None else {"variant": tuned[0], "items_per_sm": tuned[1],
-                                                              "predicted_scan_ms": tuned[2]}},
+                                                              "tuned_scan_ms": tuned[2]}},
         "reads_per_s": reads_s, "top1_acc": acc_bf16, "fp32_plain": fp32,
         "speedup_vs_fp32_plain": value / ws / fp32["value"],
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "reranker": reranker, "gpu_launches": 3 * args.steps, "clocks": clocks,

@@ -207,12 +207,14 @@ rope_status rope_score_topk_noalloc(const rope_index* idx, const float* emb_f32,
  * The BF16 scan has tile variants and a free split of the work into
  * (read group, window range) items. On the first BF16 rope_score_topk /
  * rope_map call of a shape class (device, complex dimension, stride, window
- * length and read groups rounded up to powers of two, cand_depth, sep on/off)
- * with opts->n_ranges == 0, the library times each variant with 8, 16 and 32
- * items per SM on that call's reads over the first 2^20 and 2^21 of its
- * windows (or all of them if fewer), predicts each pair's time over all the
- * call's windows from the two, and keeps the fastest for the class;
- * later calls of the class use it. Results do not depend on the choice.
+ * length, read groups and scanned windows rounded up to powers of two,
+ * cand_depth, sep on/off) with opts->n_ranges == 0, the library times each
+ * variant with 8, 16 and 32 items per SM on that call's reads and windows and
+ * keeps the fastest for the class; later calls of the class use it. Only
+ * scans of at most 2^22 windows are timed (short samples of a longer scan
+ * mispredict it: the cost per window falls with the scan's length); longer
+ * ones keep the defaults (variant 0, 16 items per SM) unless set by hand.
+ * Results do not depend on the choice.
  * Tuning is on unless the environment sets ROPE_AUTOTUNE=0; the
  * allocation-free entry point only reads earlier choices. */
 rope_status rope_autotune_enable(int32_t enabled);  /* 0 also forgets earlier choices */
@@ -221,7 +223,8 @@ rope_status rope_autotune_enable(int32_t enabled);  /* 0 also forgets earlier ch
 rope_status rope_autotune_set(const rope_index* idx, int64_t n_reads, const rope_score_opts* opts, int32_t variant,
                               int32_t items_per_sm);
 /* The choice recorded for the class of (idx, n_reads, opts): tile variant,
- * items per SM and its predicted scan time (ms, 0 if set by hand);
+ * items per SM and its measured scan time (ms; 0 if set by hand or kept as
+ * the default);
  * ROPE_ERR_INVALID_ARG if none yet. */
 rope_status rope_autotune_query(const rope_index* idx, int64_t n_reads, const rope_score_opts* opts,
                                 int32_t* variant, int32_t* items_per_sm, float* sample_ms);

@@ -618,10 +618,10 @@ rope_status check_opts(const rope_score_opts* o, rope_score_opts* v) {
 // speed does. ROPE_AUTOTUNE=0 (or rope_autotune_enable(0)) keeps the defaults.
 
 struct TuneKey {
-  int dev, D, stride, n_log2, g_log2, cand_depth, sep_on;
+  int dev, D, stride, n_log2, g_log2, w_log2, cand_depth, sep_on;
   bool operator<(const TuneKey& o) const {
-    return std::tie(dev, D, stride, n_log2, g_log2, cand_depth, sep_on) <
-           std::tie(o.dev, o.D, o.stride, o.n_log2, o.g_log2, o.cand_depth, o.sep_on);
+    return std::tie(dev, D, stride, n_log2, g_log2, w_log2, cand_depth, sep_on) <
+           std::tie(o.dev, o.D, o.stride, o.n_log2, o.g_log2, o.w_log2, o.cand_depth, o.sep_on);
   }
 };
 struct TuneVal {
@@ -642,16 +642,34 @@ bool autotune_on() {
   return g_autotune == 1;
 }
 
+// ROPE_AUTOTUNE_LOG=1 prints every candidate's predicted time to stderr.
+bool tune_log() {
+  static const bool on = [] {
+    const char* e = getenv("ROPE_AUTOTUNE_LOG");
+    return e && e[0] == '1';
+  }();
+  return on;
+}
+
 int ilog2_ceil(int64_t v) {
   int r = 0;
   while ((int64_t(1) << r) < v) ++r;
   return r;
 }
 
+// windows a call scans: [j_begin, j_end) clipped to the index as score_topk_impl does
+int64_t scanned_windows(const rope_index* idx, const rope_score_opts& o) {
+  const int64_t W = idx->ix.W;
+  const int64_t jb = o.j_begin > 0 ? o.j_begin : 0;
+  const int64_t je = o.j_end > 0 ? (o.j_end < W ? o.j_end : W) : W;
+  return je > jb ? je - jb : 0;
+}
+
 TuneKey tune_key(const rope_index* idx, int64_t n_reads, const rope_score_opts& o) {
   const DevIndex& ix = idx->ix;
   const int64_t groups = (n_reads + scan_tc_group(ix.D) - 1) / scan_tc_group(ix.D);
-  return TuneKey{idx->device, ix.D, ix.stride, ilog2_ceil(ix.N), ilog2_ceil(groups), o.cand_depth, o.sep > 0};
+  return TuneKey{idx->device,         ix.D,        ix.stride, ilog2_ceil(ix.N), ilog2_ceil(groups),
+                 ilog2_ceil(scanned_windows(idx, o)), o.cand_depth, o.sep > 0};
 }
 
 int32_t ranges_for(int items_per_sm, int num_sms, int64_t n_groups) {
@@ -686,27 +704,26 @@ rope_status time_candidate(const rope_index* idx, const uint16_t* emb_bf16, cons
   return ROPE_OK;
 }
 
-// Predicts each candidate's time over the call's windows [jb, je) and
-// records the fastest. A scan's time is its lists' warm-up (a list of depth k
-// takes about k*ln(n/k) updates over n windows, most of them early) plus a
-// cost per window; a short sample alone would overweight the warm-up. So each
-// candidate is timed on windows [jb, jb + W1) and [jb, jb + 2*W1) with the
-// same number of ranges, and the line through the two points is evaluated
-// at je - jb (measured directly when that is at most 2*W1).
+// Times each candidate on the call's own windows [jb, je) and records the
+// fastest, when the scan is short enough to be timed whole (at most
+// kTuneMaxWindows windows). A longer scan keeps the defaults: measured on this
+// GPU, a scan's cost per window falls with its length (each candidate list
+// takes about k*ln(n/k) updates over n windows, most of them early), by 2.2x
+// from 2^20 to 10^8 windows, and unevenly across the tile variants, so timings
+// of a short sample ranked the variants the wrong way round for a long scan.
+constexpr int64_t kTuneMaxWindows = (int64_t)1 << 22;
+
 rope_status tune_tc(const rope_index* idx, const uint16_t* emb_bf16, const float* emb_f32, const float* norms,
                     int64_t n_reads, int64_t jb, int64_t je, const rope_score_opts& o, DeviceCtx* c,
                     cudaStream_t stream, TuneVal* best) {
   const DevIndex& ix = idx->ix;
-  const int64_t sup = scan_tc_super_tile(ix.D);
   const int64_t n_groups = (n_reads + scan_tc_group(ix.D) - 1) / scan_tc_group(ix.D);
   static const int kItems[] = {8, 16, 32};
-  // W1: about 2^20 windows, and enough super-tiles for the finest split to
-  // give every range one
-  const int64_t w1_sup =
-      std::max<int64_t>(((int64_t)1 << 20) / sup, ((int64_t)32 * c->num_sms + n_groups - 1) / n_groups);
   const int64_t total = je - jb;
-  const int64_t w1 = w1_sup * sup;
-  const bool direct = total <= 2 * w1;
+  if (total > kTuneMaxWindows) {
+    *best = TuneVal{0, 16, 0.f};
+    return ROPE_OK;
+  }
   size_t cand_bytes = 0;
   for (int v = 0; v < scan_tc_variants(ix.D); ++v)
     for (int items : kItems) {
@@ -727,22 +744,14 @@ rope_status tune_tc(const rope_index* idx, const uint16_t* emb_bf16, const float
     for (int items : kItems) {
       const int32_t nr = ranges_for(items, c->num_sms, n_groups);
       const int reps = any ? 1 : 2;  // the very first launch warms up, untimed
-      float pred = 0.f;
-      if (direct) {
-        st = time_candidate(idx, emb_bf16, emb_f32, norms, n_reads, jb, total, nr, v, o, cand, c, stream, e0, e1,
-                            reps, &pred);
-      } else {
-        float t1 = 0.f, t2 = 0.f;
-        st = time_candidate(idx, emb_bf16, emb_f32, norms, n_reads, jb, w1, nr, v, o, cand, c, stream, e0, e1, reps,
-                            &t1);
-        if (st == ROPE_OK)
-          st = time_candidate(idx, emb_bf16, emb_f32, norms, n_reads, jb, 2 * w1, nr, v, o, cand, c, stream, e0, e1,
-                              1, &t2);
-        const double per_window = ((double)t2 - t1) / (double)w1;
-        pred = (float)(t1 + per_window * (double)(total - w1));
-      }
+      float ms = 0.f;
+      st = time_candidate(idx, emb_bf16, emb_f32, norms, n_reads, jb, total, nr, v, o, cand, c, stream, e0, e1, reps,
+                          &ms);
       if (st != ROPE_OK) break;
-      if (pred < b.sample_ms) b = TuneVal{v, items, pred};
+      if (tune_log())
+        fprintf(stderr, "rotormap tuner: D=%d stride=%d N=%d reads=%lld windows=%lld variant=%d items/SM=%d %.3f ms\n",
+                ix.D, ix.stride, ix.N, (long long)n_reads, (long long)total, v, items, ms);
+      if (ms < b.sample_ms) b = TuneVal{v, items, ms};
       any = true;
     }
   }
