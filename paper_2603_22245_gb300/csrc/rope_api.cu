@@ -799,7 +799,7 @@ rope_status choose_tc(const rope_index* idx, const uint16_t* emb_bf16, const flo
 
 rope_status rope::score_topk_impl(const rope_index* idx, const float* emb_f32, const uint16_t* emb_bf16,
                                   const float* norms, int64_t n_reads, const rope_score_opts* opts, int64_t* out_win,
-                                  float* out_score, cudaStream_t stream, int prof_slot, const int64_t* out_row) {
+                                  float* out_score, cudaStream_t stream, int prof_slot, const int64_t* out_row, const ExtCandidates* ext) {
   if (!idx) return fail(ROPE_ERR_INVALID_ARG, "index is NULL");
   rope_score_opts o;
   rope_status st = check_opts(opts, &o);
@@ -821,8 +821,8 @@ rope_status rope::score_topk_impl(const rope_index* idx, const float* emb_f32, c
   if (je > jb) {
     int32_t variant = 0, nr_req = o.n_ranges;
     if (o.precision == ROPE_PREC_BF16 &&
-        (st = choose_tc(idx, emb_bf16, emb_f32, norms, n_reads, jb, je, o, c, stream, true, &variant, &nr_req)) !=
-            ROPE_OK)
+        (st = choose_tc(idx, emb_bf16, emb_f32, norms, n_reads, jb, je, o, c, stream, ext == nullptr, &variant,
+                        &nr_req)) != ROPE_OK)
       return st;
     if ((st = plan_scan(idx, o.precision, n_reads, jb, je, nr_req, c->num_sms, &pl, variant)) != ROPE_OK) return st;
     if (pl.tc && !scan_tc_fits(ix, o.cand_depth, variant))
@@ -832,7 +832,17 @@ rope_status rope::score_topk_impl(const rope_index* idx, const float* emb_f32, c
     n_ranges = pl.a.n_ranges * pl.a.lists_per_range;
   }
   const size_t cand_bytes = (size_t)n_reads * n_ranges * o.cand_depth * sizeof(Candidate);
-  if ((st = pool_alloc(c, (void**)&cand, cand_bytes, stream)) != ROPE_OK) return st;
+  if (ext) {
+    if (ext->bytes < cand_bytes)
+      return fail(ROPE_ERR_INVALID_ARG, "candidate buffer of %zu bytes, %zu needed", ext->bytes, cand_bytes);
+    cand = ext->cand;
+  } else if ((st = pool_alloc(c, (void**)&cand, cand_bytes, stream)) != ROPE_OK) {
+    return st;
+  }
+  // the pool block is returned on every exit below; a caller's buffer is not
+  auto release = [&]() {
+    if (!ext) cudaFreeAsync(cand, stream);
+  };
   if (je > jb) {
     pl.a.emb_f32 = emb_f32;
     pl.a.emb_bf16 = emb_bf16;
@@ -845,11 +855,15 @@ rope_status rope::score_topk_impl(const rope_index* idx, const float* emb_f32, c
     cudaError_t e = pl.tc ? launch_scan_tc(ix, pl.a, false, c->num_sms, stream)
                           : launch_scan_fp32(ix, pl.a, false, c->num_sms, stream);
     if (e != cudaSuccess) {
-      cudaFreeAsync(cand, stream);
+      release();
       return fail(ROPE_ERR_CUDA, "scan launch: %s", cudaGetErrorString(e));
     }
   } else {
-    ROPE_CUDA(cudaMemsetAsync(cand, 0xFF, cand_bytes, stream));  // every slot empty
+    cudaError_t e = cudaMemsetAsync(cand, 0xFF, cand_bytes, stream);  // every slot empty
+    if (e != cudaSuccess) {
+      release();
+      return fail(ROPE_ERR_CUDA, "cudaMemsetAsync: %s", cudaGetErrorString(e));
+    }
   }
   prof_mark(prof_slot, 2, stream);
   MergeArgs m{};
@@ -869,8 +883,34 @@ rope_status rope::score_topk_impl(const rope_index* idx, const float* emb_f32, c
   m.status = c->status;
   cudaError_t e = launch_merge(ix, m, stream);
   prof_mark(prof_slot, 3, stream);
-  cudaFreeAsync(cand, stream);
+  release();
   if (e != cudaSuccess) return fail(ROPE_ERR_CUDA, "merge launch: %s", cudaGetErrorString(e));
+  return ROPE_OK;
+}
+
+rope_status rope::topk_cand_bytes(const rope_index* idx, int64_t n_reads, const rope_score_opts* opts,
+                                  size_t* bytes) {
+  if (!idx || !bytes) return fail(ROPE_ERR_INVALID_ARG, "NULL argument");
+  rope_score_opts o;
+  rope_status st = check_opts(opts, &o);
+  if (st != ROPE_OK) return st;
+  DeviceCtx* c;
+  if ((st = get_ctx(&c)) != ROPE_OK) return st;
+  const DevIndex& ix = idx->ix;
+  const int64_t jb = o.j_begin > 0 ? o.j_begin : 0;
+  const int64_t je = o.j_end > 0 ? (o.j_end < ix.W ? o.j_end : ix.W) : ix.W;
+  int32_t n_ranges = 1;
+  if (je > jb && n_reads > 0) {
+    int32_t variant = 0, nr_req = o.n_ranges;
+    if (o.precision == ROPE_PREC_BF16 &&
+        (st = choose_tc(idx, nullptr, nullptr, nullptr, n_reads, jb, je, o, c, nullptr, false, &variant, &nr_req)) !=
+            ROPE_OK)
+      return st;
+    ScanPlan pl;
+    if ((st = plan_scan(idx, o.precision, n_reads, jb, je, nr_req, c->num_sms, &pl, variant)) != ROPE_OK) return st;
+    n_ranges = pl.a.n_ranges * pl.a.lists_per_range;
+  }
+  *bytes = (size_t)n_reads * n_ranges * o.cand_depth * sizeof(Candidate);
   return ROPE_OK;
 }
 
@@ -920,7 +960,7 @@ extern "C" rope_status rope_score_topk(const rope_index* idx, const float* emb_f
   const int slot = prof_begin(stream);
   prof_mark(slot, 1, stream);
   const rope_status st = score_topk_impl(idx, emb_f32, emb_bf16, norms, n_reads, opts, out_win, out_score, stream,
-                                         slot, nullptr);
+                                         slot, nullptr, nullptr);
   if (slot >= 0 && st != ROPE_OK) {
     prof_mark(slot, 2, stream);
     prof_mark(slot, 3, stream);
@@ -988,7 +1028,7 @@ extern "C" rope_status rope_map(const rope_index* idx, const uint8_t* seqs, cons
   if (st == ROPE_OK) {
     o.j_begin = 0;
     o.j_end = 0;
-    st = score_topk_impl(idx, emb, embh, norms, n_reads, &o, out_win, out_score, stream, slot, nullptr);
+    st = score_topk_impl(idx, emb, embh, norms, n_reads, &o, out_win, out_score, stream, slot, nullptr, nullptr);
   }
   if (slot >= 0 && st != ROPE_OK) {
     prof_mark(slot, 2, stream);
@@ -1037,7 +1077,7 @@ extern "C" rope_status rope_map_strands(const rope_index* idx, const uint8_t* se
   if (st == ROPE_OK) {
     o.j_begin = 0;
     o.j_end = 0;
-    st = score_topk_impl(idx, emb, embh, norms, (int64_t)n2, &o, win2, score2, stream, slot, nullptr);
+    st = score_topk_impl(idx, emb, embh, norms, (int64_t)n2, &o, win2, score2, stream, slot, nullptr, nullptr);
   }
   if (st == ROPE_OK) {
     e = launch_strand_merge(win2, score2, n_reads, k, out_win, out_score, out_strand, stream);

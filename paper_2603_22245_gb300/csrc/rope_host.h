@@ -32,9 +32,19 @@ rope_status encode_reference_impl(const rope_params* p, const uint8_t* ref, int6
                                   const uint32_t* shared_packed, rope_index** out, cudaStream_t stream);
 // Scan + merge for n_reads encoded reads; the result of read r goes to output
 // row out_row[r] (out_row null: row r). prof_slot < 0: no stage timing.
+// A caller-provided candidate buffer for score_topk_impl: used instead of a
+// pool block, and the call then never tunes (no timing, no synchronisation).
+struct ExtCandidates {
+  Candidate* cand;
+  size_t bytes;
+};
 rope_status score_topk_impl(const rope_index* idx, const float* emb_f32, const uint16_t* emb_bf16,
                             const float* norms, int64_t n_reads, const rope_score_opts* opts, int64_t* out_win,
-                            float* out_score, cudaStream_t stream, int prof_slot, const int64_t* out_row);
+                            float* out_score, cudaStream_t stream, int prof_slot, const int64_t* out_row,
+                            const ExtCandidates* ext);
+// Candidate-buffer bytes such a call needs, with the configuration it would use
+// now (the tuned one for its class, else the defaults).
+rope_status topk_cand_bytes(const rope_index* idx, int64_t n_reads, const rope_score_opts* opts, size_t* bytes);
 
 }  // namespace rope
 

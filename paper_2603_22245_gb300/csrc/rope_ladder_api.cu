@@ -6,8 +6,16 @@
 // each non-empty bucket (encode its read heads, scan, merge) on one of a few
 // internal streams so that the tail of one bucket's scan overlaps the next
 // bucket's work; the caller's stream waits for all of them.
+//
+// The per-bucket work of a call is captured once into a CUDA graph and
+// replayed by later calls with the same bucket sizes, buffers and options:
+// the first call of such a key runs eagerly (and tunes the scans' shape
+// classes), the second captures and launches the graph, later ones launch it.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <map>
+#include <set>
 #include <vector>
 
 #include "rope_host.h"
@@ -28,7 +36,28 @@ struct rope_ladder {
   cudaStream_t streams[kLadderStreams] = {};
   cudaEvent_t fork = nullptr;
   cudaEvent_t join[kLadderStreams] = {};
+  cudaEvent_t done = nullptr;  // end of the last call, on its caller's stream
+  bool done_recorded = false;
+  // per-call scratch (bucketing, permutation, encodings), kept so that a
+  // captured graph can refer to it; grown on demand
+  uint8_t* scratch = nullptr;
+  size_t scratch_bytes = 0;
+  // candidate lists of the buckets run on each internal stream (graph path)
+  Candidate* arena[kLadderStreams] = {};
+  size_t arena_bytes[kLadderStreams] = {};
+  std::map<std::vector<int64_t>, cudaGraphExec_t> graphs;
+  std::set<std::vector<int64_t>> seen, no_graph;
 };
+
+namespace {
+
+void drop_graphs(rope_ladder* lad) {
+  for (auto& kv : lad->graphs) cudaGraphExecDestroy(kv.second);
+  lad->graphs.clear();
+  lad->seen.clear();
+}
+
+}  // namespace
 
 extern "C" int32_t rope_ladder_lengths(int32_t n_min, int32_t n_max, int32_t steps_per_octave, int32_t* out_host,
                                        int32_t cap) {
@@ -61,6 +90,11 @@ extern "C" void rope_ladder_free(rope_ladder* lad) {
     if (lad->join[i]) cudaEventDestroy(lad->join[i]);
   }
   if (lad->fork) cudaEventDestroy(lad->fork);
+  if (lad->done) cudaEventDestroy(lad->done);
+  drop_graphs(lad);
+  if (lad->scratch) cudaFree(lad->scratch);
+  for (int i = 0; i < kLadderStreams; ++i)
+    if (lad->arena[i]) cudaFree(lad->arena[i]);
   cudaSetDevice(prev);
   delete lad;
 }
@@ -111,6 +145,7 @@ extern "C" rope_status rope_ladder_create(const rope_params* p, const uint8_t* r
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&lad->join[i], cudaEventDisableTiming);
   }
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&lad->fork, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&lad->done, cudaEventDisableTiming);
   if (e != cudaSuccess) return cleanup(host_fail(ROPE_ERR_CUDA, "ladder set-up: %s", cudaGetErrorString(e)));
   *out = lad;
   return ROPE_OK;
@@ -141,7 +176,9 @@ extern "C" rope_status rope_ladder_map(const rope_ladder* lad, const uint8_t* se
   const bool bf16 = opts->precision == ROPE_PREC_BF16;
   const int slot = host_prof_begin(stream);
 
-  // scratch, one pool block: bucket | hist | base,count | perm | emb_f32 | norms | emb_bf16
+  rope_ladder* L = const_cast<rope_ladder*>(lad);  // buffers and graphs are cached in the ladder
+
+  // scratch, one block kept in the ladder: bucket | hist | base,count | perm | emb_f32 | norms | emb_bf16
   auto al = [](size_t b) { return (b + 255) & ~size_t(255); };
   const size_t b_bucket = al(sizeof(int32_t) * n_reads);
   const size_t b_hist = al(sizeof(int64_t) * ladder_hist_entries(n_reads, nbk));
@@ -150,9 +187,29 @@ extern "C" rope_status rope_ladder_map(const rope_ladder* lad, const uint8_t* se
   const size_t b_f32 = al(sizeof(float) * 2 * D * n_reads);
   const size_t b_norm = al(sizeof(float) * (1 + m) * n_reads);
   const size_t b_bf16 = bf16 ? al(sizeof(uint16_t) * 2 * D * n_reads) : 0;
-  uint8_t* scratch = nullptr;
-  st = host_pool_alloc(c, (void**)&scratch, b_bucket + b_hist + b_sizes + b_perm + b_f32 + b_norm + b_bf16, stream);
-  if (st != ROPE_OK) return st;
+  const size_t need = b_bucket + b_hist + b_sizes + b_perm + b_f32 + b_norm + b_bf16;
+  // the previous call (maybe on another stream) is done with the scratch
+  if (L->done_recorded) cudaStreamWaitEvent(stream, L->done, 0);
+  auto fail_prof = [&](rope_status s) {
+    if (slot >= 0)
+      for (int w = 1; w <= 3; ++w) host_prof_mark(slot, w, stream);
+    return s;
+  };
+  cudaError_t e = cudaSuccess;
+  if (need > L->scratch_bytes) {
+    if ((e = cudaStreamSynchronize(stream)) != cudaSuccess)
+      return fail_prof(host_fail(ROPE_ERR_CUDA, "ladder: %s", cudaGetErrorString(e)));
+    drop_graphs(L);  // they refer to the old block
+    if (L->scratch) cudaFree(L->scratch);
+    L->scratch = nullptr;
+    L->scratch_bytes = 0;
+    if ((e = cudaMalloc(&L->scratch, need + need / 4)) != cudaSuccess) {
+      cudaGetLastError();
+      return fail_prof(host_fail(ROPE_ERR_OOM, "ladder scratch of %zu bytes: %s", need, cudaGetErrorString(e)));
+    }
+    L->scratch_bytes = need + need / 4;
+  }
+  uint8_t* scratch = L->scratch;
   int32_t* bucket = reinterpret_cast<int32_t*>(scratch);
   int64_t* hist = reinterpret_cast<int64_t*>(scratch + b_bucket);
   int64_t* sizes = reinterpret_cast<int64_t*>(scratch + b_bucket + b_hist);
@@ -162,61 +219,131 @@ extern "C" rope_status rope_ladder_map(const rope_ladder* lad, const uint8_t* se
   uint16_t* emb_bf16 =
       bf16 ? reinterpret_cast<uint16_t*>(scratch + b_bucket + b_hist + b_sizes + b_perm + b_f32 + b_norm) : nullptr;
 
-  auto finish = [&](rope_status s) {
-    cudaFreeAsync(scratch, stream);
-    if (slot >= 0 && s != ROPE_OK)
-      for (int w = 1; w <= 3; ++w) host_prof_mark(slot, w, stream);
-    return s;
-  };
-  cudaError_t e = launch_fill_empty(out_win, out_score, n_reads * opts->k, stream);
+  e = launch_fill_empty(out_win, out_score, n_reads * opts->k, stream);
   if (e == cudaSuccess)
     e = launch_ladder_sort(offsets, n_reads, lad->lens_dev, nbk, bucket, out_len, hist, sizes, sizes + nbk, perm,
                            stream);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(lad->sizes_host, sizes, sizeof(int64_t) * 2 * nbk, cudaMemcpyDeviceToHost, stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
-  if (e != cudaSuccess) return finish(host_fail(ROPE_ERR_CUDA, "ladder bucketing: %s", cudaGetErrorString(e)));
+  if (e != cudaSuccess) return fail_prof(host_fail(ROPE_ERR_CUDA, "ladder bucketing: %s", cudaGetErrorString(e)));
   host_prof_mark(slot, 1, stream);
 
-  // fork: each non-empty bucket on an internal stream, round robin
-  if ((e = cudaEventRecord(lad->fork, stream)) != cudaSuccess)
-    return finish(host_fail(ROPE_ERR_CUDA, "ladder fork: %s", cudaGetErrorString(e)));
-  bool used[kLadderStreams] = {};
+  // the buckets' work: each non-empty bucket on an internal stream, round robin
+  struct Work {
+    int j;
+    int64_t base, cnt;
+    int si;
+  };
+  std::vector<Work> work;
   int next = 0;
-  st = ROPE_OK;
-  for (int j = 0; j < nbk && st == ROPE_OK; ++j) {
-    const int64_t base = lad->sizes_host[j], cnt = lad->sizes_host[nbk + j];
-    if (cnt <= 0) continue;
-    const int si = next++ % kLadderStreams;
-    cudaStream_t s = lad->streams[si];
-    if (!used[si]) {
-      used[si] = true;
-      if ((e = cudaStreamWaitEvent(s, lad->fork, 0)) != cudaSuccess) {
-        st = host_fail(ROPE_ERR_CUDA, "ladder fork: %s", cudaGetErrorString(e));
+  for (int j = 0; j < nbk; ++j) {
+    const int64_t cnt = lad->sizes_host[nbk + j];
+    if (cnt > 0) work.push_back(Work{j, lad->sizes_host[j], cnt, next++ % kLadderStreams});
+  }
+  // Enqueues every bucket; with arenas, each scan's candidate lists go to its
+  // stream's arena (no allocation, no tuning), as a captured graph needs.
+  auto enqueue = [&](bool arenas) -> rope_status {
+    cudaError_t ee;
+    if ((ee = cudaEventRecord(lad->fork, stream)) != cudaSuccess)
+      return host_fail(ROPE_ERR_CUDA, "ladder fork: %s", cudaGetErrorString(ee));
+    bool used[kLadderStreams] = {};
+    rope_status rs = ROPE_OK;
+    for (const Work& w : work) {
+      cudaStream_t s = lad->streams[w.si];
+      if (!used[w.si]) {
+        used[w.si] = true;
+        if ((ee = cudaStreamWaitEvent(s, lad->fork, 0)) != cudaSuccess) {
+          rs = host_fail(ROPE_ERR_CUDA, "ladder fork: %s", cudaGetErrorString(ee));
+          break;
+        }
+      }
+      const rope_index* ij = lad->idx[w.j];
+      float* f32 = emb_f32 + w.base * 2 * D;
+      uint16_t* b16 = bf16 ? emb_bf16 + w.base * 2 * D : nullptr;
+      float* nr = norms + w.base * (1 + m);
+      ee = launch_encode_reads(ij->enc, seqs, offsets, w.cnt, f32, b16, nr, c->status, s, perm + w.base);
+      if (ee != cudaSuccess) {
+        rs = host_fail(ROPE_ERR_CUDA, "ladder encode: %s", cudaGetErrorString(ee));
         break;
       }
+      ExtCandidates ext{L->arena[w.si], L->arena_bytes[w.si]};
+      rs = score_topk_impl(ij, f32, b16, nr, w.cnt, opts, out_win, out_score, s, -1, perm + w.base,
+                           arenas ? &ext : nullptr);
+      if (rs != ROPE_OK) break;
     }
-    const rope_index* ij = lad->idx[j];
-    float* f32 = emb_f32 + base * 2 * D;
-    uint16_t* b16 = bf16 ? emb_bf16 + base * 2 * D : nullptr;
-    float* nr = norms + base * (1 + m);
-    e = launch_encode_reads(ij->enc, seqs, offsets, cnt, f32, b16, nr, c->status, s, perm + base);
-    if (e != cudaSuccess) {
-      st = host_fail(ROPE_ERR_CUDA, "ladder encode: %s", cudaGetErrorString(e));
-      break;
+    // join every stream that took work, even after an error
+    for (int i = 0; i < kLadderStreams; ++i) {
+      if (!used[i]) continue;
+      cudaEventRecord(lad->join[i], lad->streams[i]);
+      cudaStreamWaitEvent(stream, lad->join[i], 0);
     }
-    st = score_topk_impl(ij, f32, b16, nr, cnt, opts, out_win, out_score, s, -1, perm + base);
+    return rs;
+  };
+
+  std::vector<int64_t> key = {n_reads, (int64_t)(uintptr_t)seqs, (int64_t)(uintptr_t)offsets,
+                              (int64_t)(uintptr_t)out_win, (int64_t)(uintptr_t)out_score, opts->k, opts->sep,
+                              opts->precision, opts->rescore, opts->cand_depth, opts->rescore_depth, opts->n_ranges};
+  for (const Work& w : work) key.push_back(w.cnt);
+  st = ROPE_OK;
+  auto it = L->graphs.find(key);
+  if (it != L->graphs.end()) {
+    if ((e = cudaGraphLaunch(it->second, stream)) != cudaSuccess)
+      st = host_fail(ROPE_ERR_CUDA, "ladder graph launch: %s", cudaGetErrorString(e));
+  } else if (L->seen.count(key) && !L->no_graph.count(key)) {
+    // second call with this key: size the arenas, capture, launch
+    size_t want[kLadderStreams] = {};
+    for (const Work& w : work) {
+      size_t b = 0;
+      if ((st = topk_cand_bytes(lad->idx[w.j], w.cnt, opts, &b)) != ROPE_OK) return fail_prof(st);
+      want[w.si] = std::max(want[w.si], b);
+    }
+    for (int i = 0; i < kLadderStreams && st == ROPE_OK; ++i) {
+      if (want[i] <= L->arena_bytes[i]) continue;
+      cudaStreamSynchronize(stream);
+      drop_graphs(L);
+      L->seen.insert(key);
+      if (L->arena[i]) cudaFree(L->arena[i]);
+      L->arena[i] = nullptr;
+      L->arena_bytes[i] = 0;
+      if ((e = cudaMalloc(&L->arena[i], want[i])) != cudaSuccess) {
+        cudaGetLastError();
+        st = host_fail(ROPE_ERR_OOM, "ladder candidate arena of %zu bytes: %s", want[i], cudaGetErrorString(e));
+        break;
+      }
+      L->arena_bytes[i] = want[i];
+    }
+    if (st != ROPE_OK) return fail_prof(st);
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    e = cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal);
+    rope_status cs = ROPE_OK;
+    if (e == cudaSuccess) {
+      cs = enqueue(true);
+      const cudaError_t ee = cudaStreamEndCapture(stream, &graph);
+      if (e == cudaSuccess) e = ee;
+    }
+    if (e == cudaSuccess && cs == ROPE_OK) e = cudaGraphInstantiate(&exec, graph, 0);
+    if (graph) cudaGraphDestroy(graph);
+    if (e == cudaSuccess && cs == ROPE_OK && exec) {
+      L->graphs[key] = exec;
+      if ((e = cudaGraphLaunch(exec, stream)) != cudaSuccess)
+        st = host_fail(ROPE_ERR_CUDA, "ladder graph launch: %s", cudaGetErrorString(e));
+    } else {
+      // capture refused: remember it and run the buckets eagerly
+      cudaGetLastError();
+      if (exec) cudaGraphExecDestroy(exec);
+      L->no_graph.insert(key);
+      st = enqueue(false);
+    }
+  } else {
+    L->seen.insert(key);
+    st = enqueue(false);
   }
-  // join every stream that took work, even after an error, so the scratch is
-  // not released while a bucket still runs
-  for (int i = 0; i < kLadderStreams; ++i) {
-    if (!used[i]) continue;
-    cudaEventRecord(lad->join[i], lad->streams[i]);
-    cudaStreamWaitEvent(stream, lad->join[i], 0);
-  }
-  if (st != ROPE_OK) return finish(st);
+  if (st != ROPE_OK) return fail_prof(st);
   host_prof_mark(slot, 2, stream);
-  cudaFreeAsync(scratch, stream);
+  cudaEventRecord(L->done, stream);
+  L->done_recorded = true;
   host_prof_mark(slot, 3, stream);
   return ROPE_OK;
 }

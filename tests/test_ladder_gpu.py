@@ -107,3 +107,38 @@ def test_ladder_empty_and_all_short(lib, ladder_case):
     w, s, used = lib.rope_ladder_map(c["lad"], dev(short.seqs), dev(short.offsets), k=3)
     lib.rope_sync_status()
     assert (w.cpu() == -1).all() and torch.isneginf(s.cpu()).all() and (used.cpu() == -1).all()
+
+
+def test_ladder_graph_replay(lib, ladder_case):
+    """The second call with the same bucket sizes, buffers and options captures
+    the buckets' work in a CUDA graph and later calls replay it: every call
+    gives the first (eager) call's results, also after the reads change."""
+    c = ladder_case
+    n = c["rd"].n
+    out = (torch.empty((n, 4), dtype=torch.int64, device="cuda"), torch.empty((n, 4), dtype=torch.float32,
+                                                                              device="cuda"),
+           torch.empty((n,), dtype=torch.int32, device="cuda"))
+    runs = []
+    for _ in range(4):
+        lib.rope_ladder_map(c["lad"], c["seqs"], c["offs"], k=4, out=out)
+        lib.rope_sync_status()
+        runs.append(tuple(t.cpu().clone() for t in out))
+    for r in runs[1:]:
+        assert all(torch.equal(a, b) for a, b in zip(runs[0], r))
+    # same lengths (so the same bucket sizes), other letters: the replay sees the new reads
+    other = synth.reads(c["ref"], n, seed=77, length=600, sub_rate=0.032, indel_rate=0.048, lognormal_sigma=0.7,
+                        len_min=60, len_max=3000)
+    seqs2 = c["seqs"].clone()
+    for i in range(n):
+        a, b = int(c["rd"].offsets[i]), int(c["rd"].offsets[i + 1])
+        o = int(other.offsets[i])
+        m = min(b - a, int(other.offsets[i + 1]) - o)
+        seqs2[a:a + m] = torch.from_numpy(other.seqs[o:o + m]).cuda()
+    c["seqs"].copy_(seqs2)  # in place: the captured pointers stay valid
+    lib.rope_ladder_map(c["lad"], c["seqs"], c["offs"], k=4, out=out)
+    lib.rope_sync_status()
+    replay = tuple(t.cpu().clone() for t in out)
+    fresh = lib.rope_ladder_map(c["lad"], c["seqs"], c["offs"], k=4)  # new output buffers: eager
+    lib.rope_sync_status()
+    assert all(torch.equal(a, b.cpu()) for a, b in zip(replay, fresh))
+    assert not torch.equal(replay[0], runs[0][0])
