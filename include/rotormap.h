@@ -352,6 +352,9 @@ rope_status rope_ladder_create(const rope_params* p, const uint8_t* ref, int64_t
 void rope_ladder_free(rope_ladder* lad);
 /* number of lengths; bucket j's index (owned by the ladder; NULL out of range) */
 int32_t rope_ladder_size(const rope_ladder* lad);
+/* number of captured CUDA graphs the ladder holds (one per repeated key of
+ * bucket sizes, buffers and options; see rope_ladder_map) */
+int32_t rope_ladder_graph_count(const rope_ladder* lad);
 const rope_index* rope_ladder_bucket(const rope_ladder* lad, int32_t j);
 
 /* Maps reads of any length: per read the bucket's k best window starts and
@@ -360,8 +363,11 @@ const rope_index* rope_ladder_bucket(const rope_ladder* lad, int32_t j);
  * receives the window length used, -1 for a read shorter than n_min, whose
  * outputs are all (-1, -inf). Synchronises `stream` once (after bucketing the
  * reads on the device, to read back the bucket sizes); the buckets then run on
- * the ladder's own streams and `stream` waits for them before returning. Not
- * for concurrent calls on one ladder from several host threads. */
+ * the ladder's own streams and `stream` waits for them before returning. The
+ * ladder keeps the call's scratch; the second call with the same bucket sizes,
+ * read and output buffers and options captures the buckets' work in a CUDA
+ * graph, later such calls replay it (inputs may change in place). Not for
+ * concurrent calls on one ladder from several host threads. */
 rope_status rope_ladder_map(const rope_ladder* lad, const uint8_t* seqs, const int64_t* offsets, int64_t n_reads,
                             const rope_score_opts* opts, int64_t* out_win, float* out_score, int32_t* out_len,
                             cudaStream_t stream);

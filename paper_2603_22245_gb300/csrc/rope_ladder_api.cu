@@ -151,6 +151,10 @@ extern "C" rope_status rope_ladder_create(const rope_params* p, const uint8_t* r
   return ROPE_OK;
 }
 
+extern "C" int32_t rope_ladder_graph_count(const rope_ladder* lad) {
+  return lad ? (int32_t)lad->graphs.size() : 0;
+}
+
 extern "C" int32_t rope_ladder_size(const rope_ladder* lad) { return lad ? (int32_t)lad->lens.size() : 0; }
 
 extern "C" const rope_index* rope_ladder_bucket(const rope_ladder* lad, int32_t j) {

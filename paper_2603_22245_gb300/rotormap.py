@@ -83,6 +83,7 @@ EXPORTS = {
     "rope_ladder_create": ([_P, _P, _I64, _I32, _I32, _I32, _P, _P], ctypes.c_int),
     "rope_ladder_free": ([_P], None),
     "rope_ladder_size": ([_P], _I32),
+    "rope_ladder_graph_count": ([_P], _I32),
     "rope_ladder_bucket": ([_P, _I32], _P),
     "rope_ladder_map": ([_P, _P, _P, _I64, _P, _P, _P, _P, _P], ctypes.c_int),
     "rope_merge_shards_host": ([_P, _P, _I32, _I64, _I32, _I32, _I32, _P, _P], ctypes.c_int),
@@ -376,6 +377,9 @@ class Ladder:
         if not h:
             raise IndexError(j)
         return Index(h, dataclasses.replace(self.params, window_len=self.lengths[j]), owner=self)
+
+    def graph_count(self) -> int:
+        return load().rope_ladder_graph_count(self.handle)
 
     def free(self):
         if self.handle:

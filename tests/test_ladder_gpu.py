@@ -125,6 +125,7 @@ def test_ladder_graph_replay(lib, ladder_case):
         runs.append(tuple(t.cpu().clone() for t in out))
     for r in runs[1:]:
         assert all(torch.equal(a, b) for a, b in zip(runs[0], r))
+    assert c["lad"].graph_count() >= 1  # the buckets' work was captured
     # same lengths (so the same bucket sizes), other letters: the replay sees the new reads
     other = synth.reads(c["ref"], n, seed=77, length=600, sub_rate=0.032, indel_rate=0.048, lognormal_sigma=0.7,
                         len_min=60, len_max=3000)
