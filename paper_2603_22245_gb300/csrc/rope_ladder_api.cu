@@ -14,6 +14,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <map>
 #include <set>
 #include <vector>
@@ -245,11 +246,21 @@ extern "C" rope_status rope_ladder_map(const rope_ladder* lad, const uint8_t* se
     const int64_t cnt = lad->sizes_host[nbk + j];
     if (cnt > 0) work.push_back(Work{j, lad->sizes_host[j], cnt, next++ % kLadderStreams});
   }
+  // ROPE_GRAPH_LOG=1: report where a capture gets invalidated
+  const bool log_graph = getenv("ROPE_GRAPH_LOG") != nullptr;
+  auto capture_broken = [&](cudaStream_t s, const char* step, int j) {
+    cudaStreamCaptureStatus cst = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cst) != cudaSuccess || cst == cudaStreamCaptureStatusInvalidated) {
+      fprintf(stderr, "rotormap ladder: capture invalidated after the %s of bucket %d\n", step, j);
+      return true;
+    }
+    return false;
+  };
   // Enqueues every bucket; with arenas, each scan's candidate lists go to its
   // stream's arena (no allocation, no tuning), as a captured graph needs.
-  auto enqueue = [&](bool arenas) -> rope_status {
+  auto enqueue = [&](bool arenas, cudaStream_t origin) -> rope_status {
     cudaError_t ee;
-    if ((ee = cudaEventRecord(lad->fork, stream)) != cudaSuccess)
+    if ((ee = cudaEventRecord(lad->fork, origin)) != cudaSuccess)
       return host_fail(ROPE_ERR_CUDA, "ladder fork: %s", cudaGetErrorString(ee));
     bool used[kLadderStreams] = {};
     rope_status rs = ROPE_OK;
@@ -257,7 +268,7 @@ extern "C" rope_status rope_ladder_map(const rope_ladder* lad, const uint8_t* se
       cudaStream_t s = lad->streams[w.si];
       if (!used[w.si]) {
         used[w.si] = true;
-        if ((ee = cudaStreamWaitEvent(s, lad->fork, 0)) != cudaSuccess) {
+        if (s != origin && (ee = cudaStreamWaitEvent(s, lad->fork, 0)) != cudaSuccess) {
           rs = host_fail(ROPE_ERR_CUDA, "ladder fork: %s", cudaGetErrorString(ee));
           break;
         }
@@ -272,15 +283,17 @@ extern "C" rope_status rope_ladder_map(const rope_ladder* lad, const uint8_t* se
         break;
       }
       ExtCandidates ext{L->arena[w.si], L->arena_bytes[w.si]};
+      if (arenas && log_graph && capture_broken(s, "encode", w.j)) break;
       rs = score_topk_impl(ij, f32, b16, nr, w.cnt, opts, out_win, out_score, s, -1, perm + w.base,
                            arenas ? &ext : nullptr);
       if (rs != ROPE_OK) break;
+      if (arenas && log_graph && capture_broken(s, "scan/merge", w.j)) break;
     }
     // join every stream that took work, even after an error
     for (int i = 0; i < kLadderStreams; ++i) {
-      if (!used[i]) continue;
+      if (!used[i] || lad->streams[i] == origin) continue;
       cudaEventRecord(lad->join[i], lad->streams[i]);
-      cudaStreamWaitEvent(stream, lad->join[i], 0);
+      cudaStreamWaitEvent(origin, lad->join[i], 0);
     }
     return rs;
   };
@@ -320,11 +333,14 @@ extern "C" rope_status rope_ladder_map(const rope_ladder* lad, const uint8_t* se
     if (st != ROPE_OK) return fail_prof(st);
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
-    e = cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal);
+    // captured from the ladder's first stream (the caller's stream may be the
+    // legacy default stream, which cannot be captured); launched on the caller's
+    cudaStream_t origin = lad->streams[0];
+    e = cudaStreamBeginCapture(origin, cudaStreamCaptureModeThreadLocal);
     rope_status cs = ROPE_OK;
     if (e == cudaSuccess) {
-      cs = enqueue(true);
-      const cudaError_t ee = cudaStreamEndCapture(stream, &graph);
+      cs = enqueue(true, origin);
+      const cudaError_t ee = cudaStreamEndCapture(origin, &graph);
       if (e == cudaSuccess) e = ee;
     }
     if (e == cudaSuccess && cs == ROPE_OK) e = cudaGraphInstantiate(&exec, graph, 0);
@@ -335,14 +351,17 @@ extern "C" rope_status rope_ladder_map(const rope_ladder* lad, const uint8_t* se
         st = host_fail(ROPE_ERR_CUDA, "ladder graph launch: %s", cudaGetErrorString(e));
     } else {
       // capture refused: remember it and run the buckets eagerly
+      if (getenv("ROPE_GRAPH_LOG"))
+        fprintf(stderr, "rotormap ladder: no graph (capture: %s; enqueue: %s)\n", cudaGetErrorString(e),
+                cs == ROPE_OK ? "ok" : rope_last_error());
       cudaGetLastError();
       if (exec) cudaGraphExecDestroy(exec);
       L->no_graph.insert(key);
-      st = enqueue(false);
+      st = enqueue(false, stream);
     }
   } else {
     L->seen.insert(key);
-    st = enqueue(false);
+    st = enqueue(false, stream);
   }
   if (st != ROPE_OK) return fail_prof(st);
   host_prof_mark(slot, 2, stream);

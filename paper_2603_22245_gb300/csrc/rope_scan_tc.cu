@@ -544,17 +544,42 @@ using TcShape64 = TcShape<64, 2, 64, 2, 2, 8, 1, false>;
 // Dynamic shared memory one block of this kernel may take: the device's
 // opt-in maximum per block less the kernel's static shared memory (barriers,
 // phase tables). 0 if the attributes cannot be read.
+// Read once per device and kept (so that launches made while a stream is
+// being captured into a graph query nothing).
+constexpr int kMaxDevices = 64;
+
 template <class Sh, bool kDense>
 static size_t tc_dyn_limit() {
+  static size_t cached[kMaxDevices] = {};  // value + 1, 0 = not read yet
   int dev = 0, optin = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+    cudaGetLastError();
+    return 0;
+  }
+  if (cached[dev]) return cached[dev] - 1;
   cudaFuncAttributes fa{};
-  if (cudaGetDevice(&dev) != cudaSuccess ||
-      cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess ||
+  if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess ||
       cudaFuncGetAttributes(&fa, scan_tc_kernel<Sh, kDense>) != cudaSuccess) {
     cudaGetLastError();
     return 0;
   }
-  return optin > (int)fa.sharedSizeBytes ? (size_t)optin - fa.sharedSizeBytes : 0;
+  const size_t v = optin > (int)fa.sharedSizeBytes ? (size_t)optin - fa.sharedSizeBytes : 0;
+  cached[dev] = v + 1;
+  return v;
+}
+
+// Raises the kernel's dynamic shared-memory limit on the current device when
+// a launch needs more than it was last set to (once per size increase).
+template <class Sh, bool kDense>
+static cudaError_t tc_reserve_smem(size_t smem) {
+  static size_t set[kMaxDevices] = {};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev >= 0 && dev < kMaxDevices && set[dev] >= smem) return cudaSuccess;
+  e = cudaFuncSetAttribute(scan_tc_kernel<Sh, kDense>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e == cudaSuccess && dev >= 0 && dev < kMaxDevices) set[dev] = smem;
+  return e;
 }
 
 int scan_tc_supported(int D) { return D == 32 || D == 64; }
@@ -613,7 +638,7 @@ static cudaError_t launch_tc(const DevIndex& ix, const ScanArgs& a, int num_sms,
   while (smem > limit && nb > 1) smem = tc_smem_bytes<Sh>(ix, a.cand_depth, kDense, nb >>= 1, &L);
   if (smem > limit) return cudaErrorInvalidValue;
   auto kern = scan_tc_kernel<Sh, kDense>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = tc_reserve_smem<Sh, kDense>(smem);
   if (e != cudaSuccess) {
     cudaGetLastError();  // not sticky: leave no pending error for later launches
     return e;
