@@ -245,6 +245,42 @@ def rerank_leg(rm, idx, ref, wl, args):
             "errors": "0-15% per read (2:1 substitutions : indel events)"}
 
 
+def encode_roofline(rm, p, dref, ref, rd, n_reads):
+    """HBM roofline of the encode pass: the reference's 2-bit packing (1 B in +
+    0.25 B out per letter) and the read encoding (N letters in, FP32 + BF16
+    encodings and 1+m norms out per read), CUDA events around 10 launches."""
+    import torch
+
+    peaks, src = measured_peaks()
+    peak = peaks["hbm_gbs"]
+
+    def timed(fn, reps=10):
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps / 1000.0
+
+    L = dref.numel()
+    t_pack = timed(lambda: rm.rope_pack_2bit(dref))
+    b_pack = L * 1.25
+    seqs = torch.from_numpy(rd.seqs).cuda()
+    offs = torch.from_numpy(rd.offsets[:n_reads + 1].copy()).cuda()
+    t_enc = timed(lambda: rm.rope_encode_reads(p, seqs, offs))
+    D = p.dim
+    b_enc = n_reads * (p.window_len + 2 * D * 4 + 2 * D * 2 + (1 + p.m) * 4) + (n_reads + 1) * 8
+    rm.rope_sync_status()
+    return {"bound": "hbm", "peak": peak, "unit": "GB/s", "peak_source": f"{src} hbm_gbs",
+            "pack": {"bytes": b_pack, "ms": t_pack * 1e3, "achieved": b_pack / t_pack / 1e9,
+                     "frac": b_pack / t_pack / 1e9 / peak, "letters": L},
+            "encode_reads": {"bytes": b_enc, "ms": t_enc * 1e3, "achieved": b_enc / t_enc / 1e9,
+                             "frac": b_enc / t_enc / 1e9 / peak, "reads": n_reads}}
+
+
 def run_reference(args, wl):
     """--impl reference: the FP64 oracle on this host's cores, K steps of a bounded sample."""
     ws, rank, _ = dist_setup(args)
@@ -398,6 +434,7 @@ def main():
     idx = rm.rope_encode_reference(p, dref)
     torch.cuda.synchronize()
     index_s = time.perf_counter() - t0
+    encode_pass = encode_roofline(rm, p, dref, ref, rd, min(args.batch, rd.n))
     del dref
     W = idx.n_windows
     seqs = torch.from_numpy(rd.seqs).cuda()
@@ -540,7 +577,7 @@ def main():
                    f"reads sharded over {ws} GPU(s)",
                    "scan_tiles": None if tuned is None else {"variant": tuned[0], "items_per_sm": tuned[1],
                                                               "tuned_scan_ms": tuned[2]}},
-        "reads_per_s": reads_s, "top1_acc": acc_bf16, "fp32_plain": fp32,
+        "reads_per_s": reads_s, "top1_acc": acc_bf16, "fp32_plain": fp32, "encode_pass": encode_pass,
         "speedup_vs_fp32_plain": value / ws / fp32["value"],
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "reranker": reranker, "gpu_launches": 3 * args.steps, "clocks": clocks,
     }

@@ -22,25 +22,43 @@ __device__ __forceinline__ uint32_t pack4(uint32_t x, int& bad) {
 
 // One output word (16 letters) per thread; 16-byte vector loads when aligned.
 // HBM-bound: 1 byte in and 1/4 byte out per letter.
+// One thread packs kPackWords consecutive 16-letter words per step: their
+// four 16-byte loads are issued together, so enough bytes are in flight to
+// keep HBM busy; the ragged tail and unaligned inputs take the byte path.
+constexpr int kPackWords = 4;
+
+__device__ __forceinline__ uint32_t pack_bytes(const uint8_t* seq, int64_t base, int64_t len, int& bad) {
+  uint32_t word = 0;
+  for (int i = 0; i < 16 && base + i < len; ++i) {
+    const uint32_t c = letter_code(seq[base + i]);
+    bad |= (c > 3);
+    word |= (c & 3u) << (2 * i);
+  }
+  return word;
+}
+
 __global__ void pack_kernel(const uint8_t* __restrict__ seq, int64_t len, uint32_t* __restrict__ out,
                             int64_t n_words, int* status) {
-  const bool aligned = (((uintptr_t)seq) & 15u) == 0;
+  // vector loads and stores need 16-byte aligned input and output
+  const bool aligned = ((((uintptr_t)seq) | ((uintptr_t)out)) & 15u) == 0;
   int bad = 0;
-  for (int64_t w = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; w < n_words;
-       w += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t base = w * 16;
-    uint32_t word = 0;
-    if (aligned && base + 16 <= len) {
-      const uint4 v = __ldg(reinterpret_cast<const uint4*>(seq + base));
-      word = pack4(v.x, bad) | (pack4(v.y, bad) << 8) | (pack4(v.z, bad) << 16) | (pack4(v.w, bad) << 24);
+  const int64_t n_groups = (n_words + kPackWords - 1) / kPackWords;
+  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < n_groups;
+       g += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t w0 = g * kPackWords;
+    if (aligned && (w0 + kPackWords) * 16 <= len) {
+      uint4 v[kPackWords];
+#pragma unroll
+      for (int q = 0; q < kPackWords; ++q) v[q] = __ldg(reinterpret_cast<const uint4*>(seq + (w0 + q) * 16));
+      uint32_t wd[kPackWords];
+#pragma unroll
+      for (int q = 0; q < kPackWords; ++q)
+        wd[q] = pack4(v[q].x, bad) | (pack4(v[q].y, bad) << 8) | (pack4(v[q].z, bad) << 16) |
+                (pack4(v[q].w, bad) << 24);
+      *reinterpret_cast<uint4*>(out + w0) = make_uint4(wd[0], wd[1], wd[2], wd[3]);
     } else {
-      for (int i = 0; i < 16 && base + i < len; ++i) {
-        const uint32_t c = letter_code(seq[base + i]);
-        bad |= (c > 3);
-        word |= (c & 3u) << (2 * i);
-      }
+      for (int q = 0; q < kPackWords && w0 + q < n_words; ++q) out[w0 + q] = pack_bytes(seq, (w0 + q) * 16, len, bad);
     }
-    out[w] = word;
   }
   if (bad) set_status(status, kStatusBadBase);
 }
@@ -49,7 +67,8 @@ cudaError_t launch_pack(const uint8_t* seq, int64_t len, uint32_t* out, int* sta
   const int64_t n_words = (len + 15) / 16;
   if (n_words == 0) return cudaSuccess;
   const int threads = 256;
-  int64_t blocks = (n_words + threads - 1) / threads;
+  const int64_t n_groups = (n_words + kPackWords - 1) / kPackWords;
+  int64_t blocks = (n_groups + threads - 1) / threads;
   if (blocks > 152 * 32) blocks = 152 * 32;
   pack_kernel<<<(unsigned)blocks, threads, 0, st>>>(seq, len, out, n_words, status);
   return cudaGetLastError();
@@ -94,7 +113,105 @@ __device__ __forceinline__ uint32_t head_letter(const uint8_t* seq, int64_t len,
   return c > 3 ? c : 3u - c;  // A<->T, C<->G
 }
 
+// One warp per read; lane l owns entries g = l, l + 32, ... of the D complex
+// entries (band g / 4^t, bin g % 4^t) in registers. The bins of 32 locations
+// are computed one per lane and broadcast in location order; the lane owning
+// (band k, bin b) adds e^{2 pi i f_k loc / N} for each location whose s-mer
+// falls in bin b, so every entry is summed in location order with no shared
+// memory and no warp barrier per location.
+constexpr int kEncMaxPerLane = kMaxScanDim / 32;
+
 __global__ void encode_reads_kernel(EncTables tb, const uint8_t* __restrict__ seqs,
+                                    const int64_t* __restrict__ offsets, int64_t n, float* __restrict__ emb_f32,
+                                    __nv_bfloat16* __restrict__ emb_bf16, float* __restrict__ norms, int* status,
+                                    const int64_t* __restrict__ perm, bool rc) {
+  const int lane = threadIdx.x & 31;
+  const int warp = threadIdx.x >> 5;
+  const int wpb = blockDim.x >> 5;
+  const int n_loc = tb.N - tb.s + 1;
+  const int E = (tb.D + 31) / 32;  // entries per lane
+  int band[kEncMaxPerLane], bin[kEncMaxPerLane];
+#pragma unroll
+  for (int e = 0; e < kEncMaxPerLane; ++e) {
+    const int g = lane + 32 * e;
+    band[e] = g < tb.D ? g / tb.nb : 0;
+    bin[e] = g < tb.D ? g % tb.nb : -1;  // -1: no entry
+  }
+  for (int64_t r = (int64_t)blockIdx.x * wpb + warp; r < n; r += (int64_t)gridDim.x * wpb) {
+    const int64_t src = perm ? perm[r] : r;
+    const int64_t start = offsets[src];
+    const int64_t len = offsets[src + 1] - start;
+    const uint8_t* seq = seqs + start;
+    float ar[kEncMaxPerLane], ai[kEncMaxPerLane];
+#pragma unroll
+    for (int e = 0; e < kEncMaxPerLane; ++e) ar[e] = ai[e] = 0.f;
+    bool ok = len >= tb.N;
+    if (!ok) {
+      if (lane == 0) set_status(status, kStatusShortRead);
+    } else {
+      int bad = 0;
+      for (int i = lane; i < tb.N; i += 32) bad |= head_letter(seq, len, i, rc) > 3;
+      if (__any_sync(0xffffffffu, bad)) {
+        ok = false;
+        if (lane == 0) set_status(status, kStatusBadBase);
+      }
+    }
+    if (ok) {
+      for (int loc0 = 0; loc0 < n_loc; loc0 += 32) {
+        const int loc = loc0 + lane;
+        int b = -2;
+        if (loc < n_loc) {
+          uint32_t code = 0;
+          for (int i = 0; i < tb.s; ++i) code = code * 4u + (head_letter(seq, len, loc + i, rc) & 3u);
+          b = tb.map[code];
+        }
+        const int cnt = min(32, n_loc - loc0);
+        for (int jj = 0; jj < cnt; ++jj) {
+          const int bj = __shfl_sync(0xffffffffu, b, jj);
+#pragma unroll
+          for (int e = 0; e < kEncMaxPerLane; ++e) {
+            if (e < E && bin[e] == bj) {
+              const float2 ph = tb.phase[band[e] * n_loc + loc0 + jj];
+              ar[e] += ph.x;
+              ai[e] += ph.y;
+            }
+          }
+        }
+      }
+    }
+    // per-band squared norms, then the total
+    float total = 0.f;
+    for (int k = 0; k < tb.m; ++k) {
+      float part = 0.f;
+#pragma unroll
+      for (int e = 0; e < kEncMaxPerLane; ++e)
+        if (e < E && bin[e] >= 0 && band[e] == k) part = fmaf(ar[e], ar[e], fmaf(ai[e], ai[e], part));
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+      if (lane == 0) norms[r * (1 + tb.m) + 1 + k] = part;
+      total += part;
+    }
+    if (lane == 0) norms[r * (1 + tb.m)] = total;
+    const float inv = total > kZeroNorm2 ? rsqrtf(total) : 0.f;
+#pragma unroll
+    for (int e = 0; e < kEncMaxPerLane; ++e) {
+      const int g = lane + 32 * e;
+      if (e >= E || g >= tb.D) continue;
+      if (emb_f32) {
+        emb_f32[r * 2 * tb.D + g] = ar[e];
+        emb_f32[r * 2 * tb.D + tb.D + g] = ai[e];
+      }
+      if (emb_bf16) {
+        emb_bf16[r * 2 * tb.D + g] = __float2bfloat16_rn(ar[e] * inv);
+        emb_bf16[r * 2 * tb.D + tb.D + g] = __float2bfloat16_rn(ai[e] * inv);
+      }
+    }
+  }
+}
+
+// Encodings wider than kMaxScanDim complex entries: the accumulator in shared
+// memory, updated by the lane of each band for one location at a time.
+__global__ void encode_reads_wide_kernel(EncTables tb, const uint8_t* __restrict__ seqs,
                                     const int64_t* __restrict__ offsets, int64_t n, float* __restrict__ emb_f32,
                                     __nv_bfloat16* __restrict__ emb_bf16, float* __restrict__ norms, int* status,
                                     const int64_t* __restrict__ perm, bool rc) {
@@ -179,15 +296,24 @@ cudaError_t launch_encode_reads(const EncTables& tb, const uint8_t* seqs, const 
                                 float* emb_f32, uint16_t* emb_bf16, float* norms, int* status, cudaStream_t st,
                                 const int64_t* perm, bool rc) {
   if (n <= 0) return cudaSuccess;
+  if (tb.D <= kMaxScanDim) {
+    const int wpb = 8;
+    int64_t blocks = (n + wpb - 1) / wpb;
+    if (blocks > 152 * 64) blocks = 152 * 64;
+    encode_reads_kernel<<<(unsigned)blocks, wpb * 32, 0, st>>>(tb, seqs, offsets, n, emb_f32,
+                                                                 reinterpret_cast<__nv_bfloat16*>(emb_bf16), norms,
+                                                                 status, perm, rc);
+    return cudaGetLastError();
+  }
   int wpb = (int)(48 * 1024 / (tb.D * sizeof(float2)));
   if (wpb > 8) wpb = 8;
   if (wpb < 1) wpb = 1;
   const size_t smem = (size_t)wpb * tb.D * sizeof(float2);
   int64_t blocks = (n + wpb - 1) / wpb;
   if (blocks > 152 * 64) blocks = 152 * 64;
-  encode_reads_kernel<<<(unsigned)blocks, wpb * 32, smem, st>>>(tb, seqs, offsets, n, emb_f32,
-                                                                  reinterpret_cast<__nv_bfloat16*>(emb_bf16), norms,
-                                                                  status, perm, rc);
+  encode_reads_wide_kernel<<<(unsigned)blocks, wpb * 32, smem, st>>>(tb, seqs, offsets, n, emb_f32,
+                                                                       reinterpret_cast<__nv_bfloat16*>(emb_bf16),
+                                                                       norms, status, perm, rc);
   return cudaGetLastError();
 }
 

@@ -55,7 +55,7 @@ def cfg1_gpu(lib, cfg1):
 
 # ---------------------------------------------------------------- a1, a2
 
-@pytest.mark.parametrize("n", [1, 15, 16, 17, 1000, 100_003])
+@pytest.mark.parametrize("n", [1, 15, 16, 17, 63, 64, 65, 129, 1000, 100_003])
 def test_pack_bit_exact(lib, n):
     seq = synth.uniform_ref(n, 10 + n)
     seq[::7] = np.frombuffer(bytes(seq[::7]).lower(), dtype=np.uint8)
