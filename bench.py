@@ -248,7 +248,10 @@ def rerank_leg(rm, idx, ref, wl, args):
 def encode_roofline(rm, p, dref, ref, rd, n_reads):
     """HBM roofline of the encode pass: the reference's 2-bit packing (1 B in +
     0.25 B out per letter) and the read encoding (N letters in, FP32 + BF16
-    encodings and 1+m norms out per read), CUDA events around 10 launches."""
+    encodings and 1+m norms out per read), CUDA events around 10 launches.
+    The packing is timed on the reference repeated to >= 10^9 letters and the
+    encoding on every read of the workload, so that each launch moves enough
+    bytes for its time not to be the host's call overhead."""
     import torch
 
     peaks, src = measured_peaks()
@@ -265,15 +268,18 @@ def encode_roofline(rm, p, dref, ref, rd, n_reads):
         torch.cuda.synchronize()
         return e0.elapsed_time(e1) / reps / 1000.0
 
-    L = dref.numel()
-    t_pack = timed(lambda: rm.rope_pack_2bit(dref))
+    big = dref.repeat(max(1, -(-1_000_000_000 // dref.numel())))
+    L = big.numel()
+    t_pack = timed(lambda: rm.rope_pack_2bit(big))
     b_pack = L * 1.25
     seqs = torch.from_numpy(rd.seqs).cuda()
-    offs = torch.from_numpy(rd.offsets[:n_reads + 1].copy()).cuda()
+    n_reads = rd.n
+    offs = torch.from_numpy(rd.offsets).cuda()
     t_enc = timed(lambda: rm.rope_encode_reads(p, seqs, offs))
     D = p.dim
     b_enc = n_reads * (p.window_len + 2 * D * 4 + 2 * D * 2 + (1 + p.m) * 4) + (n_reads + 1) * 8
     rm.rope_sync_status()
+    del big
     return {"bound": "hbm", "peak": peak, "unit": "GB/s", "peak_source": f"{src} hbm_gbs",
             "pack": {"bytes": b_pack, "ms": t_pack * 1e3, "achieved": b_pack / t_pack / 1e9,
                      "frac": b_pack / t_pack / 1e9 / peak, "letters": L},

@@ -114,22 +114,29 @@ __device__ __forceinline__ uint32_t head_letter(const uint8_t* seq, int64_t len,
 }
 
 // One warp per read; lane l owns entries g = l, l + 32, ... of the D complex
-// entries (band g / 4^t, bin g % 4^t) in registers. The bins of 32 locations
-// are computed one per lane and broadcast in location order; the lane owning
-// (band k, bin b) adds e^{2 pi i f_k loc / N} for each location whose s-mer
-// falls in bin b, so every entry is summed in location order with no shared
-// memory and no warp barrier per location.
+// entries (band g / 4^t, bin g % 4^t) in registers. The locations are taken 32
+// at a time, one per lane; warp ballots of the bits of their bins tell each
+// lane which of the 32 locations fall in its entries' bins, and the lane adds
+// e^{2 pi i f_k loc / N} (phase table staged in shared memory) for those
+// locations in increasing order. Every entry is thus summed in location order
+// (the direct sum of §2.1-§2.3 in FP32, deterministic), with a warp cost per
+// 32 locations of a few ballots plus the largest bin's count.
 constexpr int kEncMaxPerLane = kMaxScanDim / 32;
+constexpr int kEncMaxBinBits = 8;  // bins per band up to 256
 
 __global__ void encode_reads_kernel(EncTables tb, const uint8_t* __restrict__ seqs,
                                     const int64_t* __restrict__ offsets, int64_t n, float* __restrict__ emb_f32,
                                     __nv_bfloat16* __restrict__ emb_bf16, float* __restrict__ norms, int* status,
                                     const int64_t* __restrict__ perm, bool rc) {
+  extern __shared__ float2 enc_phase[];  // [m * n_loc] phases, staged once per block
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
   const int wpb = blockDim.x >> 5;
   const int n_loc = tb.N - tb.s + 1;
   const int E = (tb.D + 31) / 32;  // entries per lane
+  const int bin_bits = 32 - __clz(tb.nb > 1 ? tb.nb - 1 : 1);
+  for (int i = threadIdx.x; i < tb.m * n_loc; i += blockDim.x) enc_phase[i] = tb.phase[i];
+  __syncthreads();
   int band[kEncMaxPerLane], bin[kEncMaxPerLane];
 #pragma unroll
   for (int e = 0; e < kEncMaxPerLane; ++e) {
@@ -159,22 +166,33 @@ __global__ void encode_reads_kernel(EncTables tb, const uint8_t* __restrict__ se
     if (ok) {
       for (int loc0 = 0; loc0 < n_loc; loc0 += 32) {
         const int loc = loc0 + lane;
-        int b = -2;
+        uint32_t b = 0;
         if (loc < n_loc) {
           uint32_t code = 0;
           for (int i = 0; i < tb.s; ++i) code = code * 4u + (head_letter(seq, len, loc + i, rc) & 3u);
-          b = tb.map[code];
+          b = (uint32_t)tb.map[code];
         }
-        const int cnt = min(32, n_loc - loc0);
-        for (int jj = 0; jj < cnt; ++jj) {
-          const int bj = __shfl_sync(0xffffffffu, b, jj);
+        // bit planes of the 32 locations' bins: the locations whose bin is
+        // B are the lanes that agree with B on every plane
+        const uint32_t valid = __ballot_sync(0xffffffffu, loc < n_loc);
+        uint32_t plane[kEncMaxBinBits];
 #pragma unroll
-          for (int e = 0; e < kEncMaxPerLane; ++e) {
-            if (e < E && bin[e] == bj) {
-              const float2 ph = tb.phase[band[e] * n_loc + loc0 + jj];
-              ar[e] += ph.x;
-              ai[e] += ph.y;
-            }
+        for (int i = 0; i < kEncMaxBinBits; ++i)
+          plane[i] = i < bin_bits ? __ballot_sync(0xffffffffu, (b >> i) & 1u) : 0u;
+#pragma unroll
+        for (int e = 0; e < kEncMaxPerLane; ++e) {
+          if (e >= E || bin[e] < 0) continue;
+          uint32_t hit = valid;
+#pragma unroll
+          for (int i = 0; i < kEncMaxBinBits; ++i)
+            if (i < bin_bits) hit &= ((bin[e] >> i) & 1) ? plane[i] : ~plane[i];
+          const float2* ph_row = enc_phase + band[e] * n_loc + loc0;
+          while (hit) {  // the matching locations in increasing order
+            const int j = __ffs(hit) - 1;
+            hit &= hit - 1u;
+            const float2 ph = ph_row[j];
+            ar[e] += ph.x;
+            ai[e] += ph.y;
           }
         }
       }
@@ -296,11 +314,12 @@ cudaError_t launch_encode_reads(const EncTables& tb, const uint8_t* seqs, const 
                                 float* emb_f32, uint16_t* emb_bf16, float* norms, int* status, cudaStream_t st,
                                 const int64_t* perm, bool rc) {
   if (n <= 0) return cudaSuccess;
-  if (tb.D <= kMaxScanDim) {
+  const size_t phase_bytes = (size_t)tb.m * (tb.N - tb.s + 1) * sizeof(float2);
+  if (tb.D <= kMaxScanDim && phase_bytes <= 48 * 1024) {
     const int wpb = 8;
     int64_t blocks = (n + wpb - 1) / wpb;
-    if (blocks > 152 * 64) blocks = 152 * 64;
-    encode_reads_kernel<<<(unsigned)blocks, wpb * 32, 0, st>>>(tb, seqs, offsets, n, emb_f32,
+    if (blocks > 152 * 16) blocks = 152 * 16;  // each block stages the phase table once
+    encode_reads_kernel<<<(unsigned)blocks, wpb * 32, phase_bytes, st>>>(tb, seqs, offsets, n, emb_f32,
                                                                  reinterpret_cast<__nv_bfloat16*>(emb_bf16), norms,
                                                                  status, perm, rc);
     return cudaGetLastError();
