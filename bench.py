@@ -13,6 +13,8 @@ timed region (the paper's "preloaded data").
 
   value       BF16 tensor-core read x window scores/s over all ranks
   fp32_plain  the FP32 CUDA-core scan on a read subset (same metric)
+  fp8_option  the same steps with the E4M3 tensor-core scan (rate, top-1
+              accuracy, scan roofline against twice the BF16 peak)
   top1_acc    fraction of planted reads whose top-1 window overlaps the truth
   e2e         the same metric through host buffers (H2D of the reads, D2H of
               the top-k) around every step
@@ -87,6 +89,7 @@ def parse():
     ap.add_argument("--workload", default="markov100M", choices=sorted(WORKLOADS))
     ap.add_argument("--batch", type=int, default=131072)
     ap.add_argument("--fp32-reads", type=int, default=4096)
+    ap.add_argument("--fp8-steps", type=int, default=2)
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--cpu-reads", type=int, default=32)
     ap.add_argument("--cpu-windows", type=int, default=1_000_000)
@@ -534,6 +537,36 @@ def main():
     fp32 = {"value": F * W / t32, "unit": UNIT, "reads_per_s": F / t32, "reads": F, "top1_acc": acc32,
             "bf16_top1_acc_same_reads": acc16_sub, "top1_window_agreement": agree}
 
+    # E4M3 option: the same steps with the FP8 tensor-core scan (same batches,
+    # same rescoring), its top-1 accuracy on the same planted reads
+    fp8 = None
+    if args.fp8_steps > 0:
+        step(0, precision="fp8")
+        rm.rope_sync_status()
+        rm.rope_profile_enable(args.fp8_steps)
+        e0.record()
+        tops8 = []
+        for i in range(args.fp8_steps):
+            w8, _ = step(i, precision="fp8", o=step_outs[i])
+            tops8.append(w8[:, 0])
+        e1.record()
+        torch.cuda.synchronize()
+        t8 = e0.elapsed_time(e1) / 1000.0
+        st8 = rm.rope_profile_read(args.fp8_steps)
+        rm.rope_profile_enable(0)
+        rm.rope_sync_status()
+        h8 = [np.abs(t.cpu().numpy() - true_pos[(i % n_batches) * B:(i % n_batches + 1) * B]) < wl["N"]
+              for i, t in enumerate(tops8)]
+        h16 = np.concatenate(hits[:args.fp8_steps])
+        scan8 = float(np.mean(st8[:, 1])) / 1000.0
+        peak8 = peak * 2.0  # E4M3 dense rate = 2x BF16 (nominal 4.5 vs 2.25 PFLOP/s)
+        fp8 = {"value": ws * args.fp8_steps * scores_step / t8, "unit": UNIT, "steps": args.fp8_steps,
+               "top1_acc": float(np.concatenate(h8).mean()), "bf16_top1_acc_same_reads": float(h16.mean()),
+               "scan_ms": scan8 * 1000.0,
+               "roofline": {"bound": "tensor", "achieved": flops / scan8 / 1e12, "peak": peak8, "unit": "TFLOP/s",
+                            "frac": flops / scan8 / 1e12 / peak8,
+                            "peak_source": f"{peak_src} bf16_tflops_sustained x 2 (nominal E4M3/BF16 ratio)"}}
+
     # end to end through host buffers: H2D reads, rope_map, D2H top-k, every step
     e2e = None
     if args.e2e_steps > 0:
@@ -583,7 +616,8 @@ def main():
                    f"reads sharded over {ws} GPU(s)",
                    "scan_tiles": None if tuned is None else {"variant": tuned[0], "items_per_sm": tuned[1],
                                                               "tuned_scan_ms": tuned[2]}},
-        "reads_per_s": reads_s, "top1_acc": acc_bf16, "fp32_plain": fp32, "encode_pass": encode_pass,
+        "reads_per_s": reads_s, "top1_acc": acc_bf16, "fp32_plain": fp32, "fp8_option": fp8,
+        "encode_pass": encode_pass,
         "speedup_vs_fp32_plain": value / ws / fp32["value"],
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "reranker": reranker, "gpu_launches": 3 * args.steps, "clocks": clocks,
     }

@@ -78,14 +78,20 @@ typedef struct {
   const uint16_t* bin_of_mer_host;
 } rope_params;
 
-/* Scoring precision */
-enum { ROPE_PREC_FP32 = 0, ROPE_PREC_BF16 = 1 };
+/* Scoring precision. ROPE_PREC_FP8 is the tensor-core scan with E4M3
+ * operands (kind::f8f6f4, FP32 accumulation): the read's BF16 encoding and the
+ * window's normalised encoding are each scaled by 2^5 and rounded to E4M3, and
+ * the scores are scaled back by 2^-20 (exact); it takes emb_bf16 like
+ * ROPE_PREC_BF16. Its raw scores carry the E4M3 rounding (3 mantissa bits);
+ * with rescore = 1 the reported scores are the FP32 re-scores as for BF16. */
+enum { ROPE_PREC_FP32 = 0, ROPE_PREC_BF16 = 1, ROPE_PREC_FP8 = 2 };
 
 /* Options of rope_score_topk.
  *   k          results per read, 1 <= k <= 32
  *   sep        0: plain top-k. sep > 0: at most one window per bucket
  *              floor(start/sep) (the best), then the best k buckets
- *   precision  ROPE_PREC_FP32 (CUDA cores) or ROPE_PREC_BF16 (tensor cores)
+ *   precision  ROPE_PREC_FP32 (CUDA cores), ROPE_PREC_BF16 or ROPE_PREC_FP8
+ *              (tensor cores)
  *   rescore    1: re-score the kept candidates by direct FP32 summation before
  *              the final ranking; 0: report the scan's own scores
  *   cand_depth candidates kept per read per window range (0 = 16); k..32
@@ -175,7 +181,7 @@ rope_status rope_encode_reads(const rope_params* p, const uint8_t* seqs, const i
  * k window starts (int64, j*stride) and fidelities (float), best first
  * (score descending, start ascending); missing entries are (-1, -inf).
  * emb_f32/norms come from rope_encode_reads; emb_bf16 is required for
- * ROPE_PREC_BF16. Uses scratch from the library's stream-ordered pool. */
+ * ROPE_PREC_BF16 and ROPE_PREC_FP8. Uses scratch from the library's stream-ordered pool. */
 rope_status rope_score_topk(const rope_index* idx, const float* emb_f32, const uint16_t* emb_bf16,
                             const float* norms, int64_t n_reads, const rope_score_opts* opts, int64_t* out_win,
                             float* out_score, cudaStream_t stream);

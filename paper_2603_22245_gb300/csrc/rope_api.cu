@@ -550,7 +550,7 @@ rope_status plan_scan(const rope_index* idx, int32_t precision, int64_t n_reads,
                       int32_t n_ranges_req, int num_sms, ScanPlan* out, int32_t tc_variant = 0) {
   const DevIndex& ix = idx->ix;
   ScanPlan pl;
-  pl.tc = precision == ROPE_PREC_BF16;
+  pl.tc = prec_tc(precision);
   int64_t sup;
   int group;
   if (pl.tc) {
@@ -584,6 +584,7 @@ rope_status plan_scan(const rope_index* idx, int32_t precision, int64_t n_reads,
   a.range_len = sup_per_range * sup;
   a.n_ranges = (int32_t)((n_sup + sup_per_range - 1) / sup_per_range);
   a.tc_variant = pl.tc ? tc_variant : 0;
+  a.fp8 = precision == ROPE_PREC_FP8;
   a.lists_per_range = pl.tc ? scan_tc_lists_per_range(ix.D, a.tc_variant) : 1;
   a.wait_limit_ns = wait_limit_ns();
   *out = pl;
@@ -618,10 +619,10 @@ rope_status check_opts(const rope_score_opts* o, rope_score_opts* v) {
 // speed does. ROPE_AUTOTUNE=0 (or rope_autotune_enable(0)) keeps the defaults.
 
 struct TuneKey {
-  int dev, D, stride, n_log2, g_log2, w_log2, cand_depth, sep_on;
+  int dev, D, stride, n_log2, g_log2, w_log2, cand_depth, sep_on, fp8;
   bool operator<(const TuneKey& o) const {
-    return std::tie(dev, D, stride, n_log2, g_log2, w_log2, cand_depth, sep_on) <
-           std::tie(o.dev, o.D, o.stride, o.n_log2, o.g_log2, o.w_log2, o.cand_depth, o.sep_on);
+    return std::tie(dev, D, stride, n_log2, g_log2, w_log2, cand_depth, sep_on, fp8) <
+           std::tie(o.dev, o.D, o.stride, o.n_log2, o.g_log2, o.w_log2, o.cand_depth, o.sep_on, o.fp8);
   }
 };
 struct TuneVal {
@@ -669,7 +670,8 @@ TuneKey tune_key(const rope_index* idx, int64_t n_reads, const rope_score_opts& 
   const DevIndex& ix = idx->ix;
   const int64_t groups = (n_reads + scan_tc_group(ix.D) - 1) / scan_tc_group(ix.D);
   return TuneKey{idx->device,         ix.D,        ix.stride, ilog2_ceil(ix.N), ilog2_ceil(groups),
-                 ilog2_ceil(scanned_windows(idx, o)), o.cand_depth, o.sep > 0};
+                 ilog2_ceil(scanned_windows(idx, o)), o.cand_depth, o.sep > 0,
+                 o.precision == ROPE_PREC_FP8};
 }
 
 int32_t ranges_for(int items_per_sm, int num_sms, int64_t n_groups) {
@@ -683,7 +685,7 @@ rope_status time_candidate(const rope_index* idx, const uint16_t* emb_bf16, cons
                            const rope_score_opts& o, Candidate* cand, DeviceCtx* c, cudaStream_t stream,
                            cudaEvent_t e0, cudaEvent_t e1, int reps, float* ms) {
   ScanPlan pl;
-  rope_status st = plan_scan(idx, ROPE_PREC_BF16, n_reads, jb, jb + len, n_ranges, c->num_sms, &pl, variant);
+  rope_status st = plan_scan(idx, o.precision, n_reads, jb, jb + len, n_ranges, c->num_sms, &pl, variant);
   if (st != ROPE_OK) return st;
   pl.a.emb_f32 = emb_f32;
   pl.a.emb_bf16 = emb_bf16;
@@ -740,7 +742,7 @@ rope_status tune_tc(const rope_index* idx, const uint16_t* emb_bf16, const float
   TuneVal b{0, 16, 1e30f};
   bool any = false;
   for (int v = 0; v < scan_tc_variants(ix.D) && st == ROPE_OK; ++v) {
-    if (!scan_tc_fits(ix, o.cand_depth, v)) continue;
+    if (!scan_tc_fits(ix, o.cand_depth, v, o.precision == ROPE_PREC_FP8)) continue;
     for (int items : kItems) {
       const int32_t nr = ranges_for(items, c->num_sms, n_groups);
       const int reps = any ? 1 : 2;  // the very first launch warms up, untimed
@@ -807,7 +809,7 @@ rope_status rope::score_topk_impl(const rope_index* idx, const float* emb_f32, c
   if (n_reads < 0) return fail(ROPE_ERR_INVALID_ARG, "n_reads < 0");
   if (n_reads == 0) return ROPE_OK;
   if (!emb_f32 || !norms || !out_win || !out_score) return fail(ROPE_ERR_INVALID_ARG, "NULL pointer");
-  if (o.precision == ROPE_PREC_BF16 && !emb_bf16) return fail(ROPE_ERR_INVALID_ARG, "BF16 scan needs emb_bf16");
+  if (prec_tc(o.precision) && !emb_bf16) return fail(ROPE_ERR_INVALID_ARG, "tensor-core scan needs emb_bf16");
   DeviceCtx* c;
   if ((st = get_ctx(&c)) != ROPE_OK) return st;
   const DevIndex& ix = idx->ix;
@@ -820,12 +822,12 @@ rope_status rope::score_topk_impl(const rope_index* idx, const float* emb_f32, c
   int32_t n_ranges = 1;  // candidate lists per read seen by the merge
   if (je > jb) {
     int32_t variant = 0, nr_req = o.n_ranges;
-    if (o.precision == ROPE_PREC_BF16 &&
+    if (prec_tc(o.precision) &&
         (st = choose_tc(idx, emb_bf16, emb_f32, norms, n_reads, jb, je, o, c, stream, ext == nullptr, &variant,
                         &nr_req)) != ROPE_OK)
       return st;
     if ((st = plan_scan(idx, o.precision, n_reads, jb, je, nr_req, c->num_sms, &pl, variant)) != ROPE_OK) return st;
-    if (pl.tc && !scan_tc_fits(ix, o.cand_depth, variant))
+    if (pl.tc && !scan_tc_fits(ix, o.cand_depth, variant, pl.a.fp8))
       return fail(ROPE_ERR_UNSUPPORTED, "cand_depth=%d: the tensor-core scan's candidate lists at complex "
                   "dimension %d and stride %d do not fit in shared memory; use a smaller cand_depth",
                   o.cand_depth, ix.D, ix.stride);
@@ -902,7 +904,7 @@ rope_status rope::topk_cand_bytes(const rope_index* idx, int64_t n_reads, const 
   int32_t n_ranges = 1;
   if (je > jb && n_reads > 0) {
     int32_t variant = 0, nr_req = o.n_ranges;
-    if (o.precision == ROPE_PREC_BF16 &&
+    if (prec_tc(o.precision) &&
         (st = choose_tc(idx, nullptr, nullptr, nullptr, n_reads, jb, je, o, c, nullptr, false, &variant, &nr_req)) !=
             ROPE_OK)
       return st;
@@ -976,7 +978,7 @@ extern "C" rope_status rope_score_dense(const rope_index* idx, const float* emb_
     return fail(ROPE_ERR_INVALID_ARG, "bad dense range");
   if (n_reads == 0 || count == 0) return ROPE_OK;
   if (!emb_f32 || !norms || !out) return fail(ROPE_ERR_INVALID_ARG, "NULL pointer");
-  if (precision == ROPE_PREC_BF16 && !emb_bf16) return fail(ROPE_ERR_INVALID_ARG, "BF16 scan needs emb_bf16");
+  if (prec_tc(precision) && !emb_bf16) return fail(ROPE_ERR_INVALID_ARG, "tensor-core scan needs emb_bf16");
   DeviceCtx* c;
   rope_status st = get_ctx(&c);
   if (st != ROPE_OK) return st;
@@ -1143,7 +1145,7 @@ extern "C" rope_status rope_score_topk_noalloc(const rope_index* idx, const floa
   if (n_reads < 0) return fail(ROPE_ERR_INVALID_ARG, "n_reads < 0");
   if (n_reads == 0) return ROPE_OK;
   if (!emb_f32 || !norms || !out_win || !out_score) return fail(ROPE_ERR_INVALID_ARG, "NULL pointer");
-  if (o.precision == ROPE_PREC_BF16 && !emb_bf16) return fail(ROPE_ERR_INVALID_ARG, "BF16 scan needs emb_bf16");
+  if (prec_tc(o.precision) && !emb_bf16) return fail(ROPE_ERR_INVALID_ARG, "tensor-core scan needs emb_bf16");
   int dev = 0;
   ROPE_CUDA(cudaGetDevice(&dev));
   if (dev < 0 || dev >= kNoAllocMaxDevices) return fail(ROPE_ERR_UNSUPPORTED, "device ordinal %d", dev);
@@ -1167,7 +1169,7 @@ extern "C" rope_status rope_score_topk_noalloc(const rope_index* idx, const floa
   int32_t n_ranges = 1;  // candidate lists per read seen by the merge
   if (je > jb) {
     int32_t variant = 0, nr_req = o.n_ranges;
-    if (o.precision == ROPE_PREC_BF16) {
+    if (prec_tc(o.precision)) {
       // an earlier tuned choice for this shape class, if any (never tunes here:
       // tuning allocates)
       DeviceCtx tmp{};
@@ -1177,7 +1179,7 @@ extern "C" rope_status rope_score_topk_noalloc(const rope_index* idx, const floa
         return st;
     }
     if ((st = plan_scan(idx, o.precision, n_reads, jb, je, nr_req, num_sms, &pl, variant)) != ROPE_OK) return st;
-    if (pl.tc && !scan_tc_fits(idx->ix, o.cand_depth, variant))
+    if (pl.tc && !scan_tc_fits(idx->ix, o.cand_depth, variant, pl.a.fp8))
       return fail(ROPE_ERR_UNSUPPORTED, "cand_depth=%d: the tensor-core scan's candidate lists at complex "
                   "dimension %d and stride %d do not fit in shared memory; use a smaller cand_depth",
                   o.cand_depth, idx->ix.D, idx->ix.stride);

@@ -303,6 +303,17 @@ __device__ __forceinline__ void tc_mma_ss(uint32_t d_tmem, uint64_t a_desc, uint
       : "memory");
 }
 
+// D[tmem] (+)= A[smem desc] * B[smem desc], kind::f8f6f4 (8-bit inputs given
+// by the instruction descriptor, FP32 accumulate; K = 32 per instruction)
+__device__ __forceinline__ void tc_mma_ss_f8(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc, uint32_t idesc,
+                                             uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n}" ::"r"(d_tmem),
+      "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
 // arrive on `bar` once all prior tcgen05 async ops of this thread complete
 __device__ __forceinline__ void tc_commit(uint64_t* bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
@@ -343,6 +354,26 @@ __device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t saddr) {
   return d;
 }
 
+// Same for a 64-byte swizzle: rows of 64 bytes in 8-row (512-byte) groups,
+// layout code 4.
+__device__ __forceinline__ uint64_t smem_desc_sw64(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
+  d |= (uint64_t)1 << 16;                 // leading byte offset (unused for swizzled K-major)
+  d |= (uint64_t)(512 >> 4) << 32;        // stride byte offset: next 8-row group
+  d |= (uint64_t)1 << 46;                 // version
+  d |= (uint64_t)4 << 61;                 // 64-byte swizzle
+  return d;
+}
+
+// Instruction descriptor, kind::f8f6f4: E4M3 A and B (format code 0, K-major),
+// FP32 D, shape M x N.
+__host__ __device__ constexpr uint32_t idesc_e4m3_f32(int M, int N) {
+  return (1u << 4)                       // D format FP32
+         | ((uint32_t)(N >> 3) << 17)    // N / 8
+         | ((uint32_t)(M >> 4) << 24);   // M / 16
+}
+
 // Instruction descriptor, kind::f16: BF16 A and B (K-major), FP32 D, shape M x N.
 __host__ __device__ constexpr uint32_t idesc_bf16_f32(int M, int N) {
   return (1u << 4)                       // D format FP32
@@ -356,6 +387,12 @@ __host__ __device__ constexpr uint32_t idesc_bf16_f32(int M, int N) {
 // K-major tile: 16-byte chunk index XOR (row mod 8), 8-row groups 1024 B apart
 __host__ __device__ __forceinline__ uint32_t sw128_offset(uint32_t r, uint32_t o) {
   return (r >> 3) * 1024u + (r & 7u) * 128u + ((((o >> 4) ^ (r & 7u)) & 7u) << 4) + (o & 15u);
+}
+
+// byte offset of (row r, byte o of the 64-byte row) in a 64-byte-swizzled
+// K-major tile: 16-byte chunk index XOR ((row / 2) mod 4), 8-row groups 512 B apart
+__host__ __device__ __forceinline__ uint32_t sw64_offset(uint32_t r, uint32_t o) {
+  return (r >> 3) * 512u + (r & 7u) * 64u + ((((o >> 4) ^ (r >> 1)) & 3u) << 4) + (o & 15u);
 }
 
 }  // namespace rope

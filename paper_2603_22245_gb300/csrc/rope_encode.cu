@@ -9,15 +9,22 @@ namespace rope {
 
 // ---------------------------------------------------------------- a1: packing
 
-__device__ __forceinline__ uint32_t pack4(uint32_t x, int& bad) {
-  uint32_t w = 0;
-#pragma unroll
-  for (int b = 0; b < 4; ++b) {
-    const uint32_t c = letter_code((x >> (8 * b)) & 0xFFu);
-    bad |= (c > 3);
-    w |= (c & 3u) << (2 * b);
-  }
-  return w;
+// Four letters (one byte each) to four 2-bit codes in one byte, a word at a
+// time. Bits 1-2 of an ASCII letter are 0,1,3,2 for A,C,G,T (either case), a
+// Gray code: x ^ (x >> 1) turns them into 0,1,2,3. The letters are then
+// checked by rebuilding each byte's lower-case letter from its code
+// ('a' + {0, 2, 6, 19}) and comparing with the input folded to lower case;
+// any difference, accumulated in `bad`, marks a letter outside ACGTacgt. The
+// multiply gathers the byte-spaced codes into the top byte (the partial
+// products of different bytes land in disjoint bits below it).
+__device__ __forceinline__ uint32_t pack4(uint32_t x, uint32_t& bad) {
+  const uint32_t g = (x >> 1) & 0x03030303u;
+  const uint32_t code = g ^ ((g >> 1) & 0x01010101u);
+  const uint32_t hi = (code >> 1) & 0x01010101u;           // code >= 2
+  const uint32_t three = hi & code;                         // code == 3
+  const uint32_t letter = 0x61616161u + ((code + hi) << 1) + three * 11u;
+  bad |= (x | 0x20202020u) ^ letter;
+  return (code * 0x01041040u) >> 24;
 }
 
 // One output word (16 letters) per thread; 16-byte vector loads when aligned.
@@ -27,7 +34,7 @@ __device__ __forceinline__ uint32_t pack4(uint32_t x, int& bad) {
 // keep HBM busy; the ragged tail and unaligned inputs take the byte path.
 constexpr int kPackWords = 4;
 
-__device__ __forceinline__ uint32_t pack_bytes(const uint8_t* seq, int64_t base, int64_t len, int& bad) {
+__device__ __forceinline__ uint32_t pack_bytes(const uint8_t* seq, int64_t base, int64_t len, uint32_t& bad) {
   uint32_t word = 0;
   for (int i = 0; i < 16 && base + i < len; ++i) {
     const uint32_t c = letter_code(seq[base + i]);
@@ -41,7 +48,7 @@ __global__ void pack_kernel(const uint8_t* __restrict__ seq, int64_t len, uint32
                             int64_t n_words, int* status) {
   // vector loads and stores need 16-byte aligned input and output
   const bool aligned = ((((uintptr_t)seq) | ((uintptr_t)out)) & 15u) == 0;
-  int bad = 0;
+  uint32_t bad = 0;
   const int64_t n_groups = (n_words + kPackWords - 1) / kPackWords;
   for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < n_groups;
        g += (int64_t)gridDim.x * blockDim.x) {

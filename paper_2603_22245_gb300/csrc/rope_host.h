@@ -10,6 +10,9 @@
 
 namespace rope {
 
+// precisions scored by the tensor-core scan (BF16 or E4M3 operands)
+inline bool prec_tc(int32_t precision) { return precision == ROPE_PREC_BF16 || precision == ROPE_PREC_FP8; }
+
 struct DeviceCtx {
   int* status = nullptr;  // device status word
   cudaMemPool_t pool = nullptr;

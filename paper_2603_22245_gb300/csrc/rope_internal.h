@@ -41,6 +41,7 @@ struct ScanArgs {
   int32_t lists_per_range;   // candidate lists a scan keeps per read and range
   uint64_t wait_limit_ns;    // bound of every in-kernel wait
   int32_t tc_variant;        // tile variant of the tensor-core scan (< scan_tc_variants(D))
+  int32_t fp8;               // tensor-core scan with E4M3 operands instead of BF16
 };
 
 struct MergeArgs {
@@ -108,7 +109,7 @@ int scan_tc_lists_per_range(int D, int variant);
 uint64_t wait_limit_ns();
 cudaError_t launch_scan_tc(const DevIndex& ix, const ScanArgs& a, bool dense, int num_sms, cudaStream_t st);
 // whether the tensor-core scan's shared memory holds candidate lists of this depth
-int scan_tc_fits(const DevIndex& ix, int cand_depth, int variant);
+int scan_tc_fits(const DevIndex& ix, int cand_depth, int variant, int fp8);
 
 // rope_merge.cu
 cudaError_t launch_merge(const DevIndex& ix, const MergeArgs& a, cudaStream_t st);

@@ -178,7 +178,7 @@ extern "C" rope_status rope_ladder_map(const rope_ladder* lad, const uint8_t* se
   if (st != ROPE_OK) return st;
   const int nbk = (int)lad->lens.size();
   const int D = lad->idx[0]->ix.D, m = lad->p.m;
-  const bool bf16 = opts->precision == ROPE_PREC_BF16;
+  const bool bf16 = prec_tc(opts->precision);  // the tensor-core scans take the BF16 encoding
   const int slot = host_prof_begin(stream);
 
   rope_ladder* L = const_cast<rope_ladder*>(lad);  // buffers and graphs are cached in the ladder

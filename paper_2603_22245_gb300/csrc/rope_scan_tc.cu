@@ -30,7 +30,12 @@
 
 namespace rope {
 
-template <int D_, int NT_, int T_, int STAGES_, int NB_, int LPC_, int HALVES_, bool ISOLATE_MMA_>
+// Scale of both operands in the E4M3 scan (a power of two, so exact): the
+// normalised entries (|.| <= 1, typically 1/sqrt(2D)) land in [2^-6, 448],
+// the normal range of E4M3, except for entries near 0.
+constexpr float kFp8Scale = 32.f;
+
+template <int D_, int NT_, int T_, int STAGES_, int NB_, int LPC_, int HALVES_, bool ISOLATE_MMA_, bool FP8_ = false>
 struct TcShape {
   static constexpr int D = D_, NT = NT_, T = T_, STAGES = STAGES_, NB = NB_;  // NB: most B ring slots
   static constexpr int A = kAnchorPeriod;
@@ -55,24 +60,55 @@ struct TcShape {
   static constexpr int NTHREADS = 32 * NWARPS;
   static constexpr int SUP = T * A;                   // windows per super-tile
   static constexpr int GROUP = NT * 128;              // reads per work item
-  static constexpr int KSTEPS = 2 * D / 16;           // K = 2D in steps of 16
-  static constexpr int KBLOCKS = 2 * D / 64;          // 64-element (128-byte) K blocks
-  static constexpr int A_KBLK_BYTES = 128 * 128;      // one K block of an A tile
+  // operands: BF16, or E4M3 scaled by kFp8Scale (scores then carry kFp8Scale^4)
+  static constexpr bool FP8 = FP8_;
+  static constexpr int EB = FP8 ? 1 : 2;               // bytes per operand element
+  static constexpr int ROW_BYTES = 2 * D * EB;         // one operand row, K = 2D
+  static constexpr int KBLK = ROW_BYTES < 128 ? ROW_BYTES : 128;  // swizzle row: 64 or 128 bytes
+  static constexpr int KSTEPS = ROW_BYTES / 32;        // 32 bytes of K per MMA (16 BF16 or 32 E4M3)
+  static constexpr int STEPS_PER_KBLK = KBLK / 32;
+  static constexpr int KBLOCKS = ROW_BYTES / KBLK;     // swizzled K blocks per row
+  static constexpr int A_KBLK_BYTES = 128 * KBLK;      // one K block of an A tile
   static constexpr int A_TILE_BYTES = KBLOCKS * A_KBLK_BYTES;
-  static constexpr int B_KBLK_BYTES = 2 * T * 128;    // one K block of a B tile
+  static constexpr int B_KBLK_BYTES = 2 * T * KBLK;    // one K block of a B tile
   static constexpr int B_SLOT_BYTES = KBLOCKS * B_KBLK_BYTES;
   static constexpr int TMEM_COLS = 512;
-  static constexpr uint32_t IDESC = idesc_bf16_f32(128, 2 * T);
+  static constexpr uint32_t IDESC = FP8 ? idesc_e4m3_f32(128, 2 * T) : idesc_bf16_f32(128, 2 * T);
+  static constexpr float SCORE_SCALE = FP8 ? 1.f / (kFp8Scale * kFp8Scale * kFp8Scale * kFp8Scale) : 1.f;
+  static constexpr int PIECE = BPL * EB == 8 ? 8 : 16;  // bytes of one generator store
+  static constexpr int NPC = BPL * EB / PIECE;           // generator stores per half-row
+  static constexpr int WPC = PIECE / 4;                  // 32-bit words per store
+  // byte offset of (row r, byte o) of a K block
+  __host__ __device__ static uint32_t swz(uint32_t r, uint32_t o) {
+    return KBLK == 128 ? sw128_offset(r, o) : sw64_offset(r, o);
+  }
+  __device__ static uint64_t desc(uint32_t saddr) { return KBLK == 128 ? smem_desc_sw128(saddr) : smem_desc_sw64(saddr); }
   static_assert(D == 32 || D == 64, "complex dimension");
   static_assert(GEN_WARPS * CPW == T, "T must be a multiple of chains per warp");
   static_assert(STAGES * NT * 2 * T <= TMEM_COLS, "tensor memory budget");
   static_assert(WPH % 16 == 0, "the epilogue loads 16-column chunks");
-  static_assert(BPL == 4 || BPL % 8 == 0, "generator lanes write 8-byte or whole 16-byte pieces");
+  static_assert(BPL * EB == 8 || (BPL * EB) % 16 == 0, "generator lanes write 8-byte or whole 16-byte pieces");
+  static_assert(KBLK == 64 || KBLK == 128, "swizzle row");
   static_assert((2 * T) % 16 == 0 && 2 * T <= 256, "MMA N");
   static_assert(NTHREADS <= 1024, "block size");
 };
 
 constexpr int kMaxPhaseTab = 16 * 8;  // m * stride <= 16 * 8 (D <= 64 complex, t >= 1)
+
+// two floats rounded to E4M3 (nearest, saturating), lo in the low byte
+__device__ __forceinline__ uint32_t e4m3x2(float lo, float hi) {
+  uint16_t r;
+  asm("cvt.rn.satfinite.e4m3x2.f32 %0, %1, %2;" : "=h"(r) : "f"(hi), "f"(lo));
+  return r;
+}
+__device__ __forceinline__ uint32_t f32x4_to_e4m3(float a, float b, float c, float d) {
+  return e4m3x2(a, b) | (e4m3x2(c, d) << 16);
+}
+// four BF16 (two packed pairs, first entry in the low half) times kFp8Scale, as E4M3
+__device__ __forceinline__ uint32_t bf16x4_to_e4m3(uint32_t p, uint32_t q) {
+  return f32x4_to_e4m3(__uint_as_float(p << 16) * kFp8Scale, __uint_as_float(p & 0xFFFF0000u) * kFp8Scale,
+                       __uint_as_float(q << 16) * kFp8Scale, __uint_as_float(q & 0xFFFF0000u) * kFp8Scale);
+}
 
 struct TcLaunch {
   int32_t nb;              // B ring slots in use (1..NB, the most that fit in shared memory)
@@ -190,7 +226,7 @@ __global__ void __launch_bounds__(Sh::NTHREADS, 1) scan_tc_kernel(DevIndex ix, S
     // writes the kept list of read r to the slot of range rng
     auto flush = [&](int64_t r, int rng) {
       Candidate* out = a.cand + (((size_t)r * a.n_ranges + rng) * Sh::HALVES + h) * a.cand_depth;
-      for (int e = 0; e < a.cand_depth; ++e) out[e] = Candidate{ls[e * lstride], lw[e * lstride]};
+      for (int e = 0; e < a.cand_depth; ++e) out[e] = Candidate{ls[e * lstride] * Sh::SCORE_SCALE, lw[e * lstride]};
     };
     for (int64_t item = it_lo; item < it_hi; ++item) {
       const int grp = (int)(item / a.n_ranges);
@@ -213,14 +249,20 @@ __global__ void __launch_bounds__(Sh::NTHREADS, 1) scan_tc_kernel(DevIndex ix, S
           if (pr < a.n_reads) flush(pr, seg_rng);
         }
         if (h == 0) {
-          // this read's normalised BF16 row, 16-byte chunks into the swizzled tile
+          // this read's normalised BF16 row, 16-byte chunks into the swizzled
+          // tile (E4M3: each chunk of 8 entries scaled, rounded and written as 8 bytes)
           const uint4* src = reinterpret_cast<const uint4*>(a.emb_bf16 + (have_read ? r : 0) * 2 * D);
 #pragma unroll
           for (int c = 0; c < 2 * D / 8; ++c) {
             const uint4 v = have_read ? __ldg(src + c) : make_uint4(0, 0, 0, 0);
-            const int kb = c >> 3;
-            *reinterpret_cast<uint4*>(arow_base + kb * Sh::A_KBLK_BYTES +
-                                      sw128_offset((uint32_t)arow, (uint32_t)((c & 7) * 16))) = v;
+            const int byte = c * 8 * Sh::EB;  // first byte of the chunk in the operand row
+            uint8_t* dst = arow_base + (byte / Sh::KBLK) * Sh::A_KBLK_BYTES +
+                           Sh::swz((uint32_t)arow, (uint32_t)(byte % Sh::KBLK));
+            if constexpr (Sh::FP8) {
+              *reinterpret_cast<uint2*>(dst) = make_uint2(bf16x4_to_e4m3(v.x, v.y), bf16x4_to_e4m3(v.z, v.w));
+            } else {
+              *reinterpret_cast<uint4*>(dst) = v;
+            }
           }
           fence_proxy_async_smem();
         }
@@ -271,7 +313,7 @@ __global__ void __launch_bounds__(Sh::NTHREADS, 1) scan_tc_kernel(DevIndex ix, S
 #pragma unroll
                 for (int n = 0; n < 16; ++n) {
                   const uint32_t j = jc + (uint32_t)(n * A);
-                  if (j >= jlo && j < jhi) a.dense[r * (a.je - a.jb) + ((int64_t)j - a.jb)] = sc[n];
+                  if (j >= jlo && j < jhi) a.dense[r * (a.je - a.jb) + ((int64_t)j - a.jb)] = sc[n] * Sh::SCORE_SCALE;
                 }
               }
             } else {
@@ -328,8 +370,8 @@ __global__ void __launch_bounds__(Sh::NTHREADS, 1) scan_tc_kernel(DevIndex ix, S
     if (lane == 0) {
       uint32_t gs = 0, it = 0, bslot = 0, bphase = 0;
       bool ok = true;
-      const uint64_t a_desc0 = smem_desc_sw128(smem_u32(a_tiles));
-      const uint64_t b_desc0 = smem_desc_sw128(smem_u32(b_ring));
+      const uint64_t a_desc0 = Sh::desc(smem_u32(a_tiles));
+      const uint64_t b_desc0 = Sh::desc(smem_u32(b_ring));
       for (int64_t item = it_lo; item < it_hi && ok; ++item, ++it) {
         const int rng = (int)(item % a.n_ranges);
         const int64_t st_begin = a.st0 + (int64_t)rng * a.range_len;
@@ -350,10 +392,14 @@ __global__ void __launch_bounds__(Sh::NTHREADS, 1) scan_tc_kernel(DevIndex ix, S
             const uint64_t tile_desc = a_desc0 + (uint64_t)((t * Sh::A_TILE_BYTES) >> 4);
 #pragma unroll
             for (int kk = 0; kk < Sh::KSTEPS; ++kk) {
-              const uint32_t kb = kk >> 2, ko = (kk & 3) * 32;
+              const uint32_t kb = kk / Sh::STEPS_PER_KBLK, ko = (kk % Sh::STEPS_PER_KBLK) * 32;
               const uint64_t ad = tile_desc + (uint64_t)((kb * Sh::A_KBLK_BYTES + ko) >> 4);
               const uint64_t bd = slot_desc + (uint64_t)((kb * Sh::B_KBLK_BYTES + ko) >> 4);
-              tc_mma_ss(d_tmem, ad, bd, Sh::IDESC, kk > 0 ? 1u : 0u);
+              if constexpr (Sh::FP8) {
+                tc_mma_ss_f8(d_tmem, ad, bd, Sh::IDESC, kk > 0 ? 1u : 0u);
+              } else {
+                tc_mma_ss(d_tmem, ad, bd, Sh::IDESC, kk > 0 ? 1u : 0u);
+              }
             }
           }
           tc_commit(&bar_bempty[slot]);
@@ -402,17 +448,18 @@ __global__ void __launch_bounds__(Sh::NTHREADS, 1) scan_tc_kernel(DevIndex ix, S
     ChainB<BPL> ch;
     ch.setup(ix, lic);
     // byte offsets of this lane's pieces in a B slot: row chain = [cr | ci],
-    // row T+chain = [ci | -cr]; BPL bf16 = 2*BPL bytes each, written as one
-    // 8-byte piece (BPL = 4) or 16-byte pieces
-    constexpr int NPC = BPL == 4 ? 1 : BPL / 8;  // pieces per half-row
+    // row T+chain = [ci | -cr]; BPL entries = BPL*EB bytes per half-row,
+    // written as one 8-byte piece or 16-byte pieces
+    constexpr int NPC = Sh::NPC;
     uint32_t off_re_cr[NPC], off_re_ci[NPC], off_im_ci[NPC], off_im_cr[NPC];
     {
       auto off = [&](int row, int e) -> uint32_t {
-        return (uint32_t)((e >> 6) * Sh::B_KBLK_BYTES) + sw128_offset((uint32_t)row, (uint32_t)((e & 63) * 2));
+        const int byte = e * Sh::EB;
+        return (uint32_t)((byte / Sh::KBLK) * Sh::B_KBLK_BYTES) + Sh::swz((uint32_t)row, (uint32_t)(byte % Sh::KBLK));
       };
 #pragma unroll
       for (int pc = 0; pc < NPC; ++pc) {
-        const int e_lo = BPL * lic + 8 * pc, e_hi = D + BPL * lic + 8 * pc;
+        const int e_lo = BPL * lic + pc * Sh::PIECE / Sh::EB, e_hi = D + e_lo;
         off_re_cr[pc] = off(chain, e_lo);
         off_re_ci[pc] = off(chain, e_hi);
         off_im_ci[pc] = off(T + chain, e_lo);
@@ -461,20 +508,30 @@ __global__ void __launch_bounds__(Sh::NTHREADS, 1) scan_tc_kernel(DevIndex ix, S
         ch.load(ix.anchors + a_idx * D, lic);
         __syncwarp();
         for (int i = 0; i < A; ++i) {
-          const float nv = inv_t[i * T + chain];
+          const float nv = inv_t[i * T + chain] * (Sh::FP8 ? kFp8Scale : 1.f);
           if (!mbar_wait_warp(&bar_bempty[bslot], bphase ^ 1u, abort_flag, a.status, wlim)) goto gen_done;
           {
             uint8_t* bt = b_ring + bslot * Sh::B_SLOT_BYTES;
-            uint32_t pr[BPL / 2], pi[BPL / 2], pn[BPL / 2];
+            // packed operand words of cr, ci and -cr (sign bits flipped)
+            constexpr int NW = BPL * Sh::EB / 4;
+            uint32_t pr[NW], pi[NW], pn[NW];
 #pragma unroll
-            for (int hh = 0; hh < BPL / 2; ++hh) {
-              const __nv_bfloat162 rr = __floats2bfloat162_rn(ch.cr[2 * hh] * nv, ch.cr[2 * hh + 1] * nv);
-              const __nv_bfloat162 ii = __floats2bfloat162_rn(ch.ci[2 * hh] * nv, ch.ci[2 * hh + 1] * nv);
-              pr[hh] = *reinterpret_cast<const uint32_t*>(&rr);
-              pi[hh] = *reinterpret_cast<const uint32_t*>(&ii);
-              pn[hh] = pr[hh] ^ 0x80008000u;
+            for (int hh = 0; hh < NW; ++hh) {
+              if constexpr (Sh::FP8) {
+                pr[hh] = f32x4_to_e4m3(ch.cr[4 * hh] * nv, ch.cr[4 * hh + 1] * nv, ch.cr[4 * hh + 2] * nv,
+                                       ch.cr[4 * hh + 3] * nv);
+                pi[hh] = f32x4_to_e4m3(ch.ci[4 * hh] * nv, ch.ci[4 * hh + 1] * nv, ch.ci[4 * hh + 2] * nv,
+                                       ch.ci[4 * hh + 3] * nv);
+                pn[hh] = pr[hh] ^ 0x80808080u;
+              } else {
+                const __nv_bfloat162 rr = __floats2bfloat162_rn(ch.cr[2 * hh] * nv, ch.cr[2 * hh + 1] * nv);
+                const __nv_bfloat162 ii = __floats2bfloat162_rn(ch.ci[2 * hh] * nv, ch.ci[2 * hh + 1] * nv);
+                pr[hh] = *reinterpret_cast<const uint32_t*>(&rr);
+                pi[hh] = *reinterpret_cast<const uint32_t*>(&ii);
+                pn[hh] = pr[hh] ^ 0x80008000u;
+              }
             }
-            if constexpr (BPL == 4) {
+            if constexpr (Sh::PIECE == 8) {
               *reinterpret_cast<uint2*>(bt + off_re_cr[0]) = make_uint2(pr[0], pr[1]);
               *reinterpret_cast<uint2*>(bt + off_re_ci[0]) = make_uint2(pi[0], pi[1]);
               *reinterpret_cast<uint2*>(bt + off_im_ci[0]) = make_uint2(pi[0], pi[1]);
@@ -540,6 +597,11 @@ using TcShape32b = TcShape<32, 2, 64, 2, 4, 4, 1, true>;
 // d = 128: 256 reads x 64 windows per stage, MMA N = 128 (twice the tensor time
 //          per stage); 8 epilogue warps, 16 generator warps (chains of 8 lanes x 8 entries)
 using TcShape64 = TcShape<64, 2, 64, 2, 2, 8, 1, false>;
+// the same tiles with E4M3 operands (kind::f8f6f4): half the operand bytes,
+// half the MMA instructions per stage; 64-byte swizzled rows at d = 64
+using TcShape32f8 = TcShape<32, 2, 64, 2, 4, 4, 2, true, true>;
+using TcShape32bf8 = TcShape<32, 2, 64, 2, 4, 4, 1, true, true>;
+using TcShape64f8 = TcShape<64, 2, 64, 2, 2, 8, 1, false, true>;
 
 // Dynamic shared memory one block of this kernel may take: the device's
 // opt-in maximum per block less the kernel's static shared memory (barriers,
@@ -618,12 +680,16 @@ static size_t tc_smem_bytes(const DevIndex& ix, int cand_depth, bool dense, int 
          L.inv_bytes + L.bins_bytes + lists;
 }
 
-int scan_tc_fits(const DevIndex& ix, int cand_depth, int variant) {
+template <class Sh>
+static int tc_fits(const DevIndex& ix, int cand_depth) {
   TcLaunch L;
-  if (ix.D == 32 && variant == 1)
-    return tc_smem_bytes<TcShape32b>(ix, cand_depth, false, 1, &L) <= tc_dyn_limit<TcShape32b, false>();
-  if (ix.D == 32) return tc_smem_bytes<TcShape32>(ix, cand_depth, false, 1, &L) <= tc_dyn_limit<TcShape32, false>();
-  if (ix.D == 64) return tc_smem_bytes<TcShape64>(ix, cand_depth, false, 1, &L) <= tc_dyn_limit<TcShape64, false>();
+  return tc_smem_bytes<Sh>(ix, cand_depth, false, 1, &L) <= tc_dyn_limit<Sh, false>();
+}
+
+int scan_tc_fits(const DevIndex& ix, int cand_depth, int variant, int fp8) {
+  if (ix.D == 32 && variant == 1) return fp8 ? tc_fits<TcShape32bf8>(ix, cand_depth) : tc_fits<TcShape32b>(ix, cand_depth);
+  if (ix.D == 32) return fp8 ? tc_fits<TcShape32f8>(ix, cand_depth) : tc_fits<TcShape32>(ix, cand_depth);
+  if (ix.D == 64) return fp8 ? tc_fits<TcShape64f8>(ix, cand_depth) : tc_fits<TcShape64>(ix, cand_depth);
   return 0;
 }
 
@@ -650,14 +716,22 @@ static cudaError_t launch_tc(const DevIndex& ix, const ScanArgs& a, int num_sms,
   return cudaGetLastError();
 }
 
+template <class Sh>
+static cudaError_t launch_tc_any(const DevIndex& ix, const ScanArgs& a, bool dense, int num_sms, cudaStream_t st) {
+  return dense ? launch_tc<Sh, true>(ix, a, num_sms, st) : launch_tc<Sh, false>(ix, a, num_sms, st);
+}
+
 cudaError_t launch_scan_tc(const DevIndex& ix, const ScanArgs& a, bool dense, int num_sms, cudaStream_t st) {
   if (ix.stride > scan_tc_max_stride()) return cudaErrorInvalidValue;
   if (ix.D == 32 && a.tc_variant == 1)
-    return dense ? launch_tc<TcShape32b, true>(ix, a, num_sms, st) : launch_tc<TcShape32b, false>(ix, a, num_sms, st);
+    return a.fp8 ? launch_tc_any<TcShape32bf8>(ix, a, dense, num_sms, st)
+                 : launch_tc_any<TcShape32b>(ix, a, dense, num_sms, st);
   if (ix.D == 32)
-    return dense ? launch_tc<TcShape32, true>(ix, a, num_sms, st) : launch_tc<TcShape32, false>(ix, a, num_sms, st);
+    return a.fp8 ? launch_tc_any<TcShape32f8>(ix, a, dense, num_sms, st)
+                 : launch_tc_any<TcShape32>(ix, a, dense, num_sms, st);
   if (ix.D == 64)
-    return dense ? launch_tc<TcShape64, true>(ix, a, num_sms, st) : launch_tc<TcShape64, false>(ix, a, num_sms, st);
+    return a.fp8 ? launch_tc_any<TcShape64f8>(ix, a, dense, num_sms, st)
+                 : launch_tc_any<TcShape64>(ix, a, dense, num_sms, st);
   return cudaErrorInvalidValue;
 }
 

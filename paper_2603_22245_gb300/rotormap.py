@@ -21,6 +21,8 @@ _lib = None
 
 ROPE_PREC_FP32 = 0
 ROPE_PREC_BF16 = 1
+ROPE_PREC_FP8 = 2
+_PREC = {"fp32": ROPE_PREC_FP32, "bf16": ROPE_PREC_BF16, "fp8": ROPE_PREC_FP8}
 _STATUS = {0: "ROPE_OK", 1: "ROPE_ERR_INVALID_ARG", 2: "ROPE_ERR_INVALID_BASE", 3: "ROPE_ERR_OOM",
            4: "ROPE_ERR_CUDA", 5: "ROPE_ERR_TIMEOUT", 6: "ROPE_ERR_UNSUPPORTED"}
 
@@ -254,9 +256,9 @@ def rope_encode_reads(p: Params, seqs: torch.Tensor, offsets: torch.Tensor, want
 
 
 def _opts(k, sep, precision, rescore, cand_depth, rescore_depth, n_ranges, j_begin, j_end) -> rope_score_opts:
-    prec = {"fp32": ROPE_PREC_FP32, "bf16": ROPE_PREC_BF16}.get(precision, precision)
+    prec = _PREC.get(precision, precision)
     if rescore is None:
-        rescore = 1 if prec == ROPE_PREC_BF16 else 0
+        rescore = 1 if prec in (ROPE_PREC_BF16, ROPE_PREC_FP8) else 0
     return rope_score_opts(k, sep, prec, int(rescore), cand_depth, rescore_depth, n_ranges, 0, j_begin, j_end)
 
 
@@ -292,7 +294,7 @@ def rope_score_topk_noalloc(idx: Index, emb_f32: torch.Tensor, emb_bf16: torch.T
 def rope_score_dense(idx: Index, emb_f32: torch.Tensor, emb_bf16: torch.Tensor | None, norms: torch.Tensor,
                      j_begin: int, count: int, precision="fp32", stream=None) -> torch.Tensor:
     n = norms.shape[0]
-    prec = {"fp32": ROPE_PREC_FP32, "bf16": ROPE_PREC_BF16}.get(precision, precision)
+    prec = _PREC.get(precision, precision)
     out = torch.full((n, count), float("nan"), dtype=torch.float32, device=norms.device)
     _check(load().rope_score_dense(idx.handle, _ptr(emb_f32), _ptr(emb_bf16), _ptr(norms), n, prec, j_begin, count,
                                    _ptr(out), _stream(stream)))
@@ -425,9 +427,9 @@ def rope_autotune_enable(enabled: bool):
     _check(load().rope_autotune_enable(1 if enabled else 0))
 
 
-def rope_autotune_query(idx: Index, n_reads: int, k: int = 8, sep: int = 0, cand_depth: int = 0):
+def rope_autotune_query(idx: Index, n_reads: int, k: int = 8, sep: int = 0, cand_depth: int = 0, precision="bf16"):
     """(tile variant, items per SM, sample ms) chosen for this shape class, or None."""
-    o = _opts(k, sep, "bf16", None, cand_depth, 0, 0, 0, 0)
+    o = _opts(k, sep, precision, None, cand_depth, 0, 0, 0, 0)
     v, it, ms = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_float()
     st = load().rope_autotune_query(idx.handle, n_reads, ctypes.byref(o), ctypes.byref(v), ctypes.byref(it),
                                     ctypes.byref(ms))
@@ -435,7 +437,7 @@ def rope_autotune_query(idx: Index, n_reads: int, k: int = 8, sep: int = 0, cand
 
 
 def rope_autotune_set(idx: Index, n_reads: int, variant: int, items_per_sm: int, k: int = 8, sep: int = 0,
-                      cand_depth: int = 0):
+                      cand_depth: int = 0, precision="bf16"):
     """Pin the scan configuration of this shape class."""
-    o = _opts(k, sep, "bf16", None, cand_depth, 0, 0, 0, 0)
+    o = _opts(k, sep, precision, None, cand_depth, 0, 0, 0, 0)
     _check(load().rope_autotune_set(idx.handle, n_reads, ctypes.byref(o), variant, items_per_sm))

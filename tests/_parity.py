@@ -13,6 +13,22 @@ def bf16_tol(f):
     return np.maximum(2e-2 * f, 8e-3 * np.sqrt(np.maximum(f, 0)) + 2e-5)
 
 
+# E4M3 scan: per operand entry the relative rounding error is at most 2^-4
+# (3 mantissa bits, round to nearest), after the BF16 rounding (2^-8) of the
+# read's encoding; the window's FP32 entries carry ~1e-5. So every product
+# x_i c_i is off by at most (2^-4 + 2^-8 + 2^-12) + 2^-4 + (their product)
+# < 0.134 of |x_i c_i|, and Re/Im of the inner product of two unit vectors by
+# eps <= 0.134 * sum|x_i c_i| + (subnormal floor) <= 0.136. The fidelity
+# Re^2 + Im^2 then moves by at most 2 eps (|Re| + |Im|) + 2 eps^2
+# <= 2 eps sqrt(2 f) + 2 eps^2.
+FP8_EPS = 0.136
+
+
+def fp8_tol(f):
+    f = np.maximum(np.asarray(f, dtype=np.float64), 0)
+    return 2 * FP8_EPS * np.sqrt(2 * f) + 2 * FP8_EPS ** 2
+
+
 def f32_tol(f):
     return F32_REL * np.abs(np.asarray(f, dtype=np.float64)) + F32_ABS
 
