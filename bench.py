@@ -15,6 +15,8 @@ timed region (the paper's "preloaded data").
   fp32_plain  the FP32 CUDA-core scan on a read subset (same metric)
   fp8_option  the same steps with the E4M3 tensor-core scan (rate, top-1
               accuracy, scan roofline against twice the BF16 peak)
+  refine      §3.4 refinement of the top-2 candidates of one batch (+-8
+              letters, 4^8-bin encoding): rate and exact-start fraction
   top1_acc    fraction of planted reads whose top-1 window overlaps the truth
   e2e         the same metric through host buffers (H2D of the reads, D2H of
               the top-k) around every step
@@ -90,6 +92,7 @@ def parse():
     ap.add_argument("--batch", type=int, default=131072)
     ap.add_argument("--fp32-reads", type=int, default=4096)
     ap.add_argument("--fp8-steps", type=int, default=2)
+    ap.add_argument("--refine-radius", type=int, default=8)
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--cpu-reads", type=int, default=32)
     ap.add_argument("--cpu-windows", type=int, default=1_000_000)
@@ -378,6 +381,7 @@ def run_ladder(args, wl):
         elapsed = float(t.item())
         dist.barrier()
     rm.rope_sync_status()
+    top2_step0 = step_outs[0][0][:, :2].clone()  # the refinement leg's candidates (batch 0)
     stage_ms = rm.rope_profile_read(args.steps)
     rm.rope_profile_enable(0)
     w = outs[(args.steps - 1) % 2][0][:, 0].cpu().numpy()
@@ -567,6 +571,33 @@ def main():
                             "frac": flops / scan8 / 1e12 / peak8,
                             "peak_source": f"{peak_src} bf16_tflops_sustained x 2 (nominal E4M3/BF16 ratio)"}}
 
+    # refinement (§3.4): the first step's top-2 candidates of each read slid
+    # +-radius letters under a 4^8-bin encoding (s = t = 8, m = 1)
+    refine = None
+    if args.refine_radius > 0:
+        try:
+            fine = rm.Params(s=8, m=1, t=8, variant=0, window_len=wl["N"])
+            cand = top2_step0
+            ob = offs[:B + 1]
+            rm.rope_refine(idx, fine, seqs, ob, cand, args.refine_radius)
+            torch.cuda.synchronize()
+            e0.record()
+            n_rf = 3
+            for _ in range(n_rf):
+                rp, rf = rm.rope_refine(idx, fine, seqs, ob, cand, args.refine_radius)
+            e1.record()
+            torch.cuda.synchronize()
+            rm.rope_sync_status()
+            t_rf = e0.elapsed_time(e1) / 1000.0 / n_rf
+            tp0 = true_pos[:B]
+            best = rp.gather(1, rf.argmax(dim=1, keepdim=True))[:, 0].cpu().numpy()
+            refine = {"candidates_per_s": 2 * B / t_rf, "positions_per_s": 2 * B * (2 * args.refine_radius + 1) / t_rf,
+                      "ms": t_rf * 1e3, "reads": B, "radius": args.refine_radius, "encoding": "s=8 m=1 t=8 (4^8 bins)",
+                      "exact_start_before": float(np.mean(top2_step0[:, 0].cpu().numpy() == tp0)),
+                      "exact_start_after": float(np.mean(best == tp0))}
+        except Exception as exc:  # a failure here must not cost the bench line
+            refine = {"error": str(exc)}
+
     # end to end through host buffers: H2D reads, rope_map, D2H top-k, every step
     e2e = None
     if args.e2e_steps > 0:
@@ -616,7 +647,7 @@ def main():
                    f"reads sharded over {ws} GPU(s)",
                    "scan_tiles": None if tuned is None else {"variant": tuned[0], "items_per_sm": tuned[1],
                                                               "tuned_scan_ms": tuned[2]}},
-        "reads_per_s": reads_s, "top1_acc": acc_bf16, "fp32_plain": fp32, "fp8_option": fp8,
+        "reads_per_s": reads_s, "top1_acc": acc_bf16, "fp32_plain": fp32, "fp8_option": fp8, "refine": refine,
         "encode_pass": encode_pass,
         "speedup_vs_fp32_plain": value / ws / fp32["value"],
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "reranker": reranker, "gpu_launches": 3 * args.steps, "clocks": clocks,

@@ -250,6 +250,33 @@ rope_status rope_score_dense(const rope_index* idx, const float* emb_f32, const 
 rope_status rope_map(const rope_index* idx, const uint8_t* seqs, const int64_t* offsets, int64_t n_reads,
                      const rope_score_opts* opts, int64_t* out_win, float* out_score, cudaStream_t stream);
 
+/* ---- refinement (§3.4, increasing the accuracy) -------------------------
+ * Slides the window one letter at a time around coarse candidates and scores
+ * each position with the encoding p (which may differ from the index's: e.g.
+ * s = t = 8, up to 4^8 bins per band, m <= 8), using the paper's O(1)-per-step
+ * update of the inner product and an exactly tracked window norm (every bin's
+ * sum kept on chip; the norm is not skipped).
+ *   idx       supplies the 2-bit packed reference only (its own encoding is
+ *             not used)
+ *   p         s, m, t, variant, score_mode, bin map and window_len = N (the
+ *             read head length); stride is ignored. N <= reference length.
+ *   seqs, offsets, n_reads  reads as for rope_encode_reads (each >= N letters)
+ *   cand_pos  n_reads x n_cand int64 window starts (device), 1 <= n_cand <= 64;
+ *             a negative entry means no candidate; a start past the last
+ *             window is taken as the last window
+ *   radius    positions [c - radius, c + radius] clipped to [0, L - N] are
+ *             scored, 0 <= radius <= 4096
+ *   out_pos, out_fid  n_reads x n_cand (device): per candidate, the best
+ *             position of its range (ties: the lower) and its fidelity (FP32;
+ *             FP64 accumulation of the updates); (-1, -inf) where there is no
+ *             candidate or the read is invalid (status word set as for
+ *             rope_encode_reads)
+ * Returns ROPE_ERR_UNSUPPORTED when the on-chip tables for (N, m, radius) do
+ * not fit in one block's shared memory. */
+rope_status rope_refine(const rope_index* idx, const rope_params* p, const uint8_t* seqs, const int64_t* offsets,
+                        int64_t n_reads, const int64_t* cand_pos, int32_t n_cand, int32_t radius, int64_t* out_pos,
+                        float* out_fid, cudaStream_t stream);
+
 /* Both strands (§3.5 maps reads in both directions): each read is mapped by
  * its head and by the head of its reverse complement (the complement of its
  * last N letters, read backwards), both against the forward reference, and

@@ -392,3 +392,44 @@ def score_topk_strands(ref, seqs, offsets, p: Params, k: int = 8, sep: int = 0):
         for j, (ns, t, w) in enumerate(cands[:k]):
             out_w[i, j], out_s[i, j], out_t[i, j] = w, -ns, t
     return out_w, out_s, out_t
+
+
+# ------------------------------------------------------------ refinement
+
+def refine(ref, seqs, offsets, cand_pos, radius: int, p: Params, n_threads: int = 0):
+    """§3.4, increasing the accuracy: around each candidate start c the window
+    of length p.N is slid one letter at a time over [c - radius, c + radius]
+    (clipped to [0, L - N]) and each position is scored against the read head
+    with the encoding p, here by direct FP64 embedding of every window (the
+    definition the paper's O(1) update reproduces). Per (read, candidate):
+    the position of the highest fidelity (ties: the lower position) and that
+    fidelity; (-1, -inf) for a candidate < 0; a candidate past the last window
+    start counts as the last. Also returns every scored
+    (read, position, fidelity) triple, for checks of near ties."""
+    ref = _u8(ref)
+    cand_pos = np.asarray(cand_pos, dtype=np.int64)
+    n, nc = cand_pos.shape
+    last = len(ref) - p.N
+    ri, pos, owner = [], [], []
+    for i in range(n):
+        for c in range(nc):
+            x = int(cand_pos[i, c])
+            if x < 0 or last < 0:
+                continue
+            x = min(x, last)  # a start past the last window counts as the last
+            lo, hi = max(0, x - radius), min(last, x + radius)
+            for q in range(lo, hi + 1):
+                ri.append(i)
+                pos.append(q)
+                owner.append(i * nc + c)
+    out_p = np.full((n, nc), -1, dtype=np.int64)
+    out_f = np.full((n, nc), -np.inf)
+    if not ri:
+        return out_p, out_f, (np.zeros(0, np.int64), np.zeros(0, np.int64), np.zeros(0))
+    ri, pos, owner = np.array(ri), np.array(pos), np.array(owner)
+    fid = score_pairs(ref, seqs, offsets, ri, pos, p, n_threads=n_threads)
+    for o, q, f in zip(owner, pos, fid):
+        i, c = divmod(int(o), nc)
+        if f > out_f[i, c]:  # positions arrive in increasing order: ties keep the lower one
+            out_p[i, c], out_f[i, c] = q, f
+    return out_p, out_f, (owner, pos, fid)

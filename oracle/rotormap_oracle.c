@@ -492,16 +492,25 @@ int oracle_score_pairs(const uint8_t* ref, int64_t L, const uint8_t* seqs, const
 #pragma omp parallel for schedule(dynamic, 16)
 #endif
   for (int64_t i = 0; i < n_pairs; ++i) {
-    double xr[4096], xi[4096], yr[4096], yi[4096];
+    /* dense vectors of any dimension (refinement encodings reach 4^8 bins) */
+    double* buf = (double*)malloc(sizeof(double) * 4 * (size_t)D);
     int64_t r = read_idx[i], w = win_start[i];
-    if (D > 4096 || w < 0 || w + N > L || offsets[r + 1] - offsets[r] < N ||
-        oracle_embed(seqs + offsets[r], N, s, m, t, variant, map, xr, xi) != 0 ||
-        oracle_embed(ref + w, N, s, m, t, variant, map, yr, yi) != 0) {
+    if (!buf) {
       bad = 1;
       out[i] = NAN;
       continue;
     }
+    double *xr = buf, *xi = buf + D, *yr = buf + 2 * (size_t)D, *yi = buf + 3 * (size_t)D;
+    if (w < 0 || w + N > L || offsets[r + 1] - offsets[r] < N ||
+        oracle_embed(seqs + offsets[r], N, s, m, t, variant, map, xr, xi) != 0 ||
+        oracle_embed(ref + w, N, s, m, t, variant, map, yr, yi) != 0) {
+      bad = 1;
+      out[i] = NAN;
+      free(buf);
+      continue;
+    }
     out[i] = score_mode == 1 ? oracle_fidelity_per_band(xr, xi, yr, yi, m, nb) : oracle_fidelity(xr, xi, yr, yi, D);
+    free(buf);
   }
   return bad ? -1 : 0;
 }

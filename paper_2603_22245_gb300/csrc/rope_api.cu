@@ -281,6 +281,33 @@ rope_status get_enc_tables(const rope_params& p, EncTables* out) {
   return ROPE_OK;
 }
 
+}  // namespace
+
+// Tables of an encoding used only for refinement: the s-mer map and the
+// read-frame phases; unlike an index's encoding its dense dimension m*4^t is
+// not bounded (up to 4^8 bins per band), since refinement stores only the
+// bins a read or window touches.
+rope_status rope::host_refine_tables(const rope_params* p, EncTables* out) {
+  if (!p) return fail(ROPE_ERR_INVALID_ARG, "params is NULL");
+  if (p->s < 1 || p->s > 8) return fail(ROPE_ERR_INVALID_ARG, "s=%d outside [1,8]", p->s);
+  if (p->t < 1 || p->t > p->s) return fail(ROPE_ERR_INVALID_ARG, "t=%d outside [1,s]", p->t);
+  if (p->m < 1 || p->m > 8) return fail(ROPE_ERR_INVALID_ARG, "m=%d outside [1,8]", p->m);
+  if (p->variant != 0 && p->variant != 1) return fail(ROPE_ERR_INVALID_ARG, "variant=%d", p->variant);
+  if (p->score_mode != 0 && p->score_mode != 1) return fail(ROPE_ERR_INVALID_ARG, "score_mode=%d", p->score_mode);
+  if (p->window_len < p->s || p->window_len > 65536)
+    return fail(ROPE_ERR_INVALID_ARG, "window_len=%d outside [s,65536]", p->window_len);
+  if (p->bin_of_mer_host) {
+    const int nb = 1 << (2 * p->t);
+    for (int i = 0; i < (1 << (2 * p->s)); ++i)
+      if (p->bin_of_mer_host[i] >= nb) return fail(ROPE_ERR_INVALID_ARG, "bin_of_mer[%d] >= 4^t", i);
+  }
+  return get_enc_tables(*p, out);
+}
+
+void rope::host_factor(const rope_params* p, int k, int64_t* a, int64_t* q) { factor(*p, k, a, q); }
+
+namespace {
+
 // Stage recorder: CUDA events around encode / scan / merge of each call.
 struct Profiler {
   std::mutex mu;

@@ -29,6 +29,11 @@ rope_status host_pool_alloc(DeviceCtx* c, void** p, size_t bytes, cudaStream_t s
 // full) and its marks 1..3.
 int host_prof_begin(cudaStream_t st);
 void host_prof_mark(int slot, int which, cudaStream_t st);
+// Map and read-frame phase tables of a refinement encoding (validated; any
+// m*4^t), cached per device and parameter set.
+rope_status host_refine_tables(const rope_params* p, EncTables* out);
+// f_k = a / q of band k (1-based) of the encoding p.
+void host_factor(const rope_params* p, int k, int64_t* a, int64_t* q);
 // Index build; with shared_packed set, the index borrows that packed
 // reference (same letters, owned by another index) instead of packing ref.
 rope_status encode_reference_impl(const rope_params* p, const uint8_t* ref, int64_t len,

@@ -65,6 +65,7 @@ EXPORTS = {
     "rope_score_dense": ([_P, _P, _P, _P, _I64, _I32, _I64, _I64, _P, _P], ctypes.c_int),
     "rope_map": ([_P, _P, _P, _I64, _P, _P, _P, _P], ctypes.c_int),
     "rope_map_strands": ([_P, _P, _P, _I64, _P, _P, _P, _P, _P], ctypes.c_int),
+    "rope_refine": ([_P, _P, _P, _P, _I64, _P, _I32, _I32, _P, _P, _P], ctypes.c_int),
     "rope_reranker_create": ([_I32, _I32, ctypes.c_uint64, _P], ctypes.c_int),
     "rope_reranker_free": ([_P], None),
     "rope_reranker_get": ([_P, _P, _P], ctypes.c_int),
@@ -325,6 +326,22 @@ def rope_map_strands(idx: Index, seqs: torch.Tensor, offsets: torch.Tensor, k: i
     o = _opts(k, sep, precision, rescore, cand_depth, rescore_depth, n_ranges, 0, 0)
     _check(load().rope_map_strands(idx.handle, _ptr(seqs), _ptr(offsets), n, ctypes.byref(o), _ptr(out[0]),
                                    _ptr(out[1]), _ptr(out[2]), _stream(stream)))
+    return out
+
+
+def rope_refine(idx: Index, p: Params, seqs: torch.Tensor, offsets: torch.Tensor, cand_pos: torch.Tensor,
+                radius: int, stream=None):
+    """§3.4 refinement: per (read, candidate start) the best position within
+    +-radius letters under the encoding p, and its fidelity:
+    (positions int64 [n, n_cand], fidelities float32 [n, n_cand])."""
+    n = offsets.numel() - 1
+    cand_pos = cand_pos.reshape(n, -1).contiguous()
+    nc = cand_pos.shape[1]
+    out = (torch.empty((n, nc), dtype=torch.int64, device=seqs.device),
+           torch.empty((n, nc), dtype=torch.float32, device=seqs.device))
+    pc = p.c()
+    _check(load().rope_refine(idx.handle, ctypes.byref(pc), _ptr(seqs), _ptr(offsets), n, _ptr(cand_pos), nc, radius,
+                              _ptr(out[0]), _ptr(out[1]), _stream(stream)))
     return out
 
 

@@ -554,3 +554,54 @@ def test_reverse_complement_and_strands():
     assert w[0, 0] == 700 and t[0, 0] == 0 and sc[0, 0] == pytest.approx(1.0, abs=1e-9)
     assert w[1, 0] == 1900 and t[1, 0] == 1 and sc[1, 0] == pytest.approx(1.0, abs=1e-9)
     assert np.all(np.diff(sc, axis=1) <= 0)
+
+
+# ---------------------------------------------------------------- refinement (§3.4, increasing the accuracy)
+
+@pytest.mark.parametrize("pp", [dict(s=4, m=2, t=2, variant=1), dict(s=8, m=1, t=8, variant=0),
+                                dict(s=5, m=3, t=3, variant=1, score_mode=1)])
+def test_refine_finds_exact_reads(pp):
+    """An error-free read is its own window: fidelity 1 (identity) at the true
+    start, which the refinement finds from any candidate within the radius;
+    a random reference has no other window at fidelity 1."""
+    ref = synth.uniform_ref(6000, 71)
+    rd = synth.reads(ref, 12, seed=72, sub_rate=0.0, indel_rate=0.0)
+    op = oracle.Params(N=150, **pp)
+    rng = np.random.default_rng(73)
+    cand = rd.true_pos[:, None] + rng.integers(-9, 10, size=(12, 3))
+    pos, fid, _ = oracle.refine(ref, rd.seqs, rd.offsets, cand, 9, op)
+    ok = (cand >= 0) & (cand <= len(ref) - 150)
+    assert np.all(pos[ok] == np.broadcast_to(rd.true_pos[:, None], pos.shape)[ok])
+    assert np.allclose(fid[ok], 1.0, atol=1e-12)
+
+
+def test_refine_range_clipping_and_missing():
+    ref = synth.uniform_ref(2000, 81)
+    rd = synth.reads(ref, 3, seed=82)
+    op = oracle.Params(N=150)
+    last = len(ref) - 150
+    cand = np.array([[3, -1], [last - 2, 0], [last + 40, 1000]], dtype=np.int64)
+    pos, fid, (owner, scored, _) = oracle.refine(ref, rd.seqs, rd.offsets, cand, 5, op)
+    assert pos[0, 1] == -1 and np.isneginf(fid[0, 1])
+    # each candidate's scored positions are exactly its clipped range
+    want = {0: range(0, 9), 2: range(last - 7, last + 1), 3: range(0, 6), 4: range(last - 5, last + 1),
+            5: range(995, 1006)}
+    for o, rng_ in want.items():
+        assert scored[owner == o].tolist() == list(rng_)
+    assert np.all((pos[pos >= 0] >= 0) & (pos[pos >= 0] <= last))
+    # radius 0 returns the candidate itself
+    p0, f0, _ = oracle.refine(ref, rd.seqs, rd.offsets, np.array([[500], [17], [1200]]), 0, op)
+    assert p0[:, 0].tolist() == [500, 17, 1200]
+
+
+def test_refine_ties_take_the_lower_position():
+    """A reference of period 8 repeats every window 8 letters on: a read equal
+    to one window scores fidelity 1 at every start of the same phase, and the
+    lowest of them in the range is returned."""
+    unit = np.frombuffer(b"ACGGTCAT", dtype=np.uint8)
+    ref = np.tile(unit, 200).copy()
+    read = ref[100:250].copy()
+    offs = np.array([0, 150], dtype=np.int64)
+    op = oracle.Params(N=150)
+    pos, fid, _ = oracle.refine(ref, read, offs, np.array([[300]]), 20, op)
+    assert pos[0, 0] == 284 and fid[0, 0] == pytest.approx(1.0, abs=1e-12)  # 284 = 100 (mod 8), >= 280
