@@ -93,6 +93,8 @@ def parse():
     ap.add_argument("--fp32-reads", type=int, default=4096)
     ap.add_argument("--fp8-steps", type=int, default=2)
     ap.add_argument("--refine-radius", type=int, default=8)
+    ap.add_argument("--scan-variant", type=int, default=-1,
+                    help="pin the scan's tile variant (and 16 items per SM) instead of the library's choice")
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--cpu-reads", type=int, default=32)
     ap.add_argument("--cpu-windows", type=int, default=1_000_000)
@@ -465,6 +467,8 @@ def main():
         b = bi % n_batches
         return rm.rope_map(idx, seqs, offs[b * B:(b + 1) * B + 1], k=k, precision=precision, out=o or outs)
 
+    if args.scan_variant >= 0:
+        rm.rope_autotune_set(idx, B, args.scan_variant, 16, k=k)
     for i in range(args.warmup):
         step(i)
     rm.rope_sync_status()

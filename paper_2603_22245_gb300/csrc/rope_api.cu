@@ -586,8 +586,8 @@ rope_status plan_scan(const rope_index* idx, int32_t precision, int64_t n_reads,
     if (ix.score_mode != 0) return fail(ROPE_ERR_UNSUPPORTED, "tensor-core scan takes score_mode 0 only");
     if (ix.stride > scan_tc_max_stride())
       return fail(ROPE_ERR_UNSUPPORTED, "tensor-core scan takes stride <= %d", scan_tc_max_stride());
-    sup = scan_tc_super_tile(ix.D);
-    group = scan_tc_group(ix.D);
+    sup = scan_tc_super_tile(ix.D, tc_variant);
+    group = scan_tc_group(ix.D, tc_variant);
   } else if (precision == ROPE_PREC_FP32) {
     if (!scan_fp32_supported(ix.D))
       return fail(ROPE_ERR_UNSUPPORTED, "FP32 scan built for complex dimension <= 64, not %d", ix.D);
@@ -746,7 +746,7 @@ rope_status tune_tc(const rope_index* idx, const uint16_t* emb_bf16, const float
                     int64_t n_reads, int64_t jb, int64_t je, const rope_score_opts& o, DeviceCtx* c,
                     cudaStream_t stream, TuneVal* best) {
   const DevIndex& ix = idx->ix;
-  const int64_t n_groups = (n_reads + scan_tc_group(ix.D) - 1) / scan_tc_group(ix.D);
+  auto n_groups = [&](int v) -> int64_t { return (n_reads + scan_tc_group(ix.D, v) - 1) / scan_tc_group(ix.D, v); };
   static const int kItems[] = {8, 16, 32};
   const int64_t total = je - jb;
   if (total > kTuneMaxWindows) {
@@ -756,7 +756,7 @@ rope_status tune_tc(const rope_index* idx, const uint16_t* emb_bf16, const float
   size_t cand_bytes = 0;
   for (int v = 0; v < scan_tc_variants(ix.D); ++v)
     for (int items : kItems) {
-      const size_t b = (size_t)n_reads * ranges_for(items, c->num_sms, n_groups) * scan_tc_lists_per_range(ix.D, v) *
+      const size_t b = (size_t)n_reads * ranges_for(items, c->num_sms, n_groups(v)) * scan_tc_lists_per_range(ix.D, v) *
                        o.cand_depth * sizeof(Candidate);
       cand_bytes = std::max(cand_bytes, b);
     }
@@ -771,7 +771,7 @@ rope_status tune_tc(const rope_index* idx, const uint16_t* emb_bf16, const float
   for (int v = 0; v < scan_tc_variants(ix.D) && st == ROPE_OK; ++v) {
     if (!scan_tc_fits(ix, o.cand_depth, v, o.precision == ROPE_PREC_FP8)) continue;
     for (int items : kItems) {
-      const int32_t nr = ranges_for(items, c->num_sms, n_groups);
+      const int32_t nr = ranges_for(items, c->num_sms, n_groups(v));
       const int reps = any ? 1 : 2;  // the very first launch warms up, untimed
       float ms = 0.f;
       st = time_candidate(idx, emb_bf16, emb_f32, norms, n_reads, jb, total, nr, v, o, cand, c, stream, e0, e1, reps,
@@ -801,7 +801,6 @@ rope_status choose_tc(const rope_index* idx, const uint16_t* emb_bf16, const flo
   if (!scan_tc_supported(idx->ix.D) || idx->ix.score_mode != 0 || idx->ix.stride > scan_tc_max_stride())
     return ROPE_OK;  // plan_scan reports why
   const TuneKey key = tune_key(idx, n_reads, o);
-  const int64_t n_groups = (n_reads + scan_tc_group(idx->ix.D) - 1) / scan_tc_group(idx->ix.D);
   TuneVal val;
   bool found;
   {
@@ -819,7 +818,8 @@ rope_status choose_tc(const rope_index* idx, const uint16_t* emb_bf16, const flo
   }
   if (found) {
     *variant = val.variant;
-    if (o.n_ranges == 0) *n_ranges = ranges_for(val.items_per_sm, c->num_sms, n_groups);
+    const int g = scan_tc_group(idx->ix.D, val.variant);
+    if (o.n_ranges == 0) *n_ranges = ranges_for(val.items_per_sm, c->num_sms, (n_reads + g - 1) / g);
   }
   return ROPE_OK;
 }

@@ -101,8 +101,8 @@ cudaError_t launch_scan_fp32(const DevIndex& ix, const ScanArgs& a, bool dense, 
 
 // rope_scan_tc.cu
 int scan_tc_supported(int D);
-int64_t scan_tc_super_tile(int D);
-int scan_tc_group(int D);
+int64_t scan_tc_super_tile(int D, int variant = 0);
+int scan_tc_group(int D, int variant = 0);
 int scan_tc_max_stride();
 int scan_tc_variants(int D);
 int scan_tc_lists_per_range(int D, int variant);

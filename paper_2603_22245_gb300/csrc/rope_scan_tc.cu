@@ -602,6 +602,11 @@ using TcShape32 = TcShape<32, 2, 64, 2, 4, 4, 2, true>;
 //          tile (8 warps, each reading all 64 windows of a stage; one candidate
 //          list per read), more registers per thread. Faster at large strides.
 using TcShape32b = TcShape<32, 2, 64, 2, 4, 4, 1, true>;
+// d = 64, third tile variant: 512 reads (4 tiles) x 32 windows per stage, MMA
+//          N = 64 (twice the MMA instructions per score, on a tensor pipe that
+//          is a quarter busy) so that each generated window serves twice as
+//          many reads: half the window-generation work per score.
+using TcShape32c = TcShape<32, 4, 32, 2, 4, 4, 1, true>;
 // d = 128: 256 reads x 64 windows per stage, MMA N = 128 (twice the tensor time
 //          per stage); 8 epilogue warps, 16 generator warps (chains of 8 lanes x 8 entries)
 using TcShape64 = TcShape<64, 2, 64, 2, 2, 8, 1, false>;
@@ -609,6 +614,7 @@ using TcShape64 = TcShape<64, 2, 64, 2, 2, 8, 1, false>;
 // half the MMA instructions per stage; 64-byte swizzled rows at d = 64
 using TcShape32f8 = TcShape<32, 2, 64, 2, 4, 4, 2, true, true>;
 using TcShape32bf8 = TcShape<32, 2, 64, 2, 4, 4, 1, true, true>;
+using TcShape32cf8 = TcShape<32, 4, 32, 2, 4, 4, 1, true, true>;
 using TcShape64f8 = TcShape<64, 2, 64, 2, 2, 8, 1, false, true>;
 
 // Dynamic shared memory one block of this kernel may take: the device's
@@ -654,16 +660,22 @@ static cudaError_t tc_reserve_smem(size_t smem) {
 
 int scan_tc_supported(int D) { return D == 32 || D == 64; }
 
-int64_t scan_tc_super_tile(int D) { return D == 32 ? TcShape32::SUP : D == 64 ? TcShape64::SUP : 0; }
+int64_t scan_tc_super_tile(int D, int variant) {
+  if (D == 32) return variant == 2 ? TcShape32c::SUP : TcShape32::SUP;
+  return D == 64 ? TcShape64::SUP : 0;
+}
 
-int scan_tc_group(int D) { return D == 32 ? TcShape32::GROUP : D == 64 ? TcShape64::GROUP : 0; }
+int scan_tc_group(int D, int variant) {
+  if (D == 32) return variant == 2 ? TcShape32c::GROUP : TcShape32::GROUP;
+  return D == 64 ? TcShape64::GROUP : 0;
+}
 
 int scan_tc_max_stride() { return 8; }
 
-int scan_tc_variants(int D) { return D == 32 ? 2 : D == 64 ? 1 : 0; }
+int scan_tc_variants(int D) { return D == 32 ? 3 : D == 64 ? 1 : 0; }
 
 int scan_tc_lists_per_range(int D, int variant) {
-  if (D == 32) return variant == 1 ? TcShape32b::HALVES : TcShape32::HALVES;
+  if (D == 32) return variant == 1 ? TcShape32b::HALVES : variant == 2 ? TcShape32c::HALVES : TcShape32::HALVES;
   return D == 64 ? TcShape64::HALVES : 1;
 }
 
@@ -696,6 +708,7 @@ static int tc_fits(const DevIndex& ix, int cand_depth) {
 
 int scan_tc_fits(const DevIndex& ix, int cand_depth, int variant, int fp8) {
   if (ix.D == 32 && variant == 1) return fp8 ? tc_fits<TcShape32bf8>(ix, cand_depth) : tc_fits<TcShape32b>(ix, cand_depth);
+  if (ix.D == 32 && variant == 2) return fp8 ? tc_fits<TcShape32cf8>(ix, cand_depth) : tc_fits<TcShape32c>(ix, cand_depth);
   if (ix.D == 32) return fp8 ? tc_fits<TcShape32f8>(ix, cand_depth) : tc_fits<TcShape32>(ix, cand_depth);
   if (ix.D == 64) return fp8 ? tc_fits<TcShape64f8>(ix, cand_depth) : tc_fits<TcShape64>(ix, cand_depth);
   return 0;
@@ -734,6 +747,9 @@ cudaError_t launch_scan_tc(const DevIndex& ix, const ScanArgs& a, bool dense, in
   if (ix.D == 32 && a.tc_variant == 1)
     return a.fp8 ? launch_tc_any<TcShape32bf8>(ix, a, dense, num_sms, st)
                  : launch_tc_any<TcShape32b>(ix, a, dense, num_sms, st);
+  if (ix.D == 32 && a.tc_variant == 2)
+    return a.fp8 ? launch_tc_any<TcShape32cf8>(ix, a, dense, num_sms, st)
+                 : launch_tc_any<TcShape32c>(ix, a, dense, num_sms, st);
   if (ix.D == 32)
     return a.fp8 ? launch_tc_any<TcShape32f8>(ix, a, dense, num_sms, st)
                  : launch_tc_any<TcShape32>(ix, a, dense, num_sms, st);
