@@ -75,6 +75,18 @@ WORKLOADS = {
         L=20_000_000, gc=0.41, tandem=0.025, segdup=0.025, inter=0.0, ref_seed=3,
         n_reads=32768, read_len=150, sub=0.01, indel=0.005, read_seed=4,
         s=4, m=2, t=2, variant=1, N=150, stride=1, k=8),
+    "human3G": dict(
+        desc="3.1 Gbp human-shaped order-2 Markov genome (GC 41%, 50% interspersed repeats), 100k x 150 bp planted "
+             "reads (1% sub, 0.5% indel geom p=0.7), d=64 (s=4 m=2 t=2 fine-tuned), N=150, stride 1, exhaustive, top-8",
+        L=3_100_000_000, gc=0.41, tandem=0.0, segdup=0.0, inter=0.50, ref_seed=7,
+        n_reads=100_000, read_len=150, sub=0.01, indel=0.005, read_seed=8,
+        s=4, m=2, t=2, variant=1, N=150, stride=1, k=8),
+    "maize2300M": dict(
+        desc="2.3 Gbp maize-shaped order-2 Markov genome (GC 47%, 85% interspersed repeats), 100k x 150 bp planted "
+             "reads (1% sub, 0.5% indel geom p=0.7), d=64 (s=4 m=2 t=2 fine-tuned), N=150, stride 1, exhaustive, top-8",
+        L=2_300_000_000, gc=0.47, tandem=0.0, segdup=0.0, inter=0.85, ref_seed=8,
+        n_reads=100_000, read_len=150, sub=0.01, indel=0.005, read_seed=9,
+        s=4, m=2, t=2, variant=1, N=150, stride=1, k=8),
     "uniform100k": dict(
         desc="100 kbp uniform reference, 256 x 150 bp planted reads (1% sub, 0.5% indel), d=64, stride 1, top-8",
         L=100_000, gc=None, ref_seed=1, n_reads=256, read_len=150, sub=0.01, indel=0.005, read_seed=2,
@@ -646,8 +658,8 @@ def main():
         "ms_per_step": 1000.0 * elapsed / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
         "config": {"workload": args.workload + ": " + wl["desc"], "reads_per_step_per_gpu": B, "n_windows": W,
-                   "scores_per_step_per_gpu": scores_step, "l2": "inputs larger than L2 (0.8 GB index streamed "
-                   "per scan pass; reads 20 MB/step)", "index_build_s": index_s, "parallelism": f"replicated index, "
+                   "scores_per_step_per_gpu": scores_step, "l2": f"inputs larger than L2 ({(wl['L'] / 4 + 8 * W) / 1e9:.1f} GB index "
+                   f"streamed per scan pass; reads {B * wl['read_len'] / 1e6:.0f} MB/step)", "index_build_s": index_s, "parallelism": f"replicated index, "
                    f"reads sharded over {ws} GPU(s)",
                    "scan_tiles": None if tuned is None else {"variant": tuned[0], "items_per_sm": tuned[1],
                                                               "tuned_scan_ms": tuned[2]}},

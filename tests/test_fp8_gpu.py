@@ -95,9 +95,9 @@ def test_topk_fp8_other_shapes(lib, pp):
 
 
 def test_fp8_tile_variants_agree(lib, case):
-    """Both d = 64 tile variants score the same products: the same re-scored top-k."""
+    """All d = 64 tile variants score the same products: the same re-scored top-k."""
     out = []
-    for v in (0, 1):
+    for v in (0, 1, 2):
         lib.rope_autotune_set(case["idx"], 256, v, 16, k=8, precision="fp8")
         gw, gs = lib.rope_score_topk(case["idx"], case["f32"], case["bf16"], case["norms"], k=8, precision="fp8")
         lib.rope_sync_status()
@@ -105,5 +105,6 @@ def test_fp8_tile_variants_agree(lib, case):
         assert lib.rope_autotune_query(case["idx"], 256, k=8, precision="fp8")[0] == v
     lib.rope_autotune_enable(False)
     lib.rope_autotune_enable(True)
-    assert np.array_equal(out[0][0], out[1][0])
-    assert np.array_equal(out[0][1], out[1][1])
+    for o in out[1:]:
+        assert np.array_equal(out[0][0], o[0])
+        assert np.array_equal(out[0][1], o[1])
