@@ -395,7 +395,6 @@ def run_ladder(args, wl):
         elapsed = float(t.item())
         dist.barrier()
     rm.rope_sync_status()
-    top2_step0 = step_outs[0][0][:, :2].clone()  # the refinement leg's candidates (batch 0)
     stage_ms = rm.rope_profile_read(args.steps)
     rm.rope_profile_enable(0)
     w = outs[(args.steps - 1) % 2][0][:, 0].cpu().numpy()
@@ -510,6 +509,7 @@ def main():
         elapsed = float(t.item())
         dist.barrier()
     rm.rope_sync_status()
+    top2_step0 = step_outs[0][0][:, :2].clone()  # the refinement leg's candidates (batch 0)
     stage_ms = rm.rope_profile_read(args.steps)
     rm.rope_profile_enable(0)
     for i, top in enumerate(tops):

@@ -88,27 +88,6 @@ __device__ __forceinline__ uint32_t bin_at(const uint32_t* __restrict__ packed, 
 //   c   <- c * e^{-2 pi i f S/N}
 // (for S = 1 these are exactly the paper's relations: every entry rotates by
 // w^{-f}, the leaving s-mer loses w^{-f}, the entering one gains w^{f(N-s)}).
-// ---------------------------------------------------------------- packed FP32 pairs
-
-__device__ __forceinline__ uint64_t f32x2_pack(float a, float b) {
-  uint64_t r;
-  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
-  return r;
-}
-__device__ __forceinline__ void f32x2_unpack(uint64_t r, float& a, float& b) {
-  asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(r));
-}
-__device__ __forceinline__ uint64_t f32x2_mul(uint64_t a, uint64_t b) {
-  uint64_t r;
-  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
-  return r;
-}
-__device__ __forceinline__ uint64_t f32x2_fma(uint64_t a, uint64_t b, uint64_t c) {
-  uint64_t r;
-  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
-  return r;
-}
-
 template <int BPL>
 struct ChainB {
   float cr[BPL], ci[BPL];
@@ -143,19 +122,12 @@ struct ChainB {
     for (int i = 0; i < BPL; ++i) cr[i] = ci[i] = 0.f;
   }
 
-  // c <- c e^{-2 pi i f S / N}: cr' = fma(cr, rc, ci * -rs), ci' = fma(cr, rs,
-  // ci * rc), two entries per packed FP32x2 multiply / fma (each lane rounded
-  // exactly as the scalar fmaf form)
   __device__ __forceinline__ void rotate() {
-    static_assert(BPL % 2 == 0, "entries are rotated in pairs");
-    const uint64_t RC = f32x2_pack(rc, rc), RS = f32x2_pack(rs, rs), NRS = f32x2_pack(-rs, -rs);
 #pragma unroll
-    for (int i = 0; i < BPL; i += 2) {
-      const uint64_t X = f32x2_pack(cr[i], cr[i + 1]), Y = f32x2_pack(ci[i], ci[i + 1]);
-      const uint64_t nx = f32x2_fma(X, RC, f32x2_mul(Y, NRS));
-      const uint64_t ny = f32x2_fma(X, RS, f32x2_mul(Y, RC));
-      f32x2_unpack(nx, cr[i], cr[i + 1]);
-      f32x2_unpack(ny, ci[i], ci[i + 1]);
+    for (int i = 0; i < BPL; ++i) {
+      const float xr = cr[i], xi = ci[i];
+      cr[i] = fmaf(xr, rc, -xi * rs);
+      ci[i] = fmaf(xr, rs, xi * rc);
     }
   }
 

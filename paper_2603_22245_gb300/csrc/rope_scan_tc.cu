@@ -512,28 +512,20 @@ __global__ void __launch_bounds__(Sh::NTHREADS, 1) scan_tc_kernel(DevIndex ix, S
           if (!mbar_wait_warp(&bar_bempty[bslot], bphase ^ 1u, abort_flag, a.status, wlim)) goto gen_done;
           {
             uint8_t* bt = b_ring + bslot * Sh::B_SLOT_BYTES;
-            // the entries scaled by 1/sqrt(C_j) (packed FP32x2 multiplies)
-            float sr[BPL], si[BPL];
-            {
-              const uint64_t NV = f32x2_pack(nv, nv);
-#pragma unroll
-              for (int e = 0; e < BPL; e += 2) {
-                f32x2_unpack(f32x2_mul(f32x2_pack(ch.cr[e], ch.cr[e + 1]), NV), sr[e], sr[e + 1]);
-                f32x2_unpack(f32x2_mul(f32x2_pack(ch.ci[e], ch.ci[e + 1]), NV), si[e], si[e + 1]);
-              }
-            }
             // packed operand words of cr, ci and -cr (sign bits flipped)
             constexpr int NW = BPL * Sh::EB / 4;
             uint32_t pr[NW], pi[NW], pn[NW];
 #pragma unroll
             for (int hh = 0; hh < NW; ++hh) {
               if constexpr (Sh::FP8) {
-                pr[hh] = f32x4_to_e4m3(sr[4 * hh], sr[4 * hh + 1], sr[4 * hh + 2], sr[4 * hh + 3]);
-                pi[hh] = f32x4_to_e4m3(si[4 * hh], si[4 * hh + 1], si[4 * hh + 2], si[4 * hh + 3]);
+                pr[hh] = f32x4_to_e4m3(ch.cr[4 * hh] * nv, ch.cr[4 * hh + 1] * nv, ch.cr[4 * hh + 2] * nv,
+                                       ch.cr[4 * hh + 3] * nv);
+                pi[hh] = f32x4_to_e4m3(ch.ci[4 * hh] * nv, ch.ci[4 * hh + 1] * nv, ch.ci[4 * hh + 2] * nv,
+                                       ch.ci[4 * hh + 3] * nv);
                 pn[hh] = pr[hh] ^ 0x80808080u;
               } else {
-                const __nv_bfloat162 rr = __floats2bfloat162_rn(sr[2 * hh], sr[2 * hh + 1]);
-                const __nv_bfloat162 ii = __floats2bfloat162_rn(si[2 * hh], si[2 * hh + 1]);
+                const __nv_bfloat162 rr = __floats2bfloat162_rn(ch.cr[2 * hh] * nv, ch.cr[2 * hh + 1] * nv);
+                const __nv_bfloat162 ii = __floats2bfloat162_rn(ch.ci[2 * hh] * nv, ch.ci[2 * hh + 1] * nv);
                 pr[hh] = *reinterpret_cast<const uint32_t*>(&rr);
                 pi[hh] = *reinterpret_cast<const uint32_t*>(&ii);
                 pn[hh] = pr[hh] ^ 0x80008000u;
