@@ -213,13 +213,32 @@ def cpu_baseline(ref, rd, wl, n_reads, n_windows):
     op = oracle.Params(s=wl["s"], m=wl["m"], t=wl["t"], variant=wl["variant"], N=wl["N"], stride=wl["stride"])
     W = oracle.n_windows(len(ref), wl["N"], wl["stride"])
     n_windows = min(n_windows, W)
+    cores = oracle.max_threads()
     sub = rd.subset(np.arange(min(n_reads, rd.n)))
     t0 = time.perf_counter()
-    oracle.score_topk(ref, sub.seqs, sub.offsets, op, k=wl["k"], j_begin=0, j_end=n_windows)
+    oracle.score_topk(ref, sub.seqs, sub.offsets, op, k=wl["k"], j_begin=0, j_end=n_windows, n_threads=cores)
     dt = time.perf_counter() - t0
-    return {"value": sub.n * n_windows / dt, "unit": UNIT, "cores": oracle.max_threads(), "kind": "oracle",
+    # the oracle's full-DP Levenshtein distance (reranker labels) on all cores
+    n_ld = 100_000
+    rng = np.random.default_rng(0)
+    ri = rng.integers(0, rd.n, n_ld)
+    ws = rng.integers(0, len(ref) - wl["N"], n_ld)
+    t0 = time.perf_counter()
+    oracle.levenshtein_pairs(ref, rd.seqs, rd.offsets, ri, ws, wl["N"], n_threads=cores)
+    dt_ld = time.perf_counter() - t0
+    # the same scoring on one core, on an eighth of the sample (last: it sets
+    # the oracle's thread count to 1)
+    one = rd.subset(np.arange(max(1, sub.n // 8)))
+    t0 = time.perf_counter()
+    oracle.score_topk(ref, one.seqs, one.offsets, op, k=wl["k"], j_begin=0, j_end=n_windows, n_threads=1)
+    dt1 = time.perf_counter() - t0
+    return {"value": sub.n * n_windows / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"{sub.n} reads x the first {n_windows} windows, exhaustive FP64 scoring + full sort",
-            "seconds": dt}
+            "seconds": dt,
+            "single_thread": {"value": one.n * n_windows / dt1, "unit": UNIT, "cores": 1, "seconds": dt1,
+                              "sample": f"{one.n} reads x the first {n_windows} windows"},
+            "levenshtein": {"pairs_per_s": n_ld / dt_ld, "cores": cores, "seconds": dt_ld,
+                            "sample": f"{n_ld} (read head, window) pairs of {wl['N']} letters, full DP"}}
 
 
 def rerank_leg(rm, idx, ref, wl, args):
