@@ -64,6 +64,12 @@ def _load():
             "oracle_mlp_forward": ([p, p, p, f64, i32, i32, p, i64, p], None),
             "oracle_mlp_grad": ([p, p, p, f64, i32, i32, p, p, i64, p, p, p, p], f64),
             "oracle_adamw": ([p, p, p, p, i64, i64, f64, f64, f64, f64, f64], None),
+            "oracle_splitmix64": ([ctypes.c_uint64, ctypes.c_uint64], ctypes.c_uint64),
+            "oracle_mutate": ([p, i64, i64, i32, f64, ctypes.c_uint64, ctypes.c_uint64, p, p], i32),
+            "oracle_fragment_thresholds": ([p, i64, i32, i32, i64, i64, i32, i32, i32, i32, p, i32, f64, i32,
+                                            ctypes.c_uint64, i32, p], i32),
+            "oracle_threshold_pairs": ([p, i64, p, p, i64, i32, i32, i64, i64, i32, i32, i32, i32, p, i32, p, i64,
+                                        p, p, p], i64),
         }
         for name, (args, res) in sig.items():
             fn = getattr(lib, name)
@@ -433,3 +439,56 @@ def refine(ref, seqs, offsets, cand_pos, radius: int, p: Params, n_threads: int 
         if f > out_f[i, c]:  # positions arrive in increasing order: ties keep the lower one
             out_p[i, c], out_f[i, c] = q, f
     return out_p, out_f, (owner, pos, fid)
+
+
+# ------------------------------------------------------------ threshold regime
+
+def splitmix64(seed: int, i: int) -> int:
+    """The i-th output (0-based) of SplitMix64 started at state ``seed``."""
+    return int(_load().oracle_splitmix64(seed & (2**64 - 1), i))
+
+
+def mutate(ref, start: int, N: int, err: float, seed: int, stream: int):
+    """N letters of a mutated copy of ref from ``start`` (see
+    ``oracle_mutate``): (letters uint8, (walked, deletions, insertions,
+    substitutions))."""
+    ref = _u8(ref)
+    out = np.empty(N, dtype=np.uint8)
+    counts = np.zeros(4, dtype=np.int64)
+    if _load().oracle_mutate(_p(ref), len(ref), start, N, err, seed & (2**64 - 1), stream, _p(out), _p(counts)) != 0:
+        raise ValueError("invalid letter")
+    return out, tuple(int(c) for c in counts)
+
+
+def fragment_thresholds(ref, p: Params, err: float, n_samples: int, seed: int, j0: int = 0, count: int | None = None,
+                        n_threads: int = 0) -> np.ndarray:
+    """§3.4: per window, the mean fidelity against n_samples mutated copies
+    at rate err (its cutting threshold for that mutation rate)."""
+    ref = _u8(ref)
+    if count is None:
+        count = n_windows(len(ref), p.N, p.stride) - j0
+    out = np.empty(count)
+    if _load().oracle_fragment_thresholds(_p(ref), len(ref), p.N, p.stride, j0, count, p.s, p.m, p.t, p.variant,
+                                          _p(p.bin_map), p.score_mode, err, n_samples, seed & (2**64 - 1),
+                                          n_threads, _p(out)) != 0:
+        raise ValueError("oracle_fragment_thresholds failed")
+    return out
+
+
+def threshold_pairs(ref, seqs, offsets, p: Params, thr: np.ndarray, j_begin: int = 0, cap: int = 1 << 20):
+    """§3.5 multi-locus output: every (read, window) with fidelity >= the
+    window's threshold thr[j - j_begin] over windows [j_begin, j_begin +
+    len(thr)), exhaustive FP64: (reads int64, windows int64, fidelities)."""
+    ref, seqs = _u8(ref), _u8(seqs)
+    offsets = np.ascontiguousarray(offsets, dtype=np.int64)
+    thr = np.ascontiguousarray(thr, dtype=np.float64)
+    n = len(offsets) - 1
+    r = np.empty(cap, dtype=np.int64)
+    w = np.empty(cap, dtype=np.int64)
+    f = np.empty(cap)
+    got = _load().oracle_threshold_pairs(_p(ref), len(ref), _p(seqs), _p(offsets), n, p.N, p.stride, j_begin,
+                                         j_begin + len(thr), p.s, p.m, p.t, p.variant, _p(p.bin_map), p.score_mode,
+                                         _p(thr), cap, _p(r), _p(w), _p(f))
+    if got < 0 or got > cap:
+        raise ValueError("oracle_threshold_pairs failed or exceeded cap")
+    return r[:got], w[:got], f[:got]

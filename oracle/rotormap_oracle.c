@@ -644,3 +644,155 @@ void oracle_adamw(double* p, const double* g, double* m, double* v, int64_t n, i
     p[i] = p[i] * (1.0 - lr * wd) - lr * (m[i] / c1) / (sqrt(v[i] / c2) + eps);
   }
 }
+
+/* ---------------------------------------------------------------------- */
+/* Threshold regime: per-fragment fidelity thresholds (§3.4: for a target  */
+/* mutation rate, the expected fidelity of each reference fragment against */
+/* mutated copies of itself, used as its cutting threshold) and the        */
+/* multi-locus output of §3.5 (every window whose fidelity with the read    */
+/* reaches its threshold).                                                  */
+
+/* SplitMix64 (Steele, Lea, Flood, OOPSLA 2014): the i-th output (0-based)
+ * of the generator started at state `seed`: the state advances by the
+ * golden-ratio increment and each state is passed through the finaliser. */
+static uint64_t sm64_mix(uint64_t z) {
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+  return z ^ (z >> 31);
+}
+uint64_t oracle_splitmix64(uint64_t seed, uint64_t i) { return sm64_mix(seed + (i + 1) * 0x9E3779B97F4A7C15ULL); }
+
+static double sm64_unit(uint64_t z) { return (double)(z >> 11) * (1.0 / 9007199254740992.0); }
+
+/* N letters of a mutated copy of ref read from `start`: each reference
+ * letter in turn is mutated with probability err, the mutation being a
+ * deletion, an insertion (a random letter before it) or a substitution (one
+ * of the three other letters) with probability 1/3 each (the even split of
+ * the paper's mutated companions, §2.4 scoring of correlations). Randomness:
+ * the SplitMix64 stream keyed by key = oracle_splitmix64(seed, stream);
+ * reference letter number d (from start) uses its draws 3d, 3d+1, 3d+2
+ * (mutation?, which kind, which letter). Past the end of ref the walk reads
+ * 'A'. Writes upper-case letters to out[0..N) and the numbers of reference
+ * letters walked, deletions, insertions and substitutions to counts[0..3]. */
+int oracle_mutate(const uint8_t* ref, int64_t L, int64_t start, int N, double err, uint64_t seed, uint64_t stream,
+                  uint8_t* out, int64_t* counts) {
+  static const char ACGT[4] = {'A', 'C', 'G', 'T'};
+  const uint64_t key = oracle_splitmix64(seed, stream);
+  int n = 0;
+  int64_t d = 0, nd = 0, ni = 0, ns = 0;
+  while (n < N) {
+    const int64_t pos = start + d;
+    int c = pos < L ? oracle_base(ref[pos]) : 0;
+    if (c < 0) return -1;
+    const double u0 = sm64_unit(oracle_splitmix64(key, 3 * (uint64_t)d));
+    const double u1 = sm64_unit(oracle_splitmix64(key, 3 * (uint64_t)d + 1));
+    const uint64_t z2 = oracle_splitmix64(key, 3 * (uint64_t)d + 2);
+    ++d;
+    if (u0 < err) {
+      const int kind = (int)(u1 * 3.0);
+      if (kind == 0) { /* deletion: the letter is skipped */
+        ++nd;
+        continue;
+      }
+      if (kind == 1) { /* insertion: a random letter, then the reference letter */
+        ++ni;
+        out[n++] = (uint8_t)ACGT[z2 >> 62];
+        if (n < N) out[n++] = (uint8_t)ACGT[c];
+        continue;
+      }
+      ++ns; /* substitution: one of the three other letters */
+      c = (c + 1 + (int)(sm64_unit(z2) * 3.0)) & 3;
+    }
+    out[n++] = (uint8_t)ACGT[c];
+  }
+  if (counts) {
+    counts[0] = d;
+    counts[1] = nd;
+    counts[2] = ni;
+    counts[3] = ns;
+  }
+  return 0;
+}
+
+/* Per-fragment threshold of windows j0 .. j0+count-1 (start j*stride): the
+ * mean over n_samples mutated copies (stream j*n_samples + t, t < n_samples)
+ * of the fidelity between the window's encoding and the encoding of the
+ * copy's N letters (concatenated or per-band score, §2.4/§2.5). */
+int oracle_fragment_thresholds(const uint8_t* ref, int64_t L, int N, int stride, int64_t j0, int64_t count, int s,
+                               int m, int t, int variant, const uint16_t* map, int score_mode, double err,
+                               int n_samples, uint64_t seed, int n_threads, double* out) {
+  const int nb = 1 << (2 * t);
+  const int D = m * nb;
+  int bad = 0;
+#ifdef _OPENMP
+  if (n_threads > 0) omp_set_num_threads(n_threads);
+#pragma omp parallel for schedule(dynamic, 16)
+#endif
+  for (int64_t i = 0; i < count; ++i) {
+    const int64_t j = j0 + i;
+    const int64_t w = j * stride;
+    double* buf = (double*)malloc(sizeof(double) * 4 * (size_t)D);
+    uint8_t* copy = (uint8_t*)malloc((size_t)N);
+    if (!buf || !copy || w < 0 || w + N > L) {
+      bad = 1;
+      out[i] = NAN;
+      free(buf);
+      free(copy);
+      continue;
+    }
+    double *xr = buf, *xi = buf + D, *yr = buf + 2 * (size_t)D, *yi = buf + 3 * (size_t)D;
+    double acc = 0.0;
+    if (oracle_embed(ref + w, N, s, m, t, variant, map, yr, yi) != 0) bad = 1;
+    for (int k = 0; k < n_samples && !bad; ++k) {
+      if (oracle_mutate(ref, L, w, N, err, seed, (uint64_t)j * n_samples + k, copy, NULL) != 0 ||
+          oracle_embed(copy, N, s, m, t, variant, map, xr, xi) != 0) {
+        bad = 1;
+        break;
+      }
+      acc += score_mode == 1 ? oracle_fidelity_per_band(xr, xi, yr, yi, m, nb) : oracle_fidelity(xr, xi, yr, yi, D);
+    }
+    out[i] = acc / n_samples;
+    free(buf);
+    free(copy);
+  }
+  return bad ? -1 : 0;
+}
+
+/* Every (read, window) pair with fidelity >= thr[j - jb] over windows
+ * [jb, je), by exhaustive FP64 scoring, in (read, window) order. Writes at
+ * most cap pairs; returns the number of pairs found (or -1). */
+int64_t oracle_threshold_pairs(const uint8_t* ref, int64_t L, const uint8_t* seqs, const int64_t* offsets,
+                               int64_t n_reads, int N, int stride, int64_t jb, int64_t je, int s, int m, int t,
+                               int variant, const uint16_t* map, int score_mode, const double* thr, int64_t cap,
+                               int64_t* out_read, int64_t* out_win, double* out_fid) {
+  const int nb = 1 << (2 * t);
+  const int D = m * nb;
+  double* buf = (double*)malloc(sizeof(double) * 4 * (size_t)D);
+  if (!buf) return -1;
+  double *xr = buf, *xi = buf + D, *yr = buf + 2 * (size_t)D, *yi = buf + 3 * (size_t)D;
+  int64_t found = 0;
+  for (int64_t r = 0; r < n_reads; ++r) {
+    if (offsets[r + 1] - offsets[r] < N || oracle_embed(seqs + offsets[r], N, s, m, t, variant, map, xr, xi) != 0) {
+      free(buf);
+      return -1;
+    }
+    for (int64_t j = jb; j < je; ++j) {
+      if (j * stride + N > L || oracle_embed(ref + j * stride, N, s, m, t, variant, map, yr, yi) != 0) {
+        free(buf);
+        return -1;
+      }
+      const double f =
+          score_mode == 1 ? oracle_fidelity_per_band(xr, xi, yr, yi, m, nb) : oracle_fidelity(xr, xi, yr, yi, D);
+      if (f >= thr[j - jb]) {
+        if (found < cap) {
+          out_read[found] = r;
+          out_win[found] = j;
+          out_fid[found] = f;
+        }
+        ++found;
+      }
+    }
+  }
+  free(buf);
+  return found;
+}

@@ -605,3 +605,61 @@ def test_refine_ties_take_the_lower_position():
     op = oracle.Params(N=150)
     pos, fid, _ = oracle.refine(ref, read, offs, np.array([[300]]), 20, op)
     assert pos[0, 0] == 284 and fid[0, 0] == pytest.approx(1.0, abs=1e-12)  # 284 = 100 (mod 8), >= 280
+
+
+# ---------------------------------------------------------------- threshold regime (§3.4 thresholds, §3.5 output)
+
+def test_splitmix64_published_vector():
+    """SplitMix64 started at state 0: the published first three outputs."""
+    assert [oracle.splitmix64(0, i) for i in range(3)] == [0xE220A8397B1DCDAF, 0x6E789E6AA1B965F4,
+                                                          0x06C45D188009454F]
+
+
+def test_mutate_rate_split_and_edit_bound():
+    """Mutations occur at the given rate per reference letter, split evenly
+    between deletions, insertions and substitutions; a copy with no mutation
+    is the reference itself; and the copy is within (number of applied
+    mutations) edits of the reference letters it walked."""
+    ref = synth.uniform_ref(50_000, 131)
+    c, cnt = oracle.mutate(ref, 1000, 150, 0.0, 5, 0)
+    assert bytes(c) == bytes(ref[1000:1150]).upper() and cnt == (150, 0, 0, 0)
+    tot = np.zeros(4)
+    for k in range(600):
+        c, cnt = oracle.mutate(ref, 37 * k, 150, 0.3, 11, k)
+        walked, nd, ni, ns = cnt
+        ld = oracle.levenshtein(c, ref[37 * k:37 * k + walked])
+        assert ld <= nd + ni + ns
+        tot += cnt
+    n_mut = tot[1:].sum()
+    assert abs(n_mut / tot[0] - 0.3) < 4 * math.sqrt(0.3 * 0.7 / tot[0])
+    for share in tot[1:] / n_mut:
+        assert abs(share - 1 / 3) < 4 * math.sqrt(2 / 9 / n_mut)
+
+
+def test_fragment_thresholds_identity_and_monotone():
+    """At rate 0 every copy is the fragment: threshold 1 (identity); the mean
+    threshold falls as the mutation rate grows and stays in [0, 1]."""
+    ref = synth.uniform_ref(8000, 141)
+    op = oracle.Params(N=150)
+    assert np.allclose(oracle.fragment_thresholds(ref, op, 0.0, 3, 1, 0, 200), 1.0, atol=1e-12)
+    means = [oracle.fragment_thresholds(ref, op, e, 8, 2, 0, 300).mean() for e in (0.02, 0.1, 0.3)]
+    assert 1.0 > means[0] > means[1] > means[2] > 0.0
+
+
+def test_threshold_pairs_against_topk():
+    """Exhaustive threshold output agrees with the exhaustive top-k: with a
+    threshold of 0 every pair is reported; with a constant threshold t, each
+    read's pairs are exactly its windows of the top-k list scoring >= t."""
+    ref = synth.uniform_ref(3000, 151)
+    rd = synth.reads(ref, 6, seed=152)
+    op = oracle.Params(N=150)
+    W = oracle.n_windows(len(ref), 150, 1)
+    r, w, f = oracle.threshold_pairs(ref, rd.seqs, rd.offsets, op, np.zeros(W))
+    assert len(r) == 6 * W
+    ow, os_ = oracle.score_topk(ref, rd.seqs, rd.offsets, op, k=200)
+    t = 0.3
+    r, w, f = oracle.threshold_pairs(ref, rd.seqs, rd.offsets, op, np.full(W, t))
+    for i in range(6):
+        want = set(ow[i][os_[i] >= t].tolist())
+        assert len(want) < 200  # the top-200 list reaches below t
+        assert set(w[r == i].tolist()) == want
