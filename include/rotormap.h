@@ -250,6 +250,34 @@ rope_status rope_score_dense(const rope_index* idx, const float* emb_f32, const 
 rope_status rope_map(const rope_index* idx, const uint8_t* seqs, const int64_t* offsets, int64_t n_reads,
                      const rope_score_opts* opts, int64_t* out_win, float* out_score, cudaStream_t stream);
 
+/* ---- threshold regime (§3.4 per-fragment thresholds, §3.5 multi-locus output)
+ * rope_fragment_thresholds: for windows [j_begin, j_begin + count) of the
+ * index, the threshold of window j for mutation rate err: the mean fidelity
+ * (the index's score mode, FP32 sums) between the window and n_samples
+ * mutated copies of it. A copy is the first N letters of a walk from the
+ * window's start in which each reference letter is mutated with probability
+ * err: deleted, preceded by a random inserted letter, or substituted by one
+ * of the three other letters, each with probability 1/3 (past the reference
+ * end the walk reads A). Its draws are SplitMix64 outputs: the stream keyed
+ * by output j*n_samples + t of the generator started at `seed` (copy t),
+ * outputs 3d, 3d+1, 3d+2 of that stream for reference letter d of the walk,
+ * so the copies are fixed by (seed, j, t). n_samples: a power of two in
+ * [1, 32]; complex dimension <= 64. out: count floats (device).
+ *
+ * rope_score_threshold: every (read, window) pair of windows [j_begin, j_end)
+ * (j_end <= 0: all) whose BF16 tensor-core score (normalised operands, FP32
+ * accumulation, as rope_score_topk's scan) is >= thr[j] (device, one float
+ * per window of the index). The count of such pairs is written to
+ * *out_count (device); the first min(count, cap) of them, in no particular
+ * order, to out_read / out_win (window number j; start j*stride) /
+ * out_score (device). A count above cap means pairs were dropped: call
+ * again with a larger cap. Score mode 0, d = 64 (tile variant 0) or 128. */
+rope_status rope_fragment_thresholds(const rope_index* idx, double err, int32_t n_samples, uint64_t seed,
+                                     int64_t j_begin, int64_t count, float* out, cudaStream_t stream);
+rope_status rope_score_threshold(const rope_index* idx, const uint16_t* emb_bf16, int64_t n_reads, const float* thr,
+                                 int64_t j_begin, int64_t j_end, int64_t cap, int64_t* out_read, int64_t* out_win,
+                                 float* out_score, unsigned long long* out_count, cudaStream_t stream);
+
 /* ---- refinement (§3.4, increasing the accuracy) -------------------------
  * Slides the window one letter at a time around coarse candidates and scores
  * each position with the encoding p (which may differ from the index's: e.g.

@@ -759,40 +759,52 @@ int oracle_fragment_thresholds(const uint8_t* ref, int64_t L, int N, int stride,
 }
 
 /* Every (read, window) pair with fidelity >= thr[j - jb] over windows
- * [jb, je), by exhaustive FP64 scoring, in (read, window) order. Writes at
- * most cap pairs; returns the number of pairs found (or -1). */
+ * [jb, je), by exhaustive FP64 scoring (each window embedded once and scored
+ * against every read), in (read, window) order. Writes at most cap pairs;
+ * returns the number of pairs found (or -1). */
 int64_t oracle_threshold_pairs(const uint8_t* ref, int64_t L, const uint8_t* seqs, const int64_t* offsets,
                                int64_t n_reads, int N, int stride, int64_t jb, int64_t je, int s, int m, int t,
                                int variant, const uint16_t* map, int score_mode, const double* thr, int64_t cap,
                                int64_t* out_read, int64_t* out_win, double* out_fid) {
   const int nb = 1 << (2 * t);
   const int D = m * nb;
-  double* buf = (double*)malloc(sizeof(double) * 4 * (size_t)D);
-  if (!buf) return -1;
-  double *xr = buf, *xi = buf + D, *yr = buf + 2 * (size_t)D, *yi = buf + 3 * (size_t)D;
-  int64_t found = 0;
-  for (int64_t r = 0; r < n_reads; ++r) {
-    if (offsets[r + 1] - offsets[r] < N || oracle_embed(seqs + offsets[r], N, s, m, t, variant, map, xr, xi) != 0) {
-      free(buf);
-      return -1;
+  const int64_t nw = je - jb;
+  double* x = (double*)malloc(sizeof(double) * 2 * (size_t)D * (size_t)(n_reads > 0 ? n_reads : 1));
+  double* y = (double*)malloc(sizeof(double) * 2 * (size_t)D);
+  uint8_t* hit = (uint8_t*)calloc((size_t)(n_reads > 0 ? n_reads : 1) * (size_t)(nw > 0 ? nw : 1), 1);
+  double* fid = (double*)malloc(sizeof(double) * (size_t)(n_reads > 0 ? n_reads : 1) * (size_t)(nw > 0 ? nw : 1));
+  int bad = !x || !y || !hit || !fid;
+  for (int64_t r = 0; r < n_reads && !bad; ++r)
+    if (offsets[r + 1] - offsets[r] < N ||
+        oracle_embed(seqs + offsets[r], N, s, m, t, variant, map, x + 2 * (size_t)D * r, x + 2 * (size_t)D * r + D) != 0)
+      bad = 1;
+  for (int64_t j = jb; j < je && !bad; ++j) {
+    if (j * stride + N > L || oracle_embed(ref + j * stride, N, s, m, t, variant, map, y, y + D) != 0) {
+      bad = 1;
+      break;
     }
-    for (int64_t j = jb; j < je; ++j) {
-      if (j * stride + N > L || oracle_embed(ref + j * stride, N, s, m, t, variant, map, yr, yi) != 0) {
-        free(buf);
-        return -1;
-      }
-      const double f =
-          score_mode == 1 ? oracle_fidelity_per_band(xr, xi, yr, yi, m, nb) : oracle_fidelity(xr, xi, yr, yi, D);
-      if (f >= thr[j - jb]) {
+    for (int64_t r = 0; r < n_reads; ++r) {
+      const double* xr = x + 2 * (size_t)D * r;
+      const double f = score_mode == 1 ? oracle_fidelity_per_band(xr, xr + D, y, y + D, m, nb)
+                                       : oracle_fidelity(xr, xr + D, y, y + D, D);
+      hit[r * nw + (j - jb)] = f >= thr[j - jb];
+      fid[r * nw + (j - jb)] = f;
+    }
+  }
+  int64_t found = 0;
+  for (int64_t r = 0; r < n_reads && !bad; ++r)
+    for (int64_t j = 0; j < nw; ++j)
+      if (hit[r * nw + j]) {
         if (found < cap) {
           out_read[found] = r;
-          out_win[found] = j;
-          out_fid[found] = f;
+          out_win[found] = jb + j;
+          out_fid[found] = fid[r * nw + j];
         }
         ++found;
       }
-    }
-  }
-  free(buf);
-  return found;
+  free(x);
+  free(y);
+  free(hit);
+  free(fid);
+  return bad ? -1 : found;
 }

@@ -997,6 +997,40 @@ extern "C" rope_status rope_score_topk(const rope_index* idx, const float* emb_f
   return st;
 }
 
+extern "C" rope_status rope_score_threshold(const rope_index* idx, const uint16_t* emb_bf16, int64_t n_reads,
+                                            const float* thr, int64_t j_begin, int64_t j_end, int64_t cap,
+                                            int64_t* out_read, int64_t* out_win, float* out_score,
+                                            unsigned long long* out_count, cudaStream_t stream) {
+  if (!idx) return fail(ROPE_ERR_INVALID_ARG, "index is NULL");
+  if (n_reads < 0 || cap < 0) return fail(ROPE_ERR_INVALID_ARG, "n_reads or cap < 0");
+  if (!thr || !out_count || (cap > 0 && (!out_read || !out_win || !out_score)))
+    return fail(ROPE_ERR_INVALID_ARG, "NULL pointer");
+  const DevIndex& ix = idx->ix;
+  const int64_t jb = j_begin > 0 ? j_begin : 0;
+  const int64_t je = j_end > 0 ? (j_end < ix.W ? j_end : ix.W) : ix.W;
+  if (jb > ix.W) return fail(ROPE_ERR_INVALID_ARG, "j_begin beyond the last window");
+  ROPE_CUDA(cudaMemsetAsync(out_count, 0, sizeof(unsigned long long), stream));
+  if (n_reads == 0 || je <= jb) return ROPE_OK;
+  if (!emb_bf16) return fail(ROPE_ERR_INVALID_ARG, "threshold scan needs emb_bf16");
+  DeviceCtx* c;
+  rope_status st = get_ctx(&c);
+  if (st != ROPE_OK) return st;
+  ScanPlan pl;
+  if ((st = plan_scan(idx, ROPE_PREC_BF16, n_reads, jb, je, 0, c->num_sms, &pl, 0)) != ROPE_OK) return st;
+  pl.a.emb_bf16 = emb_bf16;
+  pl.a.cand_depth = 1;
+  pl.a.status = c->status;
+  pl.a.thr = thr;
+  pl.a.thr_count = out_count;
+  pl.a.thr_cap = cap;
+  pl.a.thr_read = out_read;
+  pl.a.thr_win = out_win;
+  pl.a.thr_score = out_score;
+  const cudaError_t e = launch_scan_tc_threshold(ix, pl.a, c->num_sms, stream);
+  if (e != cudaSuccess) return fail(ROPE_ERR_CUDA, "threshold scan launch: %s", cudaGetErrorString(e));
+  return ROPE_OK;
+}
+
 extern "C" rope_status rope_score_dense(const rope_index* idx, const float* emb_f32, const uint16_t* emb_bf16,
                                         const float* norms, int64_t n_reads, int32_t precision, int64_t j_begin,
                                         int64_t count, float* out, cudaStream_t stream) {

@@ -133,8 +133,12 @@ __device__ __forceinline__ uint32_t bin_staged(const uint32_t* words, int64_t wo
   return __ldg(map_lsb + field);
 }
 
-template <class Sh, bool kDense>
+// kDense: every score written to a.dense. kThr: every score at or above its
+// window's threshold a.thr[j] appended to the a.thr_* pair arrays. Otherwise:
+// per-read candidate lists (top-k).
+template <class Sh, bool kDense, bool kThr = false>
 __global__ void __launch_bounds__(Sh::NTHREADS, 1) scan_tc_kernel(DevIndex ix, ScanArgs a, TcLaunch L) {
+  constexpr bool kLists = !kDense && !kThr;
   constexpr int D = Sh::D, NT = Sh::NT, T = Sh::T, STAGES = Sh::STAGES, NB = Sh::NB, A = Sh::A, BPL = Sh::BPL;
   extern __shared__ __align__(1024) uint8_t tc_smem_raw[];
   __shared__ __align__(8) uint64_t bar_bfull[NB], bar_bempty[NB];
@@ -244,7 +248,7 @@ __global__ void __launch_bounds__(Sh::NTHREADS, 1) scan_tc_kernel(DevIndex ix, S
         // a new read group: hand over the previous group's list, load the A
         // operand and start an empty list. The previous item's MMAs have all
         // completed: this thread consumed every accumulator they wrote.
-        if (!kDense && prev_grp >= 0) {
+        if (kLists && prev_grp >= 0) {
           const int64_t pr = (int64_t)prev_grp * Sh::GROUP + rs;
           if (pr < a.n_reads) flush(pr, seg_rng);
         }
@@ -268,7 +272,7 @@ __global__ void __launch_bounds__(Sh::NTHREADS, 1) scan_tc_kernel(DevIndex ix, S
         }
         thr = -INFINITY;
         worst = 0;
-        if (!kDense) {
+        if (kLists) {
           for (int e = 0; e < a.cand_depth; ++e) {
             ls[e * lstride] = -INFINITY;
             lw[e * lstride] = kEmptyWin;
@@ -276,7 +280,7 @@ __global__ void __launch_bounds__(Sh::NTHREADS, 1) scan_tc_kernel(DevIndex ix, S
         }
         prev_grp = grp;
         seg_rng = rng;
-      } else if (!kDense && have_read) {
+      } else if (kLists && have_read) {
         // the list carries on: this range's own slot holds no list
         a.cand[(((size_t)r * a.n_ranges + rng) * Sh::HALVES + h) * a.cand_depth].win = kUnusedWin;
       }
@@ -291,6 +295,24 @@ __global__ void __launch_bounds__(Sh::NTHREADS, 1) scan_tc_kernel(DevIndex ix, S
           const uint32_t col = (uint32_t)(((int)s * NT + tile) * 2 * T);
           const uint32_t jbase = st + (uint32_t)i;  // column n holds window jbase + n*A
           const bool full = jbase >= jlo && jbase + (uint32_t)((T - 1) * A) < jhi;
+          // threshold mode: lane l holds the thresholds of this warp's
+          // columns h*WPH + 32u + l (+inf outside the scanned range), and each
+          // 16-column chunk's smallest threshold is known to all lanes
+          constexpr int TPL = kThr ? Sh::WPH / 32 : 1;
+          float thr_lane[TPL], thr_min[2 * TPL];
+          if constexpr (kThr) {
+            static_assert(Sh::WPH % 32 == 0, "threshold mode: whole columns per lane");
+#pragma unroll
+            for (int u = 0; u < TPL; ++u) {
+              const uint32_t jl = jbase + (uint32_t)((h * Sh::WPH + 32 * u + lane) * A);
+              thr_lane[u] = (jl >= jlo && jl < jhi) ? __ldg(a.thr + jl) : INFINITY;
+              float mn = thr_lane[u];
+#pragma unroll
+              for (int o = 8; o > 0; o >>= 1) mn = fminf(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+              thr_min[2 * u] = __shfl_sync(0xffffffffu, mn, 0);
+              thr_min[2 * u + 1] = __shfl_sync(0xffffffffu, mn, 16);
+            }
+          }
 #pragma unroll
           for (int c0 = h * Sh::WPH; c0 < (h + 1) * Sh::WPH; c0 += 16) {
             const uint32_t taddr = tbase + lane_base + col + c0;
@@ -308,7 +330,30 @@ __global__ void __launch_bounds__(Sh::NTHREADS, 1) scan_tc_kernel(DevIndex ix, S
 #pragma unroll
             for (int n = 0; n < 16; n += 2) abs2_pair(vr[n], vr[n + 1], vi[n], vi[n + 1], sc[n], sc[n + 1]);
             const uint32_t jc = jbase + (uint32_t)(c0 * A);
-            if (kDense) {
+            if constexpr (kThr) {
+              // the chunk's scores against their windows' thresholds
+              const float m0 = fmax3(sc[0], sc[1], sc[2]), m1 = fmax3(sc[3], sc[4], sc[5]);
+              const float m2 = fmax3(sc[6], sc[7], sc[8]), m3 = fmax3(sc[9], sc[10], sc[11]);
+              const float m4 = fmax3(sc[12], sc[13], sc[14]);
+              const float mx = fmaxf(fmax3(m0, m1, m2), fmax3(m3, m4, sc[15]));
+              const int rel = c0 - h * Sh::WPH;  // the chunk's first column in this warp's share
+              const bool any = have_read && mx * Sh::SCORE_SCALE >= thr_min[rel >> 4];
+              if (__any_sync(0xffffffffu, any)) {
+#pragma unroll
+                for (int n = 0; n < 16; ++n) {
+                  const float th = __shfl_sync(0xffffffffu, thr_lane[rel >> 5], (rel & 31) + n);
+                  const float v = sc[n] * Sh::SCORE_SCALE;
+                  if (have_read && v >= th) {
+                    const unsigned long long slot = atomicAdd(a.thr_count, 1ull);
+                    if (slot < (unsigned long long)a.thr_cap) {
+                      a.thr_read[slot] = r;
+                      a.thr_win[slot] = (int64_t)(jc + (uint32_t)(n * A));
+                      a.thr_score[slot] = v;
+                    }
+                  }
+                }
+              }
+            } else if (kDense) {
               if (have_read) {
 #pragma unroll
                 for (int n = 0; n < 16; ++n) {
@@ -360,7 +405,7 @@ __global__ void __launch_bounds__(Sh::NTHREADS, 1) scan_tc_kernel(DevIndex ix, S
         }
       }
     }
-    if (!kDense && prev_grp >= 0) {
+    if (kLists && prev_grp >= 0) {
       const int64_t pr = (int64_t)prev_grp * Sh::GROUP + rs;
       if (pr < a.n_reads) flush(pr, seg_rng);
     }
@@ -616,7 +661,7 @@ using TcShape64f8 = TcShape<64, 2, 64, 2, 2, 8, 1, false, true>;
 // being captured into a graph query nothing).
 constexpr int kMaxDevices = 64;
 
-template <class Sh, bool kDense>
+template <class Sh, bool kDense, bool kThr = false>
 static size_t tc_dyn_limit() {
   static size_t cached[kMaxDevices] = {};  // value + 1, 0 = not read yet
   int dev = 0, optin = 0;
@@ -627,7 +672,7 @@ static size_t tc_dyn_limit() {
   if (cached[dev]) return cached[dev] - 1;
   cudaFuncAttributes fa{};
   if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess ||
-      cudaFuncGetAttributes(&fa, scan_tc_kernel<Sh, kDense>) != cudaSuccess) {
+      cudaFuncGetAttributes(&fa, scan_tc_kernel<Sh, kDense, kThr>) != cudaSuccess) {
     cudaGetLastError();
     return 0;
   }
@@ -638,14 +683,14 @@ static size_t tc_dyn_limit() {
 
 // Raises the kernel's dynamic shared-memory limit on the current device when
 // a launch needs more than it was last set to (once per size increase).
-template <class Sh, bool kDense>
+template <class Sh, bool kDense, bool kThr = false>
 static cudaError_t tc_reserve_smem(size_t smem) {
   static size_t set[kMaxDevices] = {};
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if (dev >= 0 && dev < kMaxDevices && set[dev] >= smem) return cudaSuccess;
-  e = cudaFuncSetAttribute(scan_tc_kernel<Sh, kDense>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  e = cudaFuncSetAttribute(scan_tc_kernel<Sh, kDense, kThr>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e == cudaSuccess && dev >= 0 && dev < kMaxDevices) set[dev] = smem;
   return e;
 }
@@ -706,18 +751,19 @@ int scan_tc_fits(const DevIndex& ix, int cand_depth, int variant, int fp8) {
   return 0;
 }
 
-template <class Sh, bool kDense>
+template <class Sh, bool kDense, bool kThr = false>
 static cudaError_t launch_tc(const DevIndex& ix, const ScanArgs& a, int num_sms, cudaStream_t st) {
   // the deepest B ring that fits (long windows at large strides and deep
   // candidate lists leave room for fewer slots)
   TcLaunch L;
-  const size_t limit = tc_dyn_limit<Sh, kDense>();
+  const size_t limit = tc_dyn_limit<Sh, kDense, kThr>();
   int nb = Sh::NB;
-  size_t smem = tc_smem_bytes<Sh>(ix, a.cand_depth, kDense, nb, &L);
-  while (smem > limit && nb > 1) smem = tc_smem_bytes<Sh>(ix, a.cand_depth, kDense, nb >>= 1, &L);
+  constexpr bool kNoLists = kDense || kThr;
+  size_t smem = tc_smem_bytes<Sh>(ix, a.cand_depth, kNoLists, nb, &L);
+  while (smem > limit && nb > 1) smem = tc_smem_bytes<Sh>(ix, a.cand_depth, kNoLists, nb >>= 1, &L);
   if (smem > limit) return cudaErrorInvalidValue;
-  auto kern = scan_tc_kernel<Sh, kDense>;
-  cudaError_t e = tc_reserve_smem<Sh, kDense>(smem);
+  auto kern = scan_tc_kernel<Sh, kDense, kThr>;
+  cudaError_t e = tc_reserve_smem<Sh, kDense, kThr>(smem);
   if (e != cudaSuccess) {
     cudaGetLastError();  // not sticky: leave no pending error for later launches
     return e;
@@ -748,6 +794,13 @@ cudaError_t launch_scan_tc(const DevIndex& ix, const ScanArgs& a, bool dense, in
   if (ix.D == 64)
     return a.fp8 ? launch_tc_any<TcShape64f8>(ix, a, dense, num_sms, st)
                  : launch_tc_any<TcShape64>(ix, a, dense, num_sms, st);
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_scan_tc_threshold(const DevIndex& ix, const ScanArgs& a, int num_sms, cudaStream_t st) {
+  if (ix.stride > scan_tc_max_stride() || a.fp8) return cudaErrorInvalidValue;
+  if (ix.D == 32) return launch_tc<TcShape32, false, true>(ix, a, num_sms, st);
+  if (ix.D == 64) return launch_tc<TcShape64, false, true>(ix, a, num_sms, st);
   return cudaErrorInvalidValue;
 }
 

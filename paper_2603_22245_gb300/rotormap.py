@@ -66,6 +66,8 @@ EXPORTS = {
     "rope_map": ([_P, _P, _P, _I64, _P, _P, _P, _P], ctypes.c_int),
     "rope_map_strands": ([_P, _P, _P, _I64, _P, _P, _P, _P, _P], ctypes.c_int),
     "rope_refine": ([_P, _P, _P, _P, _I64, _P, _I32, _I32, _P, _P, _P], ctypes.c_int),
+    "rope_fragment_thresholds": ([_P, ctypes.c_double, _I32, ctypes.c_uint64, _I64, _I64, _P, _P], ctypes.c_int),
+    "rope_score_threshold": ([_P, _P, _I64, _P, _I64, _I64, _I64, _P, _P, _P, _P, _P], ctypes.c_int),
     "rope_reranker_create": ([_I32, _I32, ctypes.c_uint64, _P], ctypes.c_int),
     "rope_reranker_free": ([_P], None),
     "rope_reranker_get": ([_P, _P, _P], ctypes.c_int),
@@ -343,6 +345,34 @@ def rope_refine(idx: Index, p: Params, seqs: torch.Tensor, offsets: torch.Tensor
     _check(load().rope_refine(idx.handle, ctypes.byref(pc), _ptr(seqs), _ptr(offsets), n, _ptr(cand_pos), nc, radius,
                               _ptr(out[0]), _ptr(out[1]), _stream(stream)))
     return out
+
+
+def rope_fragment_thresholds(idx: Index, err: float, n_samples: int = 8, seed: int = 0, j_begin: int = 0,
+                             count: int | None = None, stream=None) -> torch.Tensor:
+    """§3.4 per-window thresholds for mutation rate err (float32 [count])."""
+    if count is None:
+        count = idx.n_windows - j_begin
+    out = torch.empty(count, dtype=torch.float32, device="cuda")
+    _check(load().rope_fragment_thresholds(idx.handle, err, n_samples, seed & (2**64 - 1), j_begin, count, _ptr(out),
+                                           _stream(stream)))
+    return out
+
+
+def rope_score_threshold(idx: Index, emb_bf16: torch.Tensor, thr: torch.Tensor, cap: int = 1 << 20,
+                         j_begin: int = 0, j_end: int = 0, stream=None):
+    """§3.5 multi-locus output: (reads int64, window numbers int64, scores
+    float32, total count) of the pairs whose score reaches their window's
+    threshold; only the first min(count, cap) pairs are returned."""
+    n = emb_bf16.shape[0]
+    r = torch.empty(max(cap, 1), dtype=torch.int64, device="cuda")
+    w = torch.empty(max(cap, 1), dtype=torch.int64, device="cuda")
+    s = torch.empty(max(cap, 1), dtype=torch.float32, device="cuda")
+    cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
+    _check(load().rope_score_threshold(idx.handle, _ptr(emb_bf16), n, _ptr(thr.contiguous()), j_begin, j_end, cap,
+                                       _ptr(r), _ptr(w), _ptr(s), _ptr(cnt), _stream(stream)))
+    total = int(cnt.item())
+    k = min(total, cap)
+    return r[:k], w[:k], s[:k], total
 
 
 def rope_profile_enable(max_calls: int):
