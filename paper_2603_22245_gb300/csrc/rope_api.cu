@@ -1020,13 +1020,8 @@ extern "C" rope_status rope_score_threshold(const rope_index* idx, const uint16_
   pl.a.emb_bf16 = emb_bf16;
   pl.a.cand_depth = 1;
   pl.a.status = c->status;
-  pl.a.thr = thr;
-  pl.a.thr_count = out_count;
-  pl.a.thr_cap = cap;
-  pl.a.thr_read = out_read;
-  pl.a.thr_win = out_win;
-  pl.a.thr_score = out_score;
-  const cudaError_t e = launch_scan_tc_threshold(ix, pl.a, c->num_sms, stream);
+  const ThrOut to{thr, out_count, cap, out_read, out_win, out_score};
+  const cudaError_t e = launch_scan_tc_threshold(ix, pl.a, to, c->num_sms, stream);
   if (e != cudaSuccess) return fail(ROPE_ERR_CUDA, "threshold scan launch: %s", cudaGetErrorString(e));
   return ROPE_OK;
 }

@@ -42,14 +42,6 @@ struct ScanArgs {
   uint64_t wait_limit_ns;    // bound of every in-kernel wait
   int32_t tc_variant;        // tile variant of the tensor-core scan (< scan_tc_variants(D))
   int32_t fp8;               // tensor-core scan with E4M3 operands instead of BF16
-  // threshold mode (tensor-core scan): every pair with score >= thr[j] is
-  // appended at index atomicAdd(thr_count, 1) when that index is < thr_cap
-  const float* thr;          // [W] per-window thresholds
-  unsigned long long* thr_count;
-  int64_t thr_cap;
-  int64_t* thr_read;
-  int64_t* thr_win;          // window number j
-  float* thr_score;
 };
 
 struct MergeArgs {
@@ -116,8 +108,19 @@ int scan_tc_variants(int D);
 int scan_tc_lists_per_range(int D, int variant);
 uint64_t wait_limit_ns();
 cudaError_t launch_scan_tc(const DevIndex& ix, const ScanArgs& a, bool dense, int num_sms, cudaStream_t st);
+// Output of the tensor-core scan's threshold mode: every pair with score >=
+// thr[j] is appended at index atomicAdd(count, 1) when that index is < cap.
+struct ThrOut {
+  const float* thr;  // [W] per-window thresholds
+  unsigned long long* count;
+  int64_t cap;
+  int64_t* read;
+  int64_t* win;      // window number j
+  float* score;
+};
 // threshold mode of the tensor-core scan (BF16, tile variant 0 at d = 64, or d = 128)
-cudaError_t launch_scan_tc_threshold(const DevIndex& ix, const ScanArgs& a, int num_sms, cudaStream_t st);
+cudaError_t launch_scan_tc_threshold(const DevIndex& ix, const ScanArgs& a, const ThrOut& out, int num_sms,
+                                     cudaStream_t st);
 // whether the tensor-core scan's shared memory holds candidate lists of this depth
 int scan_tc_fits(const DevIndex& ix, int cand_depth, int variant, int fp8);
 

@@ -116,6 +116,7 @@ struct TcLaunch {
   int32_t st_slot_bytes;   // bytes of one super-tile data slot
   int32_t bins_bytes;      // bytes of the bin arrays (per chain at stride 1, per location otherwise)
   int32_t inv_bytes;       // bytes of the chain-interleaved window norms
+  ThrOut thr;              // threshold mode's output (unused otherwise)
 };
 
 __device__ __forceinline__ float fmax3(float a, float b, float c) {
@@ -134,8 +135,8 @@ __device__ __forceinline__ uint32_t bin_staged(const uint32_t* words, int64_t wo
 }
 
 // kDense: every score written to a.dense. kThr: every score at or above its
-// window's threshold a.thr[j] appended to the a.thr_* pair arrays. Otherwise:
-// per-read candidate lists (top-k).
+// window's threshold L.thr.thr[j] appended to the L.thr pair arrays.
+// Otherwise: per-read candidate lists (top-k).
 template <class Sh, bool kDense, bool kThr = false>
 __global__ void __launch_bounds__(Sh::NTHREADS, 1) scan_tc_kernel(DevIndex ix, ScanArgs a, TcLaunch L) {
   constexpr bool kLists = !kDense && !kThr;
@@ -305,7 +306,7 @@ __global__ void __launch_bounds__(Sh::NTHREADS, 1) scan_tc_kernel(DevIndex ix, S
 #pragma unroll
             for (int u = 0; u < TPL; ++u) {
               const uint32_t jl = jbase + (uint32_t)((h * Sh::WPH + 32 * u + lane) * A);
-              thr_lane[u] = (jl >= jlo && jl < jhi) ? __ldg(a.thr + jl) : INFINITY;
+              thr_lane[u] = (jl >= jlo && jl < jhi) ? __ldg(L.thr.thr + jl) : INFINITY;
               float mn = thr_lane[u];
 #pragma unroll
               for (int o = 8; o > 0; o >>= 1) mn = fminf(mn, __shfl_xor_sync(0xffffffffu, mn, o));
@@ -344,11 +345,11 @@ __global__ void __launch_bounds__(Sh::NTHREADS, 1) scan_tc_kernel(DevIndex ix, S
                   const float th = __shfl_sync(0xffffffffu, thr_lane[rel >> 5], (rel & 31) + n);
                   const float v = sc[n] * Sh::SCORE_SCALE;
                   if (have_read && v >= th) {
-                    const unsigned long long slot = atomicAdd(a.thr_count, 1ull);
-                    if (slot < (unsigned long long)a.thr_cap) {
-                      a.thr_read[slot] = r;
-                      a.thr_win[slot] = (int64_t)(jc + (uint32_t)(n * A));
-                      a.thr_score[slot] = v;
+                    const unsigned long long slot = atomicAdd(L.thr.count, 1ull);
+                    if (slot < (unsigned long long)L.thr.cap) {
+                      L.thr.read[slot] = r;
+                      L.thr.win[slot] = (int64_t)(jc + (uint32_t)(n * A));
+                      L.thr.score[slot] = v;
                     }
                   }
                 }
@@ -752,7 +753,8 @@ int scan_tc_fits(const DevIndex& ix, int cand_depth, int variant, int fp8) {
 }
 
 template <class Sh, bool kDense, bool kThr = false>
-static cudaError_t launch_tc(const DevIndex& ix, const ScanArgs& a, int num_sms, cudaStream_t st) {
+static cudaError_t launch_tc(const DevIndex& ix, const ScanArgs& a, int num_sms, cudaStream_t st,
+                             const ThrOut* thr = nullptr) {
   // the deepest B ring that fits (long windows at large strides and deep
   // candidate lists leave room for fewer slots)
   TcLaunch L;
@@ -762,6 +764,7 @@ static cudaError_t launch_tc(const DevIndex& ix, const ScanArgs& a, int num_sms,
   size_t smem = tc_smem_bytes<Sh>(ix, a.cand_depth, kNoLists, nb, &L);
   while (smem > limit && nb > 1) smem = tc_smem_bytes<Sh>(ix, a.cand_depth, kNoLists, nb >>= 1, &L);
   if (smem > limit) return cudaErrorInvalidValue;
+  L.thr = thr ? *thr : ThrOut{};
   auto kern = scan_tc_kernel<Sh, kDense, kThr>;
   cudaError_t e = tc_reserve_smem<Sh, kDense, kThr>(smem);
   if (e != cudaSuccess) {
@@ -797,10 +800,11 @@ cudaError_t launch_scan_tc(const DevIndex& ix, const ScanArgs& a, bool dense, in
   return cudaErrorInvalidValue;
 }
 
-cudaError_t launch_scan_tc_threshold(const DevIndex& ix, const ScanArgs& a, int num_sms, cudaStream_t st) {
+cudaError_t launch_scan_tc_threshold(const DevIndex& ix, const ScanArgs& a, const ThrOut& out, int num_sms,
+                                     cudaStream_t st) {
   if (ix.stride > scan_tc_max_stride() || a.fp8) return cudaErrorInvalidValue;
-  if (ix.D == 32) return launch_tc<TcShape32, false, true>(ix, a, num_sms, st);
-  if (ix.D == 64) return launch_tc<TcShape64, false, true>(ix, a, num_sms, st);
+  if (ix.D == 32) return launch_tc<TcShape32, false, true>(ix, a, num_sms, st, &out);
+  if (ix.D == 64) return launch_tc<TcShape64, false, true>(ix, a, num_sms, st, &out);
   return cudaErrorInvalidValue;
 }
 
