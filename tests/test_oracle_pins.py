@@ -663,3 +663,20 @@ def test_threshold_pairs_against_topk():
         want = set(ow[i][os_[i] >= t].tolist())
         assert len(want) < 200  # the top-200 list reaches below t
         assert set(w[r == i].tolist()) == want
+
+
+def test_refine_scores_follow_the_ip_recurrence():
+    """The fidelities the refinement oracle scores along a candidate's range
+    equal |ip|^2 / (X C) with ip from the paper's one-letter slide relation
+    (§3.4) and C from the direct window encodings."""
+    ref = synth.uniform_ref(4000, 161)
+    rd = synth.reads(ref, 1, seed=162)
+    p = oracle.Params(s=4, m=2, t=2, variant=1, N=150)
+    c0 = int(rd.true_pos[0])
+    _, _, (owner, pos, fid) = oracle.refine(ref, rd.seqs, rd.offsets, np.array([[c0]]), 12, p)
+    x = oracle.embed(rd.seqs[:150], p)
+    lo = int(pos[0])
+    ip = oracle.ip_recurrence(ref, p, x, lo, len(pos))
+    C = np.sum(np.abs(oracle.windows_direct(ref, p, lo, len(pos))) ** 2, axis=1)
+    X = np.sum(np.abs(x) ** 2)
+    assert np.allclose(fid, np.abs(ip) ** 2 / (X * C), rtol=1e-10, atol=1e-14)
