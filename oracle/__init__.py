@@ -492,3 +492,47 @@ def threshold_pairs(ref, seqs, offsets, p: Params, thr: np.ndarray, j_begin: int
     if got < 0 or got > cap:
         raise ValueError("oracle_threshold_pairs failed or exceeded cap")
     return r[:got], w[:got], f[:got]
+
+
+# ------------------------------------------------------------ fitting curve (§2.4 scoring of correlations)
+
+def pair_fidelities(dnas, errs, p: Params, seed: int, N: int | None = None) -> np.ndarray:
+    """§2.4: for each random string dnas[i] (at least N + slack letters), the
+    fidelity between the encoding of its first N letters and that of its
+    mutated copy at rate errs[i] (``mutate``, stream i)."""
+    N = p.N if N is None else N
+    out = np.empty(len(dnas))
+    for i, (d, e) in enumerate(zip(dnas, errs)):
+        d = _u8(d)
+        mut, _ = mutate(d, 0, N, float(e), seed, i)
+        x, y = embed(d, p, N), embed(mut, p, N)
+        out[i] = fidelity(x, y) if p.score_mode == 0 else fidelity_per_band(x, y, p.m)
+    return out
+
+
+def fitting_curve(errs, fids, n_bins: int = 20, lo: float = 0.0, hi: float = 0.5):
+    """§2.4 step 2: the expected fidelity at evenly spaced mutation rates (the
+    mean fidelity of the samples in each of n_bins equal bins of (lo, hi)),
+    connected piecewise linearly. Returns (bin centres, mean fidelities)."""
+    errs, fids = np.asarray(errs, dtype=np.float64), np.asarray(fids, dtype=np.float64)
+    edges = np.linspace(lo, hi, n_bins + 1)
+    centres = (edges[:-1] + edges[1:]) / 2
+    means = np.array([fids[(errs >= a) & (errs < b)].mean() for a, b in zip(edges[:-1], edges[1:])])
+    return centres, means
+
+
+def predict_err(fids, curve) -> np.ndarray:
+    """The mutation rate read off the fitting curve at each observed fidelity
+    (the curve is decreasing in the rate, so it is inverted by interpolation)."""
+    centres, means = curve
+    order = np.argsort(means)
+    return np.interp(np.asarray(fids, dtype=np.float64), means[order], centres[order])
+
+
+def prediction_rmse(errs, fids, curve, below: float = 1.0) -> float:
+    """§2.4 step 3: root mean square of (predicted - true) mutation rate over
+    the samples whose true rate is below ``below``."""
+    errs = np.asarray(errs, dtype=np.float64)
+    sel = errs < below
+    d = predict_err(np.asarray(fids)[sel], curve) - errs[sel]
+    return float(np.sqrt(np.mean(d * d)))

@@ -680,3 +680,31 @@ def test_refine_scores_follow_the_ip_recurrence():
     C = np.sum(np.abs(oracle.windows_direct(ref, p, lo, len(pos))) ** 2, axis=1)
     X = np.sum(np.abs(x) ** 2)
     assert np.allclose(fid, np.abs(ip) ** 2 / (X * C), rtol=1e-10, atol=1e-14)
+
+
+# ---------------------------------------------------------------- fitting curve (§2.4 scoring of correlations)
+
+def test_fitting_curve_rate_zero_and_monotone():
+    p = oracle.Params(s=4, m=2, t=2, variant=1, N=1000)
+    dnas = [synth.uniform_ref(1400, 200 + i) for i in range(160)]
+    assert np.allclose(oracle.pair_fidelities(dnas[:10], np.zeros(10), p, 3), 1.0, atol=1e-12)
+    errs = np.random.default_rng(4).uniform(0, 0.5, 160)
+    fids = oracle.pair_fidelities(dnas, errs, p, 3)
+    c, m = oracle.fitting_curve(errs, fids, n_bins=8)
+    assert np.all(np.diff(m) < 0) and m[0] < 1.0 and m[-1] > 0.0
+
+
+def test_fitting_curve_rmse_as_printed():
+    """The paper's random-pair experiment (20,000-letter random strings,
+    4096 complex dimensions, mutation rates uniform in (0, 0.5) split evenly
+    between deletions, insertions and substitutions) predicts the rate from
+    the fidelity with an RMSE under 1% where the rate is below 25%; here with
+    s = t = 6, m = 1 (4^6 = 4096 bins)."""
+    N = 20_000
+    p = oracle.Params(s=6, m=1, t=6, variant=0, N=N)
+    n = 400
+    dnas = [synth.uniform_ref(N + 4000, 300 + i) for i in range(n)]
+    errs = np.random.default_rng(5).uniform(0, 0.5, n)
+    fids = oracle.pair_fidelities(dnas, errs, p, 6)
+    curve = oracle.fitting_curve(errs, fids, n_bins=10)
+    assert oracle.prediction_rmse(errs, fids, curve, below=0.25) < 0.01
