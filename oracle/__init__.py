@@ -7,7 +7,11 @@ the other. Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline
 leg of ``bench.py`` may import it.
 
 Parity status: every function here is pinned by ``tests/test_oracle_pins.py``
-against closed forms, invariants, values the paper prints, or brute force,
+against closed forms, invariants, values the paper prints, or brute force —
+including the refinement (exact reads found, range clipping, ties, the §3.4
+one-letter relation), the threshold regime (published SplitMix64 outputs,
+mutation rate and split, the edit bound, identity at rate 0, agreement with
+the exhaustive top-k) and the fitting curve (the paper's printed RMSE) —
 except the reranker network (``mlp``), which is pinned by finite differences
 only; it is marked there.
 """
