@@ -87,6 +87,22 @@ WORKLOADS = {
         L=2_300_000_000, gc=0.47, tandem=0.0, segdup=0.0, inter=0.85, ref_seed=8,
         n_reads=100_000, read_len=150, sub=0.01, indel=0.005, read_seed=9,
         s=4, m=2, t=2, variant=1, N=150, stride=1, k=8),
+    "human3G_20k": dict(
+        desc="3.1 Gbp human-shaped order-2 Markov genome (GC 41%, 50% interspersed repeats), 96k planted 20 kbp reads "
+             "at 15% errors (5% substitutions, 10% indel events of geometric length p=0.7), every other read "
+             "reverse-complemented, mapped on both strands; fine-tuned compact RoPE s=8 m=4 t=4 (1024 complex "
+             "dimensions, d=2048), window N=20000, step 1250 (the paper's long-read configuration), materialised "
+             "index scored by the BF16 tcgen05 GEMM, FP32 re-scoring, top-8",
+        L=3_100_000_000, gc=0.41, tandem=0.0, segdup=0.0, inter=0.50, ref_seed=7,
+        n_reads=96_000, read_len=20000, sub=0.05, indel=0.10, read_seed=10,
+        s=8, m=4, t=4, variant=1, N=20000, stride=1250, k=8, strands=True, batch=24_000),
+    "markov300M_20k": dict(
+        desc="300 Mbp order-2 Markov reference (GC 41%, 2.5% tandem repeats, 2.5% segmental duplicates), 8192 planted "
+             "20 kbp reads at 15% errors, both strands, s=8 m=4 t=4 (d=2048), N=20000, step 1250, top-8 (a one-batch "
+             "case of the long-read configuration small enough for ncu captures)",
+        L=300_000_000, gc=0.41, tandem=0.025, segdup=0.025, inter=0.0, ref_seed=3,
+        n_reads=8192, read_len=20000, sub=0.05, indel=0.10, read_seed=11,
+        s=8, m=4, t=4, variant=1, N=20000, stride=1250, k=8, strands=True, batch=8192),
     "uniform100k": dict(
         desc="100 kbp uniform reference, 256 x 150 bp planted reads (1% sub, 0.5% indel), d=64, stride 1, top-8",
         L=100_000, gc=None, ref_seed=1, n_reads=256, read_len=150, sub=0.01, indel=0.005, read_seed=2,
@@ -101,7 +117,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="markov100M", choices=sorted(WORKLOADS))
-    ap.add_argument("--batch", type=int, default=131072)
+    ap.add_argument("--batch", type=int, default=0, help="reads per step (0: the workload's default)")
     ap.add_argument("--fp32-reads", type=int, default=4096)
     ap.add_argument("--fp8-steps", type=int, default=2)
     ap.add_argument("--refine-radius", type=int, default=8)
@@ -126,7 +142,25 @@ def make_inputs(wl, rank):
     rd = synth.reads(ref, wl["n_reads"], seed=wl["read_seed"] + 1000 * rank, length=wl["read_len"],
                      sub_rate=wl["sub"], indel_rate=wl["indel"], lognormal_sigma=wl.get("sigma"),
                      len_min=wl.get("len_min", 100), len_max=wl.get("len_max", 10000))
+    if wl.get("strands"):
+        rd = reverse_every_other(rd)
     return ref, rd
+
+
+_COMPLEMENT = np.zeros(256, dtype=np.uint8)
+for _a, _b in zip(b"ACGTacgt", b"TGCAtgca"):
+    _COMPLEMENT[_a] = _b
+
+
+def reverse_every_other(rd):
+    """Reads of both strands: every odd read is replaced by its reverse
+    complement (the locus it came from is unchanged; its strand is 1)."""
+    seqs = rd.seqs.copy()
+    for i in range(1, rd.n, 2):
+        a, b = rd.offsets[i], rd.offsets[i + 1]
+        seqs[a:b] = _COMPLEMENT[rd.seqs[a:b][::-1]]
+    rd.seqs = seqs
+    return rd
 
 
 def measured_peaks():
@@ -137,12 +171,21 @@ def measured_peaks():
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
 
 
-def traffic_record():
+TRAFFIC_RECORDS = {  # workload -> (ncu traffic record, kernel source it was taken on, batch it is scaled to)
+    "markov100M": ("scan_tc_traffic.json", "rope_scan_tc.cu", 131072),
+    "human3G_20k": ("gemm_tc_traffic.json", "rope_dense.cu", 24000),
+}
+
+
+def traffic_record(workload, batch):
     """DRAM bytes per scan launch from the committed ncu summary, if it was
-    taken on the current kernel source (else None)."""
-    path = os.path.join(ROOT, "profiles", "scan_tc_traffic.json")
-    src = os.path.join(ROOT, "paper_2603_22245_gb300", "csrc", "rope_scan_tc.cu")
-    if not os.path.exists(path):
+    taken on the current kernel source and scaled to this launch (else None)."""
+    if workload not in TRAFFIC_RECORDS:
+        return None
+    name, kernel, b = TRAFFIC_RECORDS[workload]
+    path = os.path.join(ROOT, "profiles", name)
+    src = os.path.join(ROOT, "paper_2603_22245_gb300", "csrc", kernel)
+    if batch != b or not os.path.exists(path):
         return None
     rec = json.load(open(path))
     h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
@@ -337,7 +380,8 @@ def run_reference(args, wl):
     op = oracle.Params(s=wl["s"], m=wl["m"], t=wl["t"], variant=wl["variant"], N=wl["N"], stride=wl["stride"])
     W = oracle.n_windows(len(ref), wl["N"], wl["stride"])
     nw = min(W, 200_000)
-    per_step = 8
+    # the oracle's OpenMP loop runs over reads: one read per host core per step
+    per_step = max(8, oracle.max_threads())
     times = []
     for i in range(args.warmup + args.steps):
         sub = rd.subset(np.arange(i * per_step, (i + 1) * per_step) % rd.n)
@@ -484,28 +528,45 @@ def main():
     W = idx.n_windows
     seqs = torch.from_numpy(rd.seqs).cuda()
     offs = torch.from_numpy(rd.offsets).cuda()
-    B = min(args.batch, rd.n)
+    B = min(args.batch if args.batch > 0 else wl.get("batch", 131072), rd.n)
     n_batches = max(1, rd.n // B)
     k = wl["k"]
+    strands = bool(wl.get("strands"))
+    dense_index = p.dim > 128  # materialised index: the BF16 GEMM scan only
+    rows = 2 if strands else 1  # query rows per read (both strands)
+
+    def new_out():
+        o = (torch.empty((B, k), dtype=torch.int64, device="cuda"), torch.empty((B, k), dtype=torch.float32,
+                                                                               device="cuda"))
+        return o + (torch.empty((B, k), dtype=torch.int8, device="cuda"),) if strands else o
 
     # read batches as views: seqs is shared, offsets are absolute into it
-    outs = (torch.empty((B, k), dtype=torch.int64, device="cuda"), torch.empty((B, k), dtype=torch.float32,
-                                                                              device="cuda"))
+    outs = new_out()
     true_pos = rd.true_pos
+    true_strand = (np.arange(rd.n) % 2) if strands else np.zeros(rd.n, dtype=np.int64)
 
     def step(bi, precision="bf16", o=None):
         b = bi % n_batches
-        return rm.rope_map(idx, seqs, offs[b * B:(b + 1) * B + 1], k=k, precision=precision, out=o or outs)
+        ob = offs[b * B:(b + 1) * B + 1]
+        if strands:
+            return rm.rope_map_strands(idx, seqs, ob, k=k, precision=precision, out=o or outs)
+        return rm.rope_map(idx, seqs, ob, k=k, precision=precision, out=o or outs)
 
-    if args.scan_variant >= 0:
+    def hits_of(res, b):
+        top = res[0][:, 0].cpu().numpy()
+        h = np.abs(top - true_pos[b * B:(b + 1) * B]) < wl["N"]
+        if strands:
+            h &= res[2][:, 0].cpu().numpy() == true_strand[b * B:(b + 1) * B]
+        return h
+
+    if args.scan_variant >= 0 and not dense_index:
         rm.rope_autotune_set(idx, B, args.scan_variant, 16, k=k)
     for i in range(args.warmup):
         step(i)
     rm.rope_sync_status()
-    tuned = rm.rope_autotune_query(idx, B, k=k)  # chosen during the first warm-up step
+    tuned = None if dense_index else rm.rope_autotune_query(idx, B, k=k)  # chosen during the first warm-up step
     rm.rope_profile_enable(args.steps)
-    step_outs = [(torch.empty((B, k), dtype=torch.int64, device="cuda"),
-                  torch.empty((B, k), dtype=torch.float32, device="cuda")) for _ in range(args.steps)]
+    step_outs = [new_out() for _ in range(args.steps)]
     hits = []
     if dist:
         dist.barrier()
@@ -514,10 +575,8 @@ def main():
     clk.start()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     ev0.record()
-    tops = []
     for i in range(args.steps):
-        w, _ = step(i, o=step_outs[i])
-        tops.append(w[:, 0])
+        step(i, o=step_outs[i])
     ev1.record()
     torch.cuda.synchronize()
     clocks = clk.stop()
@@ -531,11 +590,10 @@ def main():
     top2_step0 = step_outs[0][0][:, :2].clone()  # the refinement leg's candidates (batch 0)
     stage_ms = rm.rope_profile_read(args.steps)
     rm.rope_profile_enable(0)
-    for i, top in enumerate(tops):
-        b = i % n_batches
-        hits.append(np.abs(top.cpu().numpy() - true_pos[b * B:(b + 1) * B]) < wl["N"])
+    for i in range(args.steps):
+        hits.append(hits_of(step_outs[i], i % n_batches))
     acc_bf16 = float(np.concatenate(hits).mean())
-    scores_step = B * W
+    scores_step = rows * B * W
     value = ws * args.steps * scores_step / elapsed
     reads_s = ws * args.steps * B / elapsed
 
@@ -545,57 +603,58 @@ def main():
     peaks, peak_src = measured_peaks()
     peak = peaks["bf16_tflops_sustained"]
     achieved = flops / scan_s / 1e12
-    trec = traffic_record() if (args.workload == "markov100M" and B == 131072) else None
+    trec = traffic_record(args.workload, B)
     roofline = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                 "traffic": (trec["dram_bytes_per_launch_scaled"] * 1.0) if trec else None,
-                "kernel": "scan_tc_kernel (BF16 tcgen05)", "peak_source": f"{peak_src} bf16_tflops_sustained",
+                "kernel": "gemm_tc_kernel (BF16 tcgen05 GEMM over the materialised index, A operand build included)"
+                if dense_index else "scan_tc_kernel (BF16 tcgen05)", "peak_source": f"{peak_src} bf16_tflops_sustained",
                 "flops_per_launch": flops, "ms_per_launch": scan_s * 1000.0,
                 "stage_ms": {"encode": float(np.mean(stage_ms[:, 0])), "scan": float(np.mean(stage_ms[:, 1])),
                              "merge_rescore": float(np.mean(stage_ms[:, 2]))}}
 
     # FP32 plain path and BF16 on the same read subset (equal-accuracy check)
-    F = min(args.fp32_reads, B)
-    fo = (torch.empty((F, k), dtype=torch.int64, device="cuda"), torch.empty((F, k), dtype=torch.float32,
-                                                                             device="cuda"))
-    osub = offs[:F + 1]
-    rm.rope_map(idx, seqs, osub, k=k, precision="fp32", out=fo)
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record()
-    n32 = 2
-    for _ in range(n32):
+    fp32 = None
+    F = min(args.fp32_reads, B) if not dense_index else 0
+    if F > 0:
+        fo = (torch.empty((F, k), dtype=torch.int64, device="cuda"), torch.empty((F, k), dtype=torch.float32,
+                                                                                 device="cuda"))
+        osub = offs[:F + 1]
         rm.rope_map(idx, seqs, osub, k=k, precision="fp32", out=fo)
-    e1.record()
-    torch.cuda.synchronize()
-    t32 = e0.elapsed_time(e1) / 1000.0 / n32
-    acc32 = float(np.mean(np.abs(fo[0][:, 0].cpu().numpy() - true_pos[:F]) < wl["N"]))
-    bo = rm.rope_map(idx, seqs, osub, k=k, precision="bf16")
-    acc16_sub = float(np.mean(np.abs(bo[0][:, 0].cpu().numpy() - true_pos[:F]) < wl["N"]))
-    agree = float(torch.mean((bo[0][:, 0] == fo[0][:, 0]).float()).item())
-    rm.rope_sync_status()
-    fp32 = {"value": F * W / t32, "unit": UNIT, "reads_per_s": F / t32, "reads": F, "top1_acc": acc32,
-            "bf16_top1_acc_same_reads": acc16_sub, "top1_window_agreement": agree}
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        n32 = 2
+        for _ in range(n32):
+            rm.rope_map(idx, seqs, osub, k=k, precision="fp32", out=fo)
+        e1.record()
+        torch.cuda.synchronize()
+        t32 = e0.elapsed_time(e1) / 1000.0 / n32
+        acc32 = float(np.mean(np.abs(fo[0][:, 0].cpu().numpy() - true_pos[:F]) < wl["N"]))
+        bo = rm.rope_map(idx, seqs, osub, k=k, precision="bf16")
+        acc16_sub = float(np.mean(np.abs(bo[0][:, 0].cpu().numpy() - true_pos[:F]) < wl["N"]))
+        agree = float(torch.mean((bo[0][:, 0] == fo[0][:, 0]).float()).item())
+        rm.rope_sync_status()
+        fp32 = {"value": F * W / t32, "unit": UNIT, "reads_per_s": F / t32, "reads": F, "top1_acc": acc32,
+                "bf16_top1_acc_same_reads": acc16_sub, "top1_window_agreement": agree}
 
     # E4M3 option: the same steps with the FP8 tensor-core scan (same batches,
     # same rescoring), its top-1 accuracy on the same planted reads
     fp8 = None
-    if args.fp8_steps > 0:
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if args.fp8_steps > 0 and not dense_index:
         step(0, precision="fp8")
         rm.rope_sync_status()
         rm.rope_profile_enable(args.fp8_steps)
         e0.record()
-        tops8 = []
         for i in range(args.fp8_steps):
-            w8, _ = step(i, precision="fp8", o=step_outs[i])
-            tops8.append(w8[:, 0])
+            step(i, precision="fp8", o=step_outs[i])
         e1.record()
         torch.cuda.synchronize()
         t8 = e0.elapsed_time(e1) / 1000.0
         st8 = rm.rope_profile_read(args.fp8_steps)
         rm.rope_profile_enable(0)
         rm.rope_sync_status()
-        h8 = [np.abs(t.cpu().numpy() - true_pos[(i % n_batches) * B:(i % n_batches + 1) * B]) < wl["N"]
-              for i, t in enumerate(tops8)]
+        h8 = [hits_of(step_outs[i], i % n_batches) for i in range(args.fp8_steps)]
         h16 = np.concatenate(hits[:args.fp8_steps])
         scan8 = float(np.mean(st8[:, 1])) / 1000.0
         peak8 = peak * 2.0  # E4M3 dense rate = 2x BF16 (nominal 4.5 vs 2.25 PFLOP/s)
@@ -611,7 +670,7 @@ def main():
     # fine-tuned: two bands of different frequency, so that a shifted window
     # changes the bands' relative phase)
     refine = None
-    if args.refine_radius > 0:
+    if args.refine_radius > 0 and not dense_index:
         try:
             fine = rm.Params(s=8, m=2, t=8, variant=1, window_len=wl["N"])
             cand = top2_step0
@@ -645,6 +704,7 @@ def main():
         off_pin = torch.from_numpy(np.ascontiguousarray(o_h - o_h[0])).pin_memory()
         w_pin = torch.empty((B, k), dtype=torch.int64).pin_memory()
         s_pin = torch.empty((B, k), dtype=torch.float32).pin_memory()
+        t_pin = torch.empty((B, k), dtype=torch.int8).pin_memory()
         dseq = torch.empty(seq_pin.shape, dtype=torch.uint8, device="cuda")
         doff = torch.empty(off_pin.shape, dtype=torch.int64, device="cuda")
         for it in range(2 + args.e2e_steps):
@@ -653,7 +713,11 @@ def main():
                 t0 = time.perf_counter()
             dseq.copy_(seq_pin, non_blocking=True)
             doff.copy_(off_pin, non_blocking=True)
-            w_, s_ = rm.rope_map(idx, dseq, doff, k=k, precision="bf16", out=outs)
+            if strands:
+                w_, s_, t_ = rm.rope_map_strands(idx, dseq, doff, k=k, precision="bf16", out=outs)
+                t_pin.copy_(t_, non_blocking=True)
+            else:
+                w_, s_ = rm.rope_map(idx, dseq, doff, k=k, precision="bf16", out=outs)
             w_pin.copy_(w_, non_blocking=True)
             s_pin.copy_(s_, non_blocking=True)
             torch.cuda.synchronize()
@@ -664,10 +728,10 @@ def main():
             te = float(t.item())
         e2e = {"value": ws * scores_step / te, "unit": UNIT, "reads_per_s": ws * B / te,
                "h2d_bytes_per_step": int(seq_pin.numel() + off_pin.numel() * 8),
-               "d2h_bytes_per_step": int(w_pin.numel() * 8 + s_pin.numel() * 4)}
+               "d2h_bytes_per_step": int(w_pin.numel() * 8 + s_pin.numel() * 4 + (t_pin.numel() if strands else 0))}
 
     reranker = None
-    if args.rerank_train_reads > 0:
+    if args.rerank_train_reads > 0 and not dense_index:
         reranker = rerank_leg(rm, idx, ref, wl, args)
 
     cpu = None
@@ -686,7 +750,7 @@ def main():
                                                               "tuned_scan_ms": tuned[2]}},
         "reads_per_s": reads_s, "top1_acc": acc_bf16, "fp32_plain": fp32, "fp8_option": fp8, "refine": refine,
         "encode_pass": encode_pass,
-        "speedup_vs_fp32_plain": value / ws / fp32["value"],
+        "speedup_vs_fp32_plain": value / ws / fp32["value"] if fp32 else None,
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "reranker": reranker, "gpu_launches": 3 * args.steps, "clocks": clocks,
     }
     if rank == 0:

@@ -128,6 +128,20 @@ int32_t rope_dim(const rope_params* p);
  * (a read shorter than N) or ROPE_ERR_TIMEOUT. */
 rope_status rope_sync_status(cudaStream_t stream);
 
+/* Bound of every in-kernel wait of later launches on any device, in seconds
+ * (the paper has no counterpart: this is part of failure detection). The
+ * default is 2 s, or the environment's ROPE_WAIT_LIMIT_S (clamped to
+ * [0.05, 120]) for runs that slow kernels down on purpose, such as a profiler
+ * replaying them. `seconds` in [1e-9, 120] sets the bound, 0 restores the
+ * default; else ROPE_ERR_INVALID_ARG. A wait that runs out sets the timeout
+ * bit (ROPE_ERR_TIMEOUT from rope_sync_status); the kernel then waits (at
+ * least 1 s more) for its own copies and tensor-core operations in flight,
+ * frees its tensor memory and returns, so the context stays usable. Bounds of
+ * nanoseconds make every wait that is not satisfied at once run out: the
+ * tests of this path use them. Launches captured in a CUDA graph keep the
+ * bound in force when they were captured. */
+rope_status rope_set_wait_limit(double seconds);
+
 /* ---- step a1: 2-bit packing (§2.1 alphabet) ------------------------------
  * seq: len letters (uint8). out_words: ceil(len/16) uint32; base i goes to
  * bits 2*(i mod 16) of word i/16, unused high bits of the last word are 0.
@@ -145,11 +159,31 @@ rope_status rope_mer_bins(const rope_params* p, const uint32_t* packed, int64_t 
  * j < W = floor((len-N)/stride)+1 computes its squared norm exactly enough
  * (FP64 recurrence from FP64 anchors) to store 1/sqrt(C_j) in FP32 (0 for a
  * zero vector, whose fidelity is 0), per-band norms when score_mode = 1, and
- * the FP32 anchors c(j) every 64 windows that seed the on-chip recurrence.
- * Requires 1 <= W < 2^32. Synchronous: returns after the index is built.
- * *out receives a new index owned by the caller (free with rope_index_free). */
+ * the FP32 anchors c(j) every 64 windows that seed the on-chip recurrence
+ * (the on-the-fly index: stride <= 64, complex dimension m*4^t <= 128; the
+ * scans regenerate every window on chip). Encodings wider than 128 complex
+ * dimensions get the materialised index of rope_encode_reference_dense
+ * instead. Requires 1 <= W < 2^32. Synchronous: returns after the index is
+ * built. *out receives a new index owned by the caller (free with
+ * rope_index_free). */
 rope_status rope_encode_reference(const rope_params* p, const uint8_t* ref, int64_t len, rope_index** out,
                                   cudaStream_t stream);
+
+/* Materialised index (§3.1's "database of vectors", sized in §3.2 for 20 kbp
+ * reads: window 20,000, step 1,250, 1024 complex dimensions). Stores every
+ * window's encoding twice on the device -- FP32 [W, 2D] unnormalised
+ * (re block, im block; for re-scoring) and BF16 [W, 2D] divided by its norm
+ * (the tensor-core operand) -- plus 1/|c_j| in FP32: W * 2D * 6 bytes (30 GB
+ * for a 3.1 Gbp genome at those settings), and 8 * D bytes per window of
+ * scratch during the build. Each window is summed exactly from per-block sums
+ * over blocks of `stride` s-mer starts (no recurrence, no drift; FP32).
+ * Any stride (1..65536); D = m*4^t a multiple of 32, at most 4096; score_mode
+ * 0; W < 2^31. rope_score_topk / rope_map / rope_map_strands / rope_score_dense
+ * on it run the BF16 tensor-core GEMM (precision ROPE_PREC_BF16 only) with
+ * the top-k fused into its epilogue, and re-score in FP32 from the stored
+ * rows; the other scans refuse it (ROPE_ERR_UNSUPPORTED). Synchronous. */
+rope_status rope_encode_reference_dense(const rope_params* p, const uint8_t* ref, int64_t len, rope_index** out,
+                                        cudaStream_t stream);
 
 /* Frees an index (NULL is allowed). Synchronises the device first. */
 void rope_index_free(rope_index* idx);
@@ -192,22 +226,34 @@ rope_status rope_score_topk(const rope_index* idx, const float* emb_f32, const u
  * gives nearly all device memory to its own arena at start-up, or a
  * latency-critical loop that cannot take the device-wide synchronisation of
  * cudaMalloc/cudaFree. Same arguments, results and kernels as
- * rope_score_topk; the caller still passes the inputs and outputs. The
- * scratch (status word + candidate lists) is a 16 MiB array inside the
+ * rope_score_topk (the split of the windows into ranges may differ, which
+ * does not change the result: the union of per-range top lists always holds
+ * the overall top list); the caller still passes the inputs and outputs. The
+ * scratch (status words + candidate lists) is a 16 MiB array inside the
  * library that every GPU which loads the library holds until exit; a call
  * needing more (n_reads * n_ranges * cand_depth * 8 bytes beyond 16 MiB - 256 B)
  * is rejected with ROPE_ERR_INVALID_ARG and a message giving the limit
  * (n_ranges = 0 picks the largest split that fits). No cudaMalloc, cudaFree
- * or pool allocation happens. The first call on a device looks up the array's
- * device address (cudaGetSymbolAddress), so make that first call before any
- * stream capture on that device. All calls on a device share the one array:
- * calls that overlap on the GPU (e.g. on two streams at once) race and
- * corrupt each other's results; serialise them. A bounded in-kernel wait that
- * runs out here is recorded only in the array's own status word (not the one
- * rope_sync_status reads) and shows up as (-1, -inf) entries. */
+ * or pool allocation happens; every call sets its candidate lists empty
+ * (cudaMemsetAsync, at most 16 MiB) before the scan. The first call on a
+ * device looks up the array's device address (cudaGetSymbolAddress), so make
+ * that first call before any stream capture on that device. All calls on a
+ * device share the one array: calls that overlap on the GPU (e.g. on two
+ * streams at once) race and corrupt each other's results; serialise them. A
+ * bounded in-kernel wait that runs out during a call makes that call's
+ * output (-1, -inf) for every read, and is recorded in the array's own status
+ * word, which rope_noalloc_sync_status reads (not rope_sync_status). */
 rope_status rope_score_topk_noalloc(const rope_index* idx, const float* emb_f32, const uint16_t* emb_bf16,
                                     const float* norms, int64_t n_reads, const rope_score_opts* opts,
                                     int64_t* out_win, float* out_score, cudaStream_t stream);
+
+/* Status of the allocation-free calls on the current device: synchronises
+ * `stream`, then returns and clears the bits every rope_score_topk_noalloc
+ * call since the last read has recorded -- ROPE_OK, ROPE_ERR_TIMEOUT (a
+ * bounded wait ran out; that call's output is (-1, -inf)) or
+ * ROPE_ERR_INVALID_ARG (the merge found a corrupt candidate slot and skipped
+ * it). Allocates nothing; no counterpart in the paper. */
+rope_status rope_noalloc_sync_status(cudaStream_t stream);
 
 /* ---- tuner (no counterpart in the paper) --------------------------------
  * The BF16 scan has tile variants and a free split of the work into

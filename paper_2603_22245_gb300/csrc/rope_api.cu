@@ -8,6 +8,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <algorithm>
+#include <atomic>
 #include <tuple>
 #include <cstdlib>
 #include <cstring>
@@ -64,8 +65,9 @@ extern "C" const char* rope_last_error(void) { return g_last_error; }
 
 // Bound of every in-kernel wait: 2 s, or ROPE_WAIT_LIMIT_S seconds (clamped to
 // [0.05, 120]) for runs that slow kernels down on purpose, such as profilers
-// replaying a kernel under instrumentation.
-uint64_t rope::wait_limit_ns() {
+// replaying a kernel under instrumentation; rope_set_wait_limit overrides it
+// for later launches (tests of the timeout path use a limit of nanoseconds).
+static uint64_t default_wait_limit_ns() {
   static const uint64_t v = [] {
     const char* e = getenv("ROPE_WAIT_LIMIT_S");
     double s = e ? atof(e) : 2.0;
@@ -74,6 +76,24 @@ uint64_t rope::wait_limit_ns() {
     return (uint64_t)(s * 1e9);
   }();
   return v;
+}
+
+static std::atomic<uint64_t> g_wait_limit_override{0};
+
+uint64_t rope::wait_limit_ns() {
+  const uint64_t o = g_wait_limit_override.load(std::memory_order_relaxed);
+  return o ? o : default_wait_limit_ns();
+}
+
+extern "C" rope_status rope_set_wait_limit(double seconds) {
+  if (seconds == 0.0) {
+    g_wait_limit_override.store(0, std::memory_order_relaxed);
+    return ROPE_OK;
+  }
+  if (!(seconds >= 1e-9 && seconds <= 120.0))
+    return fail(ROPE_ERR_INVALID_ARG, "wait limit %g s outside [1e-9, 120] (0 restores the default)", seconds);
+  g_wait_limit_override.store((uint64_t)(seconds * 1e9 + 0.5), std::memory_order_relaxed);
+  return ROPE_OK;
 }
 
 // ---------------------------------------------------------------- per-device context
@@ -138,7 +158,7 @@ rope_status check_params(const rope_params* p) {
   if (p->score_mode != 0 && p->score_mode != 1) return fail(ROPE_ERR_INVALID_ARG, "score_mode=%d", p->score_mode);
   if (p->window_len < p->s || p->window_len > 65536)
     return fail(ROPE_ERR_INVALID_ARG, "window_len=%d outside [s,65536]", p->window_len);
-  if (p->stride < 1 || p->stride > 64) return fail(ROPE_ERR_INVALID_ARG, "stride=%d outside [1,64]", p->stride);
+  if (p->stride < 1 || p->stride > 65536) return fail(ROPE_ERR_INVALID_ARG, "stride=%d outside [1,65536]", p->stride);
   if (p->bin_of_mer_host) {
     const int nb = 1 << (2 * p->t);
     for (int i = 0; i < (1 << (2 * p->s)); ++i)
@@ -423,6 +443,165 @@ extern "C" void rope_index_free(rope_index* idx) {
   delete idx;
 }
 
+// ---------------------------------------------------------------- materialised index
+
+namespace {
+
+using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+// TMA descriptor of a row-major BF16 matrix [rows, cols] read in boxes of
+// 128 rows x 64 columns (128 bytes, the 128-byte swizzle of the MMA operands);
+// rows past the end read as zero.
+rope_status tensor_map_rows(CUtensorMap* m, const void* base, int64_t rows, int cols) {
+  static EncodeTiledFn fn = [] {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q{};
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess) {
+      cudaGetLastError();
+      f = nullptr;
+    }
+    return reinterpret_cast<EncodeTiledFn>(f);
+  }();
+  if (!fn) return fail(ROPE_ERR_CUDA, "cuTensorMapEncodeTiled is not available from the driver");
+  if (rows < 1 || rows > 0x7FFFFFFF || cols % 64 != 0) return fail(ROPE_ERR_INVALID_ARG, "tensor map of %lld x %d", (long long)rows, cols);
+  const cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  const cuuint64_t strides[1] = {(cuuint64_t)cols * 2};
+  const cuuint32_t box[2] = {64, 128};
+  const cuuint32_t es[2] = {1, 1};
+  const CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, es,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return fail(ROPE_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+  return ROPE_OK;
+}
+
+}  // namespace
+
+// The paper's index (§3.1): every window's encoding stored, FP32 and
+// normalised BF16, built from per-block sums (see rope_dense.cu).
+rope_status rope::encode_reference_dense_impl(const rope_params* p, const uint8_t* ref, int64_t len,
+                                              rope_index** out, cudaStream_t stream) {
+  rope_status st = check_params(p);
+  if (st != ROPE_OK) return st;
+  if (!out) return fail(ROPE_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (!ref || len < p->window_len) return fail(ROPE_ERR_INVALID_ARG, "reference shorter than the window");
+  const int D = p->m << (2 * p->t);
+  if (D % 32 != 0 || D > 4096)
+    return fail(ROPE_ERR_UNSUPPORTED, "materialised index: complex dimension %d is not a multiple of 32 up to 4096", D);
+  if (p->score_mode != 0) return fail(ROPE_ERR_UNSUPPORTED, "materialised index takes score_mode 0");
+  const int S = p->stride, N = p->window_len;
+  const int64_t W = (len - N) / S + 1;
+  if (W > 0x7FFFFFFF - 256) return fail(ROPE_ERR_UNSUPPORTED, "more than 2^31 windows");
+  DeviceCtx* c;
+  if ((st = get_ctx(&c)) != ROPE_OK) return st;
+
+  rope_index* idx = new rope_index();
+  ROPE_CUDA(cudaGetDevice(&idx->device));
+  idx->p = *p;
+  idx->p.bin_of_mer_host = nullptr;
+  idx->dense = true;
+  auto cleanup = [&](rope_status s) {
+    rope_index_free(idx);
+    return s;
+  };
+  HostTables h;
+  build_tables(*p, h);
+  // blocks of S starts: n_loc = full * S + rem; the partial block's starts are
+  // added directly, or a whole block is summed and the over-covered starts
+  // removed, whichever touches fewer starts
+  const int n_loc = N - p->s + 1;
+  const int full = n_loc / S, rem = n_loc - full * S;
+  int n_blk = full, t0 = 0, n_t = 0;
+  double sign = 1.0;
+  if (rem > 0 && rem <= S - rem) {
+    t0 = full * S;
+    n_t = rem;
+  } else if (rem > 0) {
+    n_blk = full + 1;
+    t0 = n_loc;
+    n_t = S - rem;
+    sign = -1.0;
+  }
+  std::vector<float2> bph((size_t)p->m * S), rotu((size_t)std::max(n_blk, 1) * p->m), tph((size_t)p->m * std::max(n_t, 1));
+  for (int k = 1; k <= p->m; ++k) {
+    int64_t a, q;
+    factor(*p, k, &a, &q);
+    for (int i = 0; i < S; ++i) {
+      const double2 v = unit(a, q, N, i);
+      bph[(size_t)(k - 1) * S + i] = make_float2((float)v.x, (float)v.y);
+    }
+    for (int u = 0; u < n_blk; ++u) {
+      const double2 v = unit(a, q, N, (int64_t)u * S);
+      rotu[(size_t)u * p->m + (k - 1)] = make_float2((float)v.x, (float)v.y);
+    }
+    for (int i = 0; i < n_t; ++i) {
+      const double2 v = unit(a, q, N, (int64_t)t0 + i);
+      tph[(size_t)(k - 1) * n_t + i] = make_float2((float)(sign * v.x), (float)(sign * v.y));
+    }
+  }
+  const int64_t n_words = (len + 15) / 16;
+  const int64_t pad_words = 16384 + kPackPadWords + ((int64_t)S + 15) / 16;
+  const int64_t n_blocks = n_blk > 0 ? W + n_blk - 1 : 0;
+  uint32_t* packed = nullptr;
+  float *inv_norm = nullptr, *win_f32 = nullptr;
+  uint16_t *win_bf16 = nullptr, *map_lsb = nullptr, *map = nullptr;
+  float2 *phase = nullptr, *d_bph = nullptr, *d_rotu = nullptr, *d_tph = nullptr;
+  if ((st = upload(idx->owned, std::vector<uint32_t>(), &packed, (size_t)(n_words + pad_words))) != ROPE_OK ||
+      (st = upload(idx->owned, std::vector<float>(), &inv_norm, (size_t)W + 256)) != ROPE_OK ||
+      (st = upload(idx->owned, std::vector<float>(), &win_f32, (size_t)W * 2 * D)) != ROPE_OK ||
+      (st = upload(idx->owned, std::vector<uint16_t>(), &win_bf16, (size_t)W * 2 * D)) != ROPE_OK ||
+      (st = upload(idx->owned, h.map_lsb, &map_lsb)) != ROPE_OK || (st = upload(idx->owned, h.map, &map)) != ROPE_OK ||
+      (st = upload(idx->owned, to_f32(h.phase), &phase)) != ROPE_OK ||
+      (st = upload(idx->owned, bph, &d_bph)) != ROPE_OK || (st = upload(idx->owned, rotu, &d_rotu)) != ROPE_OK ||
+      (st = upload(idx->owned, tph, &d_tph)) != ROPE_OK)
+    return cleanup(st);
+  DevIndex& ix = idx->ix;
+  ix.packed = packed;
+  ix.L = len;
+  ix.W = W;
+  ix.N = N;
+  ix.s = p->s;
+  ix.m = p->m;
+  ix.t = p->t;
+  ix.nb = h.nb;
+  ix.D = D;
+  ix.stride = S;
+  ix.A = 0;
+  ix.variant = p->variant;
+  ix.score_mode = p->score_mode;
+  ix.inv_norm = inv_norm;
+  ix.map_lsb = map_lsb;
+  ix.phase = phase;
+  ix.win_f32 = win_f32;
+  ix.win_bf16 = win_bf16;
+  idx->enc = EncTables{N, p->s, p->m, p->t, h.nb, D, map, phase};
+  DenseTables dt{n_blk, t0, n_t, n_blocks, d_bph, d_rotu, d_tph};
+
+  float2* bsum = nullptr;
+  int zero = 0;
+  cudaError_t e = cudaMemcpy(c->status, &zero, sizeof(int), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess && n_blocks > 0) e = cudaMalloc(&bsum, (size_t)n_blocks * D * sizeof(float2));
+  if (e == cudaErrorMemoryAllocation) return cleanup(fail(ROPE_ERR_OOM, "block sums: %s", cudaGetErrorString(e)));
+  if (e == cudaSuccess) e = launch_pack(ref, len, packed, c->status, stream);
+  if (e == cudaSuccess) e = launch_dense_index(ix, dt, bsum, win_f32, win_bf16, inv_norm, stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+  if (bsum) cudaFree(bsum);
+  if (e != cudaSuccess) return cleanup(fail(ROPE_ERR_CUDA, "materialised index build: %s", cudaGetErrorString(e)));
+  if ((st = rope_sync_status(stream)) != ROPE_OK) return cleanup(st);
+  if ((st = tensor_map_rows(&idx->tm_win, win_bf16, W, 2 * D)) != ROPE_OK) return cleanup(st);
+  *out = idx;
+  return ROPE_OK;
+}
+
+extern "C" rope_status rope_encode_reference_dense(const rope_params* p, const uint8_t* ref, int64_t len,
+                                                   rope_index** out, cudaStream_t stream) {
+  return encode_reference_dense_impl(p, ref, len, out, stream);
+}
+
 rope_status rope::encode_reference_impl(const rope_params* p, const uint8_t* ref, int64_t len,
                                         const uint32_t* shared_packed, rope_index** out, cudaStream_t stream) {
   rope_status st = check_params(p);
@@ -431,7 +610,11 @@ rope_status rope::encode_reference_impl(const rope_params* p, const uint8_t* ref
   *out = nullptr;
   if (!ref || len < p->window_len) return fail(ROPE_ERR_INVALID_ARG, "reference shorter than the window");
   const int D = p->m << (2 * p->t);
-  if (D > kMaxScanDim) return fail(ROPE_ERR_UNSUPPORTED, "index dimension %d > %d", D, kMaxScanDim);
+  if (D > kMaxScanDim) {
+    if (shared_packed) return fail(ROPE_ERR_UNSUPPORTED, "index dimension %d > %d in a ladder", D, kMaxScanDim);
+    return encode_reference_dense_impl(p, ref, len, out, stream);
+  }
+  if (p->stride > 64) return fail(ROPE_ERR_UNSUPPORTED, "stride=%d: the on-the-fly index takes stride <= 64", p->stride);
   const int64_t W = (len - p->window_len) / p->stride + 1;
   // window numbers are 32-bit in the scans, with room for one super-tile past the end
   if (W > (int64_t)0xFFFFFFFF - 65536) return fail(ROPE_ERR_UNSUPPORTED, "more than 2^32 - 2^16 windows");
@@ -543,6 +726,12 @@ extern "C" rope_status rope_window_embeddings(const rope_index* idx, int64_t j_b
                                               cudaStream_t stream) {
   if (!idx || !out) return fail(ROPE_ERR_INVALID_ARG, "NULL argument");
   if (j_begin < 0 || count < 0 || j_begin + count > idx->ix.W) return fail(ROPE_ERR_INVALID_ARG, "window range");
+  if (idx->dense) {
+    const size_t row = (size_t)2 * idx->ix.D * sizeof(float);
+    ROPE_CUDA(cudaMemcpyAsync(out, idx->ix.win_f32 + (size_t)j_begin * 2 * idx->ix.D, (size_t)count * row,
+                              cudaMemcpyDeviceToDevice, stream));
+    return ROPE_OK;
+  }
   ROPE_CUDA(launch_window_embeddings(idx->ix, j_begin, count, out, stream));
   return ROPE_OK;
 }
@@ -576,6 +765,7 @@ struct ScanPlan {
 rope_status plan_scan(const rope_index* idx, int32_t precision, int64_t n_reads, int64_t jb, int64_t je,
                       int32_t n_ranges_req, int num_sms, ScanPlan* out, int32_t tc_variant = 0) {
   const DevIndex& ix = idx->ix;
+  if (idx->dense) return fail(ROPE_ERR_UNSUPPORTED, "a materialised index is scored by rope_score_topk / rope_map / rope_score_dense only");
   ScanPlan pl;
   pl.tc = prec_tc(precision);
   int64_t sup;
@@ -826,6 +1016,110 @@ rope_status choose_tc(const rope_index* idx, const uint16_t* emb_bf16, const flo
 
 }  // namespace
 
+namespace {
+
+// Scan of a materialised index: the A operand, the tcgen05 GEMM with its fused
+// top-k (or every score into dense_out), then the merge with FP32 re-scoring
+// from the stored FP32 window rows.
+rope_status dense_scan(const rope_index* idx, const uint16_t* emb_bf16, const float* emb_f32, const float* norms,
+                       int64_t n_reads, const rope_score_opts& o, int64_t jb, int64_t je, int64_t* out_win,
+                       float* out_score, float* dense_out, cudaStream_t stream, int prof_slot,
+                       const int64_t* out_row) {
+  const DevIndex& ix = idx->ix;
+  if (o.precision != ROPE_PREC_BF16)
+    return fail(ROPE_ERR_UNSUPPORTED, "a materialised index is scored by the BF16 tensor-core GEMM (precision %d)",
+                o.precision);
+  if (!emb_bf16) return fail(ROPE_ERR_INVALID_ARG, "the tensor-core scan needs emb_bf16");
+  DeviceCtx* c;
+  rope_status st = get_ctx(&c);
+  if (st != ROPE_OK) return st;
+  const int BM = gemm_tc_group(), BN = gemm_tc_window_tile();
+  const int64_t n_pad = (n_reads + BM - 1) / BM * BM;
+  if (2 * n_pad > 0x7FFFFFFF) return fail(ROPE_ERR_UNSUPPORTED, "more than 2^30 reads in one call");
+  const int n_rt = (int)(n_pad / BM);
+  const int64_t n_wt = je > jb ? (je - jb + BN - 1) / BN : 0;
+  // waves of grp read tiles x n_ranges window ranges (one block each): the
+  // grp read tiles' operands stay in L2 while each range's window tiles stream
+  // past its grp blocks
+  int grp, n_ranges;
+  if ((int64_t)n_rt * 4 >= c->num_sms) {
+    n_ranges = 4;
+    grp = std::max(1, c->num_sms / 4);
+  } else {
+    grp = n_rt;
+    n_ranges = std::max(1, c->num_sms / n_rt);
+  }
+  if (n_ranges > n_wt) n_ranges = (int)std::max<int64_t>(1, n_wt);
+  const int64_t tiles_per_range = n_wt > 0 ? (n_wt + n_ranges - 1) / n_ranges : 1;
+  if (n_wt > 0) n_ranges = (int)((n_wt + tiles_per_range - 1) / tiles_per_range);
+  const int stages = gemm_tc_stages(dense_out ? 0 : o.cand_depth);
+  if (stages < 2) return fail(ROPE_ERR_UNSUPPORTED, "cand_depth=%d: the GEMM scan does not fit in shared memory", o.cand_depth);
+  auto al = [](size_t b) { return (b + 255) & ~size_t(255); };
+  const size_t a_bytes = al((size_t)2 * n_pad * 2 * ix.D * sizeof(uint16_t));
+  const size_t cand_bytes = dense_out ? 0 : (size_t)n_reads * n_ranges * o.cand_depth * sizeof(Candidate);
+  uint8_t* scratch = nullptr;
+  if ((st = pool_alloc(c, (void**)&scratch, a_bytes + cand_bytes, stream)) != ROPE_OK) return st;
+  uint16_t* a_op = reinterpret_cast<uint16_t*>(scratch);
+  Candidate* cand = reinterpret_cast<Candidate*>(scratch + a_bytes);
+  auto release = [&](rope_status r) {
+    cudaFreeAsync(scratch, stream);
+    return r;
+  };
+  cudaError_t e = cudaSuccess;
+  if (n_wt > 0) {
+    CUtensorMap tmA;
+    e = launch_gemm_a(emb_bf16, n_reads, n_pad, ix.D, a_op, stream);
+    if (e != cudaSuccess) return release(fail(ROPE_ERR_CUDA, "A operand launch: %s", cudaGetErrorString(e)));
+    if ((st = tensor_map_rows(&tmA, a_op, 2 * n_pad, 2 * ix.D)) != ROPE_OK) return release(st);
+    GemmArgs g{};
+    g.n_reads = n_reads;
+    g.n_rt = n_rt;
+    g.grp = grp;
+    g.n_ranges = n_ranges;
+    g.k_blocks = 2 * ix.D / 64;
+    g.a_im_row0 = (int32_t)n_pad;
+    g.stages = stages;
+    g.jb = jb;
+    g.je = je;
+    g.range_len = tiles_per_range * BN;
+    g.cand_depth = dense_out ? 1 : o.cand_depth;
+    g.sep = o.sep;
+    g.stride = ix.stride;
+    g.cand = dense_out ? nullptr : cand;
+    g.dense = dense_out;
+    g.status = c->status;
+    g.wait_limit_ns = wait_limit_ns();
+    e = launch_gemm_tc(tmA, idx->tm_win, g, dense_out != nullptr, c->num_sms, stream);
+    if (e != cudaSuccess) return release(fail(ROPE_ERR_CUDA, "GEMM scan launch: %s", cudaGetErrorString(e)));
+  } else if (!dense_out) {
+    e = cudaMemsetAsync(cand, 0xFF, cand_bytes, stream);  // every slot empty
+    if (e != cudaSuccess) return release(fail(ROPE_ERR_CUDA, "cudaMemsetAsync: %s", cudaGetErrorString(e)));
+  }
+  if (dense_out) return release(ROPE_OK);
+  prof_mark(prof_slot, 2, stream);
+  MergeArgs m{};
+  m.cand = cand;
+  m.n_reads = n_reads;
+  m.n_ranges = n_ranges;
+  m.cand_depth = o.cand_depth;
+  m.k = o.k;
+  m.sep = o.sep;
+  m.rescore = o.rescore;
+  m.rescore_depth = o.rescore_depth;
+  m.emb_f32 = emb_f32;
+  m.norms = norms;
+  m.out_win = out_win;
+  m.out_score = out_score;
+  m.out_row = out_row;
+  m.status = c->status;
+  e = launch_merge(ix, m, stream);
+  prof_mark(prof_slot, 3, stream);
+  if (e != cudaSuccess) return release(fail(ROPE_ERR_CUDA, "merge launch: %s", cudaGetErrorString(e)));
+  return release(ROPE_OK);
+}
+
+}  // namespace
+
 rope_status rope::score_topk_impl(const rope_index* idx, const float* emb_f32, const uint16_t* emb_bf16,
                                   const float* norms, int64_t n_reads, const rope_score_opts* opts, int64_t* out_win,
                                   float* out_score, cudaStream_t stream, int prof_slot, const int64_t* out_row, const ExtCandidates* ext) {
@@ -843,6 +1137,11 @@ rope_status rope::score_topk_impl(const rope_index* idx, const float* emb_f32, c
   const int64_t jb = o.j_begin > 0 ? o.j_begin : 0;
   const int64_t je = o.j_end > 0 ? (o.j_end < ix.W ? o.j_end : ix.W) : ix.W;
   if (jb > ix.W) return fail(ROPE_ERR_INVALID_ARG, "j_begin beyond the last window");
+  if (idx->dense) {
+    if (ext) return fail(ROPE_ERR_UNSUPPORTED, "a materialised index takes no caller candidate buffer");
+    return dense_scan(idx, emb_bf16, emb_f32, norms, n_reads, o, jb, je, out_win, out_score, nullptr, stream,
+                      prof_slot, out_row);
+  }
 
   ScanPlan pl;
   Candidate* cand = nullptr;
@@ -1035,6 +1334,14 @@ extern "C" rope_status rope_score_dense(const rope_index* idx, const float* emb_
   if (n_reads == 0 || count == 0) return ROPE_OK;
   if (!emb_f32 || !norms || !out) return fail(ROPE_ERR_INVALID_ARG, "NULL pointer");
   if (prec_tc(precision) && !emb_bf16) return fail(ROPE_ERR_INVALID_ARG, "tensor-core scan needs emb_bf16");
+  if (idx->dense) {
+    rope_score_opts o{};
+    o.k = 1;
+    o.precision = precision;
+    o.cand_depth = 1;
+    return dense_scan(idx, emb_bf16, emb_f32, norms, n_reads, o, j_begin, j_begin + count, nullptr, nullptr, out,
+                      stream, -1, nullptr);
+  }
   DeviceCtx* c;
   rope_status st = get_ctx(&c);
   if (st != ROPE_OK) return st;
@@ -1207,6 +1514,8 @@ extern "C" rope_status rope_score_topk_noalloc(const rope_index* idx, const floa
   if (dev < 0 || dev >= kNoAllocMaxDevices) return fail(ROPE_ERR_UNSUPPORTED, "device ordinal %d", dev);
   void* base = nullptr;
   int num_sms = 0;
+  if (idx->dense)
+    return fail(ROPE_ERR_UNSUPPORTED, "the allocation-free scan takes the on-the-fly index, not a materialised one");
   if ((st = noalloc_setup(dev, &base, &num_sms)) != ROPE_OK) return st;
 
   const DevIndex& ix = idx->ix;
@@ -1256,9 +1565,13 @@ extern "C" rope_status rope_score_topk_noalloc(const rope_index* idx, const floa
   int* status = static_cast<int*>(base);
   Candidate* cand = reinterpret_cast<Candidate*>(static_cast<unsigned char*>(base) + kNoAllocHeadBytes);
   const size_t cand_bytes = (size_t)n_ranges * per_range;
-  // the status word must start at zero; the candidate lists are fully written
-  // by the scan (or set empty below) before the merge reads them
+  // The call's status word starts at zero and every candidate slot empty on
+  // every call: a scan block that gives up on a bounded wait leaves its lists
+  // unwritten, and those slots must not show the previous call's candidates.
+  // The merge also ORs the call's bits into the sticky word (status[1]) that
+  // rope_noalloc_sync_status reads and clears.
   ROPE_CUDA(cudaMemsetAsync(status, 0, sizeof(int), stream));
+  ROPE_CUDA(cudaMemsetAsync(cand, 0xFF, cand_bytes, stream));
   if (je > jb) {
     pl.a.emb_f32 = emb_f32;
     pl.a.emb_bf16 = emb_bf16;
@@ -1271,10 +1584,10 @@ extern "C" rope_status rope_score_topk_noalloc(const rope_index* idx, const floa
     cudaError_t e = pl.tc ? launch_scan_tc(ix, pl.a, false, num_sms, stream)
                           : launch_scan_fp32(ix, pl.a, false, num_sms, stream);
     if (e != cudaSuccess) return fail(ROPE_ERR_CUDA, "scan launch: %s", cudaGetErrorString(e));
-  } else {
-    ROPE_CUDA(cudaMemsetAsync(cand, 0xFF, cand_bytes, stream));  // every slot empty
   }
   MergeArgs m{};
+  m.empty_on_timeout = 1;
+  m.sticky_status = status + 1;
   m.cand = cand;
   m.n_reads = n_reads;
   m.n_ranges = n_ranges;
@@ -1290,5 +1603,24 @@ extern "C" rope_status rope_score_topk_noalloc(const rope_index* idx, const floa
   m.status = status;
   cudaError_t e = launch_merge(ix, m, stream);
   if (e != cudaSuccess) return fail(ROPE_ERR_CUDA, "merge launch: %s", cudaGetErrorString(e));
+  return ROPE_OK;
+}
+
+extern "C" rope_status rope_noalloc_sync_status(cudaStream_t stream) {
+  int dev = 0;
+  ROPE_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kNoAllocMaxDevices) return fail(ROPE_ERR_UNSUPPORTED, "device ordinal %d", dev);
+  void* base = nullptr;
+  int num_sms = 0;
+  rope_status st = noalloc_setup(dev, &base, &num_sms);
+  if (st != ROPE_OK) return st;
+  ROPE_CUDA(cudaStreamSynchronize(stream));
+  int* sticky = static_cast<int*>(base) + 1;
+  int v = 0;
+  ROPE_CUDA(cudaMemcpy(&v, sticky, sizeof(int), cudaMemcpyDeviceToHost));
+  ROPE_CUDA(cudaMemset(sticky, 0, sizeof(int)));
+  if (v & kStatusTimeout)
+    return fail(ROPE_ERR_TIMEOUT, "a bounded in-kernel wait ran out; the results were set to (-1, -inf)");
+  if (v & kStatusBadArg) return fail(ROPE_ERR_INVALID_ARG, "a kernel saw an out-of-range argument");
   return ROPE_OK;
 }

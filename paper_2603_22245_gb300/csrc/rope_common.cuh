@@ -43,6 +43,9 @@ struct DevIndex {
   const float2* rot;        // [m] exp(-2 pi i f_k stride / N)
   const float2* eout;       // [m * stride] exp(2 pi i f_k j / N), j < stride
   const float2* ein;        // [m * stride] exp(2 pi i f_k (N-s+1+j) / N), j < stride
+  // materialised index (the window matrix of §3.1; null for the on-the-fly index)
+  const float* win_f32;     // [W, 2D] unnormalised [cr | ci]
+  const uint16_t* win_bf16; // [W, 2D] BF16 [cr | ci] / |c|
 };
 
 // ---------------------------------------------------------------- status
@@ -227,17 +230,39 @@ __device__ __forceinline__ bool mbar_try_wait_suspend(uint64_t* bar, uint32_t pa
 }
 
 // Bounded wait on a phase parity. Returns false (and sets the timeout bit and
-// the block's abort flag) if the phase did not complete within kWaitLimitNs,
-// or if another role of the block has already aborted.
+// the block's abort flag) if the phase did not complete within limit_ns, or
+// if another role of the block has already aborted. Limits shorter than the
+// suspend hint poll without suspending, so that a short limit is kept.
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag, int* status,
                                           uint64_t limit_ns = kWaitLimitNs) {
   if (mbar_try_wait(bar, parity)) return true;
   const uint64_t t0 = globaltimer_ns();
+  const bool suspend = limit_ns >= 4ull * kSuspendHintNs;
   for (;;) {
-    if (mbar_try_wait_suspend(bar, parity)) return true;
+    if (suspend ? mbar_try_wait_suspend(bar, parity) : mbar_try_wait(bar, parity)) return true;
     if (*abort_flag) return false;
     if (globaltimer_ns() - t0 > limit_ns) {
       *abort_flag = 1;
+      set_status(status, kStatusTimeout);
+      return false;
+    }
+  }
+}
+
+// Bound of a drain wait: at least one second, whatever the ordinary limit.
+constexpr uint64_t kDrainLimitNs = 1000000000ull;
+
+// Wait for this block's own asynchronous work in flight (bulk copies, MMAs)
+// before it frees tensor memory and exits: unlike mbar_wait it does not give
+// up when the block has aborted, only when max(limit_ns, kDrainLimitNs) has
+// passed (then it sets the timeout bit and returns false).
+__device__ __forceinline__ bool mbar_drain_wait(uint64_t* bar, uint32_t parity, int* status, uint64_t limit_ns) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const uint64_t lim = limit_ns > kDrainLimitNs ? limit_ns : kDrainLimitNs;
+  const uint64_t t0 = globaltimer_ns();
+  for (;;) {
+    if (mbar_try_wait_suspend(bar, parity)) return true;
+    if (globaltimer_ns() - t0 > lim) {
       set_status(status, kStatusTimeout);
       return false;
     }
@@ -261,6 +286,23 @@ __device__ __forceinline__ void bulk_g2s(void* dst_smem, const void* src, uint32
       "cp.async.bulk.shared::cta.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(smem_u32(dst_smem)),
       "l"(src), "r"(bytes), "r"(smem_u32(bar))
       : "memory");
+}
+
+// 2-D tiled tensor copy global -> shared (TMA), completion signalled on `bar`
+// (tx bytes = the whole box, out-of-bounds elements filled with zero). x is the
+// innermost coordinate in elements (x * element size a multiple of 16 bytes),
+// y the row; dst 1024-byte aligned for the 128-byte swizzle.
+__device__ __forceinline__ void tma_load_2d(void* dst_smem, const void* tensor_map, int32_t x, int32_t y,
+                                            uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::
+          "r"(smem_u32(dst_smem)),
+      "l"(tensor_map), "r"(x), "r"(y), "r"(smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ void prefetch_tensor_map(const void* tensor_map) {
+  asm volatile("prefetch.tensormap [%0];" ::"l"(tensor_map) : "memory");
 }
 
 __device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }

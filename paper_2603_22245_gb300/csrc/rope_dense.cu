@@ -1,0 +1,532 @@
+// Materialised window index and its tensor-core scan (wide encodings).
+//
+// §3.1 builds an index of window encodings -- a database of vectors -- and
+// scores a read against it by a matrix product; §3.2 sizes it for 20 kbp reads
+// (window N = 20,000, step 1,250, 1024 complex dimensions: ~2.5M vectors for a
+// 3.1 Gbp genome). At that width regenerating windows per read tile (the
+// on-the-fly scan of the narrow encodings) would cost more than scoring them,
+// so this index stores every window once, in BF16 for the tensor cores and in
+// FP32 for re-scoring, and the scan is a GEMM.
+//
+// Index build, exact up to FP32 rounding (no recurrence, so no drift). With
+// stride S, the s-mer starts of the reference fall into blocks of S starts;
+// block q's sums B_q[k][b] = sum_{i<S} [bin(qS+i) = b] w_k^{f_k i} use
+// block-relative phases. Window j (start jS) covers starts jS .. jS+N-s, i.e.
+// blocks j .. j+n_blk-1 with block u's phases shifted by w_k^{f_k u S}:
+//     c_j[k][b] = sum_u w_k^{f_k u S} B_{j+u}[k][b]  (+/- a short tail)
+// where the tail adds the starts of a partial last block, or removes the
+// starts past N-s that a whole last block over-covers (§2.1-§2.3 definition,
+// summed in another order).
+//
+// Scan: C[read][window] = <x|c> as a real GEMM on tcgen05 (BF16 in, FP32 in
+// tensor memory). Per tile 128 reads x 128 windows and per 64-wide K block, TMA
+// brings three 128-row boxes into shared memory: the reads' [xr | xi] rows
+// (A_re), their [-xi | xr] rows (A_im) and the windows' [cr | ci] rows (B), so
+// that D_re = A_re B^T = Re<x|c> and D_im = A_im B^T = Im<x|c> land in the same
+// tensor-memory lane (the read) and column (the window): the epilogue thread of
+// a read forms |.|^2 with no data exchange (§4's real identity).
+#include <cuda.h>
+#include <cuda_bf16.h>
+
+#include "rope_internal.h"
+#include "rope_topk.cuh"
+
+namespace rope {
+
+// ---------------------------------------------------------------- index build
+
+// One warp per block of S s-mer starts: lanes compute 32 bins at a time from
+// the packed letters, then the lane of each band adds the block-relative
+// phase of every start to its bin, in start order (deterministic FP32 sums).
+__global__ void block_sums_kernel(DevIndex ix, DenseTables dt, float2* __restrict__ out) {
+  extern __shared__ float2 bs_acc[];
+  const int lane = threadIdx.x & 31;
+  const int warp = threadIdx.x >> 5;
+  const int wpb = blockDim.x >> 5;
+  float2* acc = bs_acc + (size_t)warp * ix.D;
+  const int S = ix.stride;
+  for (int64_t q = (int64_t)blockIdx.x * wpb + warp; q < dt.n_blocks; q += (int64_t)gridDim.x * wpb) {
+    for (int g = lane; g < ix.D; g += 32) acc[g] = make_float2(0.f, 0.f);
+    __syncwarp();
+    const int64_t p0 = q * S;
+    for (int i0 = 0; i0 < S; i0 += 32) {
+      const int i = i0 + lane;
+      const uint32_t b = i < S ? bin_at(ix.packed, p0 + i, ix.s, ix.map_lsb) : 0u;
+      const int cnt = min(32, S - i0);
+      for (int jj = 0; jj < cnt; ++jj) {
+        const uint32_t bj = __shfl_sync(0xffffffffu, b, jj);
+        if (lane < ix.m) {
+          const float2 ph = __ldg(dt.bph + (size_t)lane * S + i0 + jj);
+          float2& a = acc[lane * ix.nb + bj];
+          a.x += ph.x;
+          a.y += ph.y;
+        }
+        __syncwarp();
+      }
+    }
+    float2* o = out + (size_t)q * ix.D;
+    for (int g = lane; g < ix.D; g += 32) o[g] = acc[g];
+    __syncwarp();
+  }
+}
+
+// One block of 256 threads per run of consecutive windows; thread t holds
+// entries t, t+256, ... (EPT of them). Per window: the tail sums (one warp, in
+// start order, into shared memory), the block combination, the squared norm
+// (fixed-order block reduction), then the FP32 row, the normalised BF16 row
+// and 1/|c|.
+template <int EPT>
+__global__ void __launch_bounds__(256) dense_windows_kernel(DevIndex ix, DenseTables dt,
+                                                            const float2* __restrict__ bsum,
+                                                            float* __restrict__ out_f32,
+                                                            __nv_bfloat16* __restrict__ out_bf16,
+                                                            float* __restrict__ inv_norm, int64_t run) {
+  extern __shared__ float2 dw_tail[];  // [D]
+  __shared__ float red[8];
+  const int tid = threadIdx.x;
+  const int lane = tid & 31;
+  const int warp = tid >> 5;
+  const int D = ix.D;
+  int band[EPT];
+#pragma unroll
+  for (int i = 0; i < EPT; ++i) {
+    const int e = tid + 256 * i;
+    band[i] = e < D ? e / ix.nb : 0;
+  }
+  const int64_t j_lo = (int64_t)blockIdx.x * run;
+  const int64_t j_hi = min(ix.W, j_lo + run);
+  for (int64_t j = j_lo; j < j_hi; ++j) {
+    if (dt.n_t > 0) {
+      for (int e = tid; e < D; e += 256) dw_tail[e] = make_float2(0.f, 0.f);
+      __syncthreads();
+      if (warp == 0) {
+        const int64_t p0 = j * ix.stride + dt.t0;
+        for (int i0 = 0; i0 < dt.n_t; i0 += 32) {
+          const int i = i0 + lane;
+          const uint32_t b = i < dt.n_t ? bin_at(ix.packed, p0 + i, ix.s, ix.map_lsb) : 0u;
+          const int cnt = min(32, dt.n_t - i0);
+          for (int jj = 0; jj < cnt; ++jj) {
+            const uint32_t bj = __shfl_sync(0xffffffffu, b, jj);
+            if (lane < ix.m) {
+              const float2 ph = __ldg(dt.tph + (size_t)lane * dt.n_t + i0 + jj);
+              float2& a = dw_tail[lane * ix.nb + bj];
+              a.x += ph.x;
+              a.y += ph.y;
+            }
+            __syncwarp();
+          }
+        }
+      }
+      __syncthreads();
+    }
+    float cr[EPT], ci[EPT];
+#pragma unroll
+    for (int i = 0; i < EPT; ++i) cr[i] = ci[i] = 0.f;
+    for (int u = 0; u < dt.n_blk; ++u) {
+      const float2* row = bsum + (size_t)(j + u) * D;
+#pragma unroll
+      for (int i = 0; i < EPT; ++i) {
+        const int e = tid + 256 * i;
+        if (e < D) {
+          const float2 v = __ldg(row + e);
+          const float2 r = __ldg(dt.rotu + (size_t)u * ix.m + band[i]);
+          cr[i] = fmaf(v.x, r.x, fmaf(-v.y, r.y, cr[i]));
+          ci[i] = fmaf(v.x, r.y, fmaf(v.y, r.x, ci[i]));
+        }
+      }
+    }
+    float part = 0.f;
+#pragma unroll
+    for (int i = 0; i < EPT; ++i) {
+      const int e = tid + 256 * i;
+      if (e < D) {
+        if (dt.n_t > 0) {
+          cr[i] += dw_tail[e].x;
+          ci[i] += dw_tail[e].y;
+        }
+        part = fmaf(cr[i], cr[i], fmaf(ci[i], ci[i], part));
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+    if (lane == 0) red[warp] = part;
+    __syncthreads();
+    float tot = 0.f;
+#pragma unroll
+    for (int w = 0; w < 8; ++w) tot += red[w];
+    const float inv = tot > kZeroNorm2 ? (float)(1.0 / sqrt((double)tot)) : 0.f;
+    float* of = out_f32 + (size_t)j * 2 * D;
+    __nv_bfloat16* ob = out_bf16 + (size_t)j * 2 * D;
+#pragma unroll
+    for (int i = 0; i < EPT; ++i) {
+      const int e = tid + 256 * i;
+      if (e < D) {
+        of[e] = cr[i];
+        of[D + e] = ci[i];
+        ob[e] = __float2bfloat16_rn(cr[i] * inv);
+        ob[D + e] = __float2bfloat16_rn(ci[i] * inv);
+      }
+    }
+    if (tid == 0) inv_norm[j] = inv;
+    __syncthreads();  // red and the tail buffer are reused by the next window
+  }
+}
+
+cudaError_t launch_dense_index(const DevIndex& ix, const DenseTables& dt, float2* bsum, float* win_f32,
+                               uint16_t* win_bf16, float* inv_norm, cudaStream_t st) {
+  {
+    const int wpb = 8;
+    const size_t smem = (size_t)wpb * ix.D * sizeof(float2);
+    if (smem > 48 * 1024) {
+      cudaError_t e = cudaFuncSetAttribute(block_sums_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+    }
+    int64_t blocks = (dt.n_blocks + wpb - 1) / wpb;
+    if (blocks > 152 * 32) blocks = 152 * 32;
+    block_sums_kernel<<<(unsigned)blocks, wpb * 32, smem, st>>>(ix, dt, bsum);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  const int64_t run = 32;
+  const int64_t grid = (ix.W + run - 1) / run;
+  const size_t smem = (size_t)ix.D * sizeof(float2);
+  auto go = [&](auto kern) -> cudaError_t {
+    if (smem > 48 * 1024) {
+      cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+    }
+    kern<<<(unsigned)grid, 256, smem, st>>>(ix, dt, bsum, win_f32, reinterpret_cast<__nv_bfloat16*>(win_bf16),
+                                            inv_norm, run);
+    return cudaGetLastError();
+  };
+  const int ept = (ix.D + 255) / 256;
+  if (ept <= 1) return go(dense_windows_kernel<1>);
+  if (ept <= 2) return go(dense_windows_kernel<2>);
+  if (ept <= 4) return go(dense_windows_kernel<4>);
+  if (ept <= 8) return go(dense_windows_kernel<8>);
+  if (ept <= 16) return go(dense_windows_kernel<16>);
+  return cudaErrorInvalidValue;
+}
+
+// ---------------------------------------------------------------- scan operands
+
+// A operand of the scan: rows [0, n_pad) are the reads' normalised [xr | xi]
+// (zero past n), rows [n_pad, 2 n_pad) are [-xi | xr]. Four BF16 entries per
+// thread (D is a multiple of 32).
+__global__ void gemm_a_kernel(const uint16_t* __restrict__ emb, int64_t n, int64_t n_pad, int D,
+                              uint16_t* __restrict__ a) {
+  const int q4 = D / 4;
+  const int64_t total = n_pad * q4;
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = idx / q4;
+    const int g = (int)(idx % q4) * 4;
+    uint2 xr = make_uint2(0, 0), xi = make_uint2(0, 0);
+    if (r < n) {
+      xr = *reinterpret_cast<const uint2*>(emb + r * 2 * D + g);
+      xi = *reinterpret_cast<const uint2*>(emb + r * 2 * D + D + g);
+    }
+    const uint2 nxi = make_uint2(xi.x ^ 0x80008000u, xi.y ^ 0x80008000u);
+    *reinterpret_cast<uint2*>(a + r * 2 * D + g) = xr;
+    *reinterpret_cast<uint2*>(a + r * 2 * D + D + g) = xi;
+    *reinterpret_cast<uint2*>(a + (n_pad + r) * 2 * D + g) = nxi;
+    *reinterpret_cast<uint2*>(a + (n_pad + r) * 2 * D + D + g) = xr;
+  }
+}
+
+cudaError_t launch_gemm_a(const uint16_t* emb, int64_t n, int64_t n_pad, int D, uint16_t* a, cudaStream_t st) {
+  const int64_t total = n_pad * (D / 4);
+  int64_t blocks = (total + 255) / 256;
+  if (blocks > 152 * 64) blocks = 152 * 64;
+  if (blocks < 1) return cudaSuccess;
+  gemm_a_kernel<<<(unsigned)blocks, 256, 0, st>>>(emb, n, n_pad, D, a);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- tensor-core scan
+
+struct GemmShape {
+  static constexpr int BM = 128;                 // reads per tile (tensor-memory lanes)
+  static constexpr int BN = 128;                 // windows per tile (MMA N)
+  static constexpr int BK = 64;                  // K per stage: one 128-byte swizzled BF16 row
+  static constexpr int MAX_STAGES = 4;
+  static constexpr int BOX_BYTES = 128 * BK * 2;           // one 128-row box: 16 KB
+  static constexpr int STAGE_BYTES = 3 * BOX_BYTES;        // A_re, A_im, B
+  static constexpr int ACC_COLS = 2 * BN;                  // Re and Im accumulators of a tile
+  static constexpr int TMEM_COLS = 512;                    // two accumulator buffers
+  static constexpr int EPI_WARPS = 4;
+  static constexpr int NTHREADS = 32 * (2 + EPI_WARPS);    // producer, MMA, epilogue
+  static constexpr uint32_t IDESC = idesc_bf16_f32(BM, BN);
+  static_assert(2 * ACC_COLS <= TMEM_COLS, "tensor memory");
+};
+
+// (read tile, window range) of item `it`; false for the padding items of the
+// last wave. Items come in waves of grp read tiles x n_ranges ranges, range
+// by range, so that a wave's blocks share each window tile in L2 while its
+// grp read tiles stay resident there.
+__device__ __forceinline__ bool gemm_item(const GemmArgs& g, int64_t it, int& rt, int& rg, int64_t& w_lo,
+                                          int64_t& w_hi) {
+  const int64_t per_wave = (int64_t)g.grp * g.n_ranges;
+  const int64_t wv = it / per_wave;
+  const int64_t in = it % per_wave;
+  rg = (int)(in / g.grp);
+  rt = (int)(wv * g.grp + in % g.grp);
+  w_lo = g.jb + (int64_t)rg * g.range_len;
+  w_hi = min(w_lo + g.range_len, g.je);
+  return rt < g.n_rt;
+}
+
+template <bool kDense>
+__global__ void __launch_bounds__(GemmShape::NTHREADS, 1)
+    gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, GemmArgs g) {
+  using Sh = GemmShape;
+  extern __shared__ __align__(1024) uint8_t gm_raw[];
+  __shared__ __align__(8) uint64_t bar_full[Sh::MAX_STAGES], bar_empty[Sh::MAX_STAGES];
+  __shared__ __align__(8) uint64_t bar_accfull[2], bar_accempty[2], bar_drain;
+  __shared__ uint32_t tmem_base_s;
+  __shared__ int abort_s;
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(gm_raw) + 1023) & ~uintptr_t(1023));
+  uint8_t* stages = smem;
+  float* list_s = reinterpret_cast<float*>(smem + (size_t)g.stages * Sh::STAGE_BYTES);
+  uint32_t* list_w = reinterpret_cast<uint32_t*>(list_s + (size_t)g.cand_depth * Sh::BM);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const uint64_t wlim = g.wait_limit_ns;
+  volatile int* abort_flag = &abort_s;
+  const int ns = g.stages;
+
+  if (tid == 0) {
+    for (int i = 0; i < ns; ++i) {
+      mbar_init(&bar_full[i], 1);
+      mbar_init(&bar_empty[i], 1);
+    }
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(&bar_accfull[i], 1);
+      mbar_init(&bar_accempty[i], Sh::EPI_WARPS);
+    }
+    mbar_init(&bar_drain, 1);
+    abort_s = 0;
+    fence_barrier_init();
+    prefetch_tensor_map(&tmA);
+    prefetch_tensor_map(&tmB);
+  }
+  if (warp == 1) {
+    tmem_alloc(&tmem_base_s, Sh::TMEM_COLS);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tbase = tmem_base_s;
+  const int64_t n_items = (int64_t)((g.n_rt + g.grp - 1) / g.grp) * g.grp * g.n_ranges;
+
+  if (warp == 0) {
+    // ================================================================ TMA producer
+    if (lane == 0) {
+      uint32_t stage = 0, phase = 0;
+      int64_t issued = 0;
+      for (int64_t it = blockIdx.x; it < n_items; it += gridDim.x) {
+        int rt, rg;
+        int64_t w_lo, w_hi;
+        if (!gemm_item(g, it, rt, rg, w_lo, w_hi)) continue;
+        bool ok = true;
+        for (int64_t w0 = w_lo; w0 < w_hi && ok; w0 += Sh::BN) {
+          for (int kb = 0; kb < g.k_blocks; ++kb) {
+            if (!mbar_wait(&bar_empty[stage], phase ^ 1u, abort_flag, g.status, wlim)) {
+              ok = false;
+              break;
+            }
+            uint8_t* st = stages + (size_t)stage * Sh::STAGE_BYTES;
+            mbar_expect_tx(&bar_full[stage], Sh::STAGE_BYTES);
+            tma_load_2d(st, &tmA, kb * Sh::BK, rt * Sh::BM, &bar_full[stage]);
+            tma_load_2d(st + Sh::BOX_BYTES, &tmA, kb * Sh::BK, g.a_im_row0 + rt * Sh::BM, &bar_full[stage]);
+            tma_load_2d(st + 2 * Sh::BOX_BYTES, &tmB, kb * Sh::BK, (int32_t)w0, &bar_full[stage]);
+            ++issued;
+            if (++stage == (uint32_t)ns) {
+              stage = 0;
+              phase ^= 1u;
+            }
+          }
+        }
+        if (!ok) break;
+      }
+      // the latest copy into each stage may still be in flight (after an abort)
+      for (int64_t i = issued > ns ? issued - ns : 0; i < issued; ++i)
+        mbar_drain_wait(&bar_full[i % ns], (uint32_t)((i / ns) & 1), g.status, wlim);
+    }
+  } else if (warp == 1) {
+    // ================================================================ MMA issue
+    if (lane == 0) {
+      uint32_t stage = 0, phase = 0, t = 0;
+      bool ok = true;
+      for (int64_t it = blockIdx.x; it < n_items && ok; it += gridDim.x) {
+        int rt, rg;
+        int64_t w_lo, w_hi;
+        if (!gemm_item(g, it, rt, rg, w_lo, w_hi)) continue;
+        for (int64_t w0 = w_lo; w0 < w_hi && ok; w0 += Sh::BN, ++t) {
+          const uint32_t buf = t & 1u;
+          if (!mbar_wait(&bar_accempty[buf], ((t >> 1) & 1u) ^ 1u, abort_flag, g.status, wlim)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t d_re = tbase + buf * Sh::ACC_COLS, d_im = d_re + Sh::BN;
+          for (int kb = 0; kb < g.k_blocks; ++kb) {
+            if (!mbar_wait(&bar_full[stage], phase, abort_flag, g.status, wlim)) {
+              ok = false;
+              break;
+            }
+            tc_fence_after();
+            const uint32_t base = smem_u32(stages + (size_t)stage * Sh::STAGE_BYTES);
+            const uint64_t a_re = smem_desc_sw128(base), a_im = smem_desc_sw128(base + Sh::BOX_BYTES);
+            const uint64_t b = smem_desc_sw128(base + 2 * Sh::BOX_BYTES);
+#pragma unroll
+            for (int kk = 0; kk < Sh::BK / 16; ++kk) {
+              const uint32_t acc = (kb > 0 || kk > 0) ? 1u : 0u;
+              // K step kk: 32 bytes further along the 128-byte rows (16-byte units)
+              tc_mma_ss(d_re, a_re + 2 * kk, b + 2 * kk, Sh::IDESC, acc);
+              tc_mma_ss(d_im, a_im + 2 * kk, b + 2 * kk, Sh::IDESC, acc);
+            }
+            tc_commit(&bar_empty[stage]);
+            if (++stage == (uint32_t)ns) {
+              stage = 0;
+              phase ^= 1u;
+            }
+          }
+          if (ok) tc_commit(&bar_accfull[buf]);
+        }
+      }
+      // every MMA issued by this thread has completed (also after an abort)
+      tc_commit(&bar_drain);
+      mbar_drain_wait(&bar_drain, 0, g.status, wlim);
+    }
+  } else {
+    // ================================================================ epilogue
+    // thread = one read (tensor-memory lane 32q + lane of its warp's quarter)
+    const int q = warp & 3;
+    const int row = 32 * q + lane;
+    const uint32_t lane_base = (uint32_t)(32 * q) << 16;
+    float* ls = list_s + row;
+    uint32_t* lw = list_w + row;
+    uint32_t t = 0;
+    const int64_t n_dense = g.je - g.jb;
+    for (int64_t it = blockIdx.x; it < n_items; it += gridDim.x) {
+      int rt, rg;
+      int64_t w_lo, w_hi;
+      if (!gemm_item(g, it, rt, rg, w_lo, w_hi)) continue;
+      const int64_t r = (int64_t)rt * Sh::BM + row;
+      const bool have = r < g.n_reads;
+      float thr = -INFINITY;
+      int worst = 0;
+      if (!kDense) {
+        for (int e = 0; e < g.cand_depth; ++e) {
+          ls[e * Sh::BM] = -INFINITY;
+          lw[e * Sh::BM] = kEmptyWin;
+        }
+      }
+      for (int64_t w0 = w_lo; w0 < w_hi; w0 += Sh::BN, ++t) {
+        const uint32_t buf = t & 1u;
+        if (!mbar_wait_warp(&bar_accfull[buf], (t >> 1) & 1u, abort_flag, g.status, wlim)) goto epi_done;
+        tc_fence_after();
+        const bool full = w0 + Sh::BN <= w_hi;
+#pragma unroll 1
+        for (int c0 = 0; c0 < Sh::BN; c0 += 16) {
+          const uint32_t taddr = tbase + lane_base + buf * Sh::ACC_COLS + (uint32_t)c0;
+          uint32_t vr[16], vi[16];
+          tmem_ld16(taddr, vr);
+          tmem_ld16(taddr + Sh::BN, vi);
+          tc_wait_ld();
+          if (c0 + 16 == Sh::BN) {
+            // the tile's last columns are in registers: hand the buffer back
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&bar_accempty[buf]);
+          }
+          float sc[16];
+#pragma unroll
+          for (int n = 0; n < 16; n += 2) abs2_pair(vr[n], vr[n + 1], vi[n], vi[n + 1], sc[n], sc[n + 1]);
+          const int64_t jc = w0 + c0;
+          if constexpr (kDense) {
+            if (have) {
+#pragma unroll
+              for (int n = 0; n < 16; ++n)
+                if (jc + n < w_hi) g.dense[r * n_dense + (jc + n - g.jb)] = sc[n];
+            }
+          } else {
+            float mx = -INFINITY;
+            if (full) {
+#pragma unroll
+              for (int n = 0; n < 16; ++n) mx = fmaxf(mx, sc[n]);
+            } else {
+#pragma unroll
+              for (int n = 0; n < 16; ++n)
+                if (jc + n < w_hi) mx = fmaxf(mx, sc[n]);
+            }
+            if (have && mx >= thr) {
+              for (int n = 0; n < 16; ++n) {
+                if (jc + n >= w_hi || !(sc[n] >= thr)) continue;
+                const ListState nsl = list_insert(ls, lw, Sh::BM, g.cand_depth, worst, sc[n], (uint32_t)(jc + n),
+                                                  g.sep, g.stride);
+                thr = nsl.thr;
+                worst = nsl.worst;
+              }
+            }
+          }
+        }
+      }
+      if (!kDense && have) {
+        Candidate* out = g.cand + ((size_t)r * g.n_ranges + rg) * g.cand_depth;
+        for (int e = 0; e < g.cand_depth; ++e) out[e] = Candidate{ls[e * Sh::BM], lw[e * Sh::BM]};
+      }
+    }
+  epi_done:;
+  }
+
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    __syncwarp();
+    tc_fence_after();
+    tmem_dealloc(tbase, Sh::TMEM_COLS);
+  }
+}
+
+int gemm_tc_group() { return GemmShape::BM; }
+int gemm_tc_window_tile() { return GemmShape::BN; }
+
+// Shared memory of a launch with `stages` stages and lists of cand_depth.
+static size_t gemm_smem(int stages, int cand_depth) {
+  return 1024 + (size_t)stages * GemmShape::STAGE_BYTES + (size_t)cand_depth * GemmShape::BM * 8;
+}
+
+int gemm_tc_stages(int cand_depth) {
+  int optin = 0, dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  const size_t avail = (size_t)optin > 2048 ? (size_t)optin - 2048 : 0;  // static shared memory
+  for (int s = GemmShape::MAX_STAGES; s >= 2; --s)
+    if (gemm_smem(s, cand_depth) <= avail) return s;
+  return 0;
+}
+
+cudaError_t launch_gemm_tc(const CUtensorMap& tmA, const CUtensorMap& tmB, const GemmArgs& g, bool dense,
+                           int num_sms, cudaStream_t st) {
+  const int64_t n_items = (int64_t)((g.n_rt + g.grp - 1) / g.grp) * g.grp * g.n_ranges;
+  const int grid = (int)(n_items < num_sms ? n_items : num_sms);
+  if (grid < 1) return cudaSuccess;
+  const size_t smem = gemm_smem(g.stages, dense ? 0 : g.cand_depth);
+  auto go = [&](auto kern) -> cudaError_t {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return e;
+    }
+    kern<<<grid, GemmShape::NTHREADS, smem, st>>>(tmA, tmB, g);
+    return cudaGetLastError();
+  };
+  return dense ? go(gemm_tc_kernel<true>) : go(gemm_tc_kernel<false>);
+}
+
+}  // namespace rope

@@ -38,6 +38,9 @@ void host_factor(const rope_params* p, int k, int64_t* a, int64_t* q);
 // reference (same letters, owned by another index) instead of packing ref.
 rope_status encode_reference_impl(const rope_params* p, const uint8_t* ref, int64_t len,
                                   const uint32_t* shared_packed, rope_index** out, cudaStream_t stream);
+// Materialised index (every window's encoding stored; any stride).
+rope_status encode_reference_dense_impl(const rope_params* p, const uint8_t* ref, int64_t len, rope_index** out,
+                                        cudaStream_t stream);
 // Scan + merge for n_reads encoded reads; the result of read r goes to output
 // row out_row[r] (out_row null: row r). prof_slot < 0: no stage timing.
 // A caller-provided candidate buffer for score_topk_impl: used instead of a
@@ -69,4 +72,8 @@ struct rope_index {
   rope::DevIndex ix{};
   rope::EncTables enc{};
   std::vector<void*> owned;
+  // materialised index (rope_encode_reference_dense, or any encoding wider
+  // than the on-the-fly scans take): the window matrix's TMA descriptor
+  bool dense = false;
+  CUtensorMap tm_win{};
 };

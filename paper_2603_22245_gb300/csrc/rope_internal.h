@@ -2,6 +2,7 @@
 // launchers of the other translation units.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -54,6 +55,12 @@ struct MergeArgs {
   float* out_score;
   const int64_t* out_row;  // output row of read r (null: row r)
   int* status;
+  // when the status word already carries the timeout bit (a scan of this call
+  // gave up), write (-1, -inf) for every read instead of merging
+  int32_t empty_on_timeout;
+  // if not null, the status bits of this call (the scan's and the merge's)
+  // are also OR-ed into this word
+  int* sticky_status;
 };
 
 // rope_ladder.cu
@@ -126,6 +133,43 @@ int scan_tc_fits(const DevIndex& ix, int cand_depth, int variant, int fp8);
 
 // rope_merge.cu
 cudaError_t launch_merge(const DevIndex& ix, const MergeArgs& a, cudaStream_t st);
+
+// rope_dense.cu: materialised window index (wide encodings) and its GEMM scan
+struct DenseTables {
+  int32_t n_blk;         // whole blocks of `stride` starts summed per window
+  int32_t t0, n_t;       // tail: window-relative starts [t0, t0 + n_t), signs folded into tph
+  int64_t n_blocks;      // block sums built (W + n_blk - 1)
+  const float2* bph;     // [m * stride] exp(2 pi i f_k i / N), i < stride
+  const float2* rotu;    // [n_blk * m] exp(2 pi i f_k u stride / N)
+  const float2* tph;     // [m * n_t] +-exp(2 pi i f_k (t0 + i) / N)
+};
+// block sums into bsum [n_blocks, D] (scratch), then every window's FP32 row
+// [W, 2D], normalised BF16 row [W, 2D] and 1/|c| [W]
+cudaError_t launch_dense_index(const DevIndex& ix, const DenseTables& dt, float2* bsum, float* win_f32,
+                               uint16_t* win_bf16, float* inv_norm, cudaStream_t st);
+// the scan's A operand [2 n_pad, 2D]: [xr | xi] rows then [-xi | xr] rows
+cudaError_t launch_gemm_a(const uint16_t* emb, int64_t n, int64_t n_pad, int D, uint16_t* a, cudaStream_t st);
+struct GemmArgs {
+  int64_t n_reads;
+  int32_t n_rt;          // read tiles of 128
+  int32_t grp;           // read tiles per wave
+  int32_t n_ranges;      // window ranges (candidate lists per read)
+  int32_t k_blocks;      // 2D / 64
+  int32_t a_im_row0;     // first [-xi | xr] row of the A operand (n_pad)
+  int32_t stages;        // shared-memory pipeline depth
+  int64_t jb, je;        // scanned windows [jb, je)
+  int64_t range_len;     // windows per range (multiple of 128)
+  int32_t cand_depth, sep, stride;
+  Candidate* cand;       // [n_reads, n_ranges, cand_depth]
+  float* dense;          // [n_reads, je - jb] (dense mode)
+  int* status;
+  uint64_t wait_limit_ns;
+};
+int gemm_tc_group();       // reads per tile
+int gemm_tc_window_tile(); // windows per tile
+int gemm_tc_stages(int cand_depth);  // deepest pipeline that fits (0: none)
+cudaError_t launch_gemm_tc(const CUtensorMap& tmA, const CUtensorMap& tmB, const GemmArgs& g, bool dense,
+                           int num_sms, cudaStream_t st);
 
 // rope_rerank.cu
 constexpr int kMaxFeatures = 32;

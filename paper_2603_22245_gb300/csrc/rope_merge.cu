@@ -45,8 +45,20 @@ __global__ void merge_kernel(DevIndex ix, MergeArgs a) {
   const int depth = a.rescore ? a.rescore_depth : a.k;
   const int n_loc = ix.N - ix.s + 1;
   const int D = ix.D;
+  // the scan's lists are incomplete after a timeout: report nothing rather than part
+  const int scan_bits = *reinterpret_cast<volatile int*>(a.status);
+  const bool give_up = a.empty_on_timeout && (scan_bits & kStatusTimeout);
+  if (a.sticky_status && blockIdx.x == 0 && threadIdx.x == 0 && scan_bits) atomicOr(a.sticky_status, scan_bits);
 
   for (int64_t r = (int64_t)blockIdx.x * wpb + warp; r < a.n_reads; r += (int64_t)gridDim.x * wpb) {
+    if (give_up) {
+      const int64_t orow = a.out_row ? a.out_row[r] : r;
+      for (int e = lane; e < a.k; e += 32) {
+        a.out_win[orow * a.k + e] = -1;
+        a.out_score[orow * a.k + e] = -INFINITY;
+      }
+      continue;
+    }
     const Candidate* cands = a.cand + (size_t)r * total;
     uint64_t last = ~0ull;
     int n_sel = 0;
@@ -57,6 +69,12 @@ __global__ void merge_kernel(DevIndex ix, MergeArgs a) {
         const Candidate c = cands[e];
         if (c.win >= kUnusedWin) continue;  // empty entry, or the mark of an unused slot
         if (cands[e - e % a.cand_depth].win == kUnusedWin) continue;  // rest of an unused slot
+        if (c.win >= ix.W) {
+          // no scan writes a window past the index: a corrupt slot, never dereferenced
+          set_status(a.status, kStatusBadArg);
+          set_status(a.sticky_status, kStatusBadArg);
+          continue;
+        }
         const uint64_t key = cand_key(c.score, c.win);
         if (key < last && key > best) best = key;
       }
@@ -81,6 +99,30 @@ __global__ void merge_kernel(DevIndex ix, MergeArgs a) {
         const uint64_t key = __shfl_sync(0xffffffffu, my_key, i);
         const uint32_t jw = 0xFFFFFFFFu - (uint32_t)key;
         const int64_t w0 = (int64_t)jw * ix.stride;
+        if (ix.win_f32) {
+          // materialised index: the window's stored FP32 encoding (§2.1-§2.3
+          // sums, built once) against the read's FP32 encoding
+          const float* cw = ix.win_f32 + (size_t)jw * 2 * D;
+          float re = 0.f, im = 0.f, C = 0.f;
+          for (int g = lane; g < D; g += 32) {
+            const float xr = x[g], xi = x[D + g];
+            const float cr = cw[g], ci = cw[D + g];
+            re = fmaf(xr, cr, fmaf(xi, ci, re));
+            im = fmaf(xr, ci, fmaf(-xi, cr, im));
+            C = fmaf(cr, cr, fmaf(ci, ci, C));
+          }
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) {
+            re += __shfl_xor_sync(0xffffffffu, re, o);
+            im += __shfl_xor_sync(0xffffffffu, im, o);
+            C += __shfl_xor_sync(0xffffffffu, C, o);
+          }
+          const float X = nr[0];
+          const float fid = (X > kZeroNorm2 && C > kZeroNorm2) ? fmaf(re, re, im * im) / (X * C) : 0.f;
+          if (lane == i) my_key = cand_key(fid, jw);
+          __syncwarp();
+          continue;
+        }
         for (int g = lane; g < D; g += 32) acc[g] = make_float2(0.f, 0.f);
         __syncwarp();
         for (int loc0 = 0; loc0 < n_loc; loc0 += 32) {
@@ -173,7 +215,7 @@ cudaError_t launch_merge(const DevIndex& ix, const MergeArgs& a, cudaStream_t st
   const int wpb = 8;
   int64_t blocks = (a.n_reads + wpb - 1) / wpb;
   if (blocks > 152 * 32) blocks = 152 * 32;
-  const size_t smem = (size_t)wpb * ix.D * sizeof(float2);
+  const size_t smem = ix.win_f32 ? 0 : (size_t)wpb * ix.D * sizeof(float2);
   merge_kernel<<<(unsigned)blocks, wpb * 32, smem, st>>>(ix, a);
   return cudaGetLastError();
 }

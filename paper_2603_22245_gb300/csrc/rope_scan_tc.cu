@@ -456,9 +456,10 @@ __global__ void __launch_bounds__(Sh::NTHREADS, 1) scan_tc_kernel(DevIndex ix, S
           }
         }
       }
-      // drain: every MMA issued by this thread has completed
+      // drain: every MMA issued by this thread has completed (waited for even
+      // after an abort, so that tensor memory is freed with no MMA in flight)
       tc_commit(&bar_drain);
-      mbar_wait(&bar_drain, 0, abort_flag, a.status, wlim);
+      mbar_drain_wait(&bar_drain, 0, a.status, wlim);
     }
   } else if (warp == Sh::WARP_PROD) {
     // ================================================================ bulk-copy producer
@@ -482,9 +483,11 @@ __global__ void __launch_bounds__(Sh::NTHREADS, 1) scan_tc_kernel(DevIndex ix, S
         }
         if (!ok) break;
       }
-      // wait for the copies still in flight into either slot (the latest phase of each)
+      // wait for the copies still in flight into either slot (the latest phase
+      // of each), also after an abort: the block's shared memory must not be
+      // released with a copy still writing to it
       for (uint32_t h = (g >= 2 ? g - 2 : 0); h < g; ++h)
-        mbar_wait(&bar_stfull[h & 1], (h >> 1) & 1, abort_flag, a.status, wlim);
+        mbar_drain_wait(&bar_stfull[h & 1], (h >> 1) & 1, a.status, wlim);
     }
   } else if (!Sh::ISOLATE_MMA || (warp & 3) != 0) {
     // ================================================================ window generators

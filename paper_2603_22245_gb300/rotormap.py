@@ -53,9 +53,12 @@ EXPORTS = {
     "rope_last_error": ([], ctypes.c_char_p),
     "rope_dim": ([_P], _I32),
     "rope_sync_status": ([_P], ctypes.c_int),
+    "rope_set_wait_limit": ([ctypes.c_double], ctypes.c_int),
+    "rope_noalloc_sync_status": ([_P], ctypes.c_int),
     "rope_pack_2bit": ([_P, _I64, _P, _P], ctypes.c_int),
     "rope_mer_bins": ([_P, _P, _I64, _P, _P], ctypes.c_int),
     "rope_encode_reference": ([_P, _P, _I64, _P, _P], ctypes.c_int),
+    "rope_encode_reference_dense": ([_P, _P, _I64, _P, _P], ctypes.c_int),
     "rope_index_free": ([_P], None),
     "rope_index_info": ([_P, _P, _P, _P, _P, _P], ctypes.c_int),
     "rope_window_embeddings": ([_P, _I64, _I64, _P, _P], ctypes.c_int),
@@ -161,6 +164,16 @@ def rope_sync_status(stream=None):
     _check(load().rope_sync_status(_stream(stream)))
 
 
+def rope_set_wait_limit(seconds: float):
+    """Bound of every in-kernel wait of later launches (0 restores the default)."""
+    _check(load().rope_set_wait_limit(float(seconds)))
+
+
+def rope_noalloc_sync_status(stream=None):
+    """Raises the status recorded by rope_score_topk_noalloc calls since the last read."""
+    _check(load().rope_noalloc_sync_status(_stream(stream)))
+
+
 def rope_pack_2bit(seq: torch.Tensor, stream=None) -> torch.Tensor:
     out = torch.empty((seq.numel() + 15) // 16, dtype=torch.int32, device=seq.device)
     _check(load().rope_pack_2bit(_ptr(seq), seq.numel(), _ptr(out), _stream(stream)))
@@ -231,6 +244,15 @@ def rope_encode_reference(p: Params, ref: torch.Tensor, stream=None) -> Index:
     h = ctypes.c_void_p()
     pc = p.c()
     _check(load().rope_encode_reference(ctypes.byref(pc), _ptr(ref), ref.numel(), ctypes.byref(h), _stream(stream)))
+    return Index(h.value, p)
+
+
+def rope_encode_reference_dense(p: Params, ref: torch.Tensor, stream=None) -> Index:
+    """The materialised index (every window's FP32 and BF16 encoding stored)."""
+    h = ctypes.c_void_p()
+    pc = p.c()
+    _check(load().rope_encode_reference_dense(ctypes.byref(pc), _ptr(ref), ref.numel(), ctypes.byref(h),
+                                              _stream(stream)))
     return Index(h.value, p)
 
 
@@ -319,12 +341,13 @@ def rope_map(idx: Index, seqs: torch.Tensor, offsets: torch.Tensor, k: int = 8, 
 
 def rope_map_strands(idx: Index, seqs: torch.Tensor, offsets: torch.Tensor, k: int = 8, sep: int = 0,
                      precision="bf16", rescore=None, cand_depth: int = 0, rescore_depth: int = 0, n_ranges: int = 0,
-                     stream=None):
+                     out=None, stream=None):
     """Both strands: (starts [n, k], fidelities [n, k], strand int8 [n, k]: 0 forward, 1 reverse, -1 missing)."""
     n = offsets.numel() - 1
-    out = (torch.empty((n, k), dtype=torch.int64, device=seqs.device),
-           torch.empty((n, k), dtype=torch.float32, device=seqs.device),
-           torch.empty((n, k), dtype=torch.int8, device=seqs.device))
+    if out is None:
+        out = (torch.empty((n, k), dtype=torch.int64, device=seqs.device),
+               torch.empty((n, k), dtype=torch.float32, device=seqs.device),
+               torch.empty((n, k), dtype=torch.int8, device=seqs.device))
     o = _opts(k, sep, precision, rescore, cand_depth, rescore_depth, n_ranges, 0, 0)
     _check(load().rope_map_strands(idx.handle, _ptr(seqs), _ptr(offsets), n, ctypes.byref(o), _ptr(out[0]),
                                    _ptr(out[1]), _ptr(out[2]), _stream(stream)))

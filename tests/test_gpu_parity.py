@@ -1,14 +1,18 @@
 """GPU path vs the FP64 oracle, element by element, through the C ABI.
 
-Tolerances (the arithmetic behind them is in DESIGN.md, "Tolerances"):
+Tolerances:
   * packing, s-mer bins, window indices: bit-exact;
-  * FP32 embeddings: |gpu - oracle| <= 1e-5 * ||oracle vector||;
+  * FP32 embeddings: |gpu - oracle| <= 1e-5 * ||oracle vector|| (FP32 direct
+    sums of at most N unit phases);
   * FP32 scores: |gpu - oracle| <= 1e-5 * fid + 1e-7;
   * BF16 tensor-core scores before re-scoring: |gpu - oracle| <= max(2e-2 * fid, 8e-3 * sqrt(fid) + 2e-5)
-    (BF16 rounding of two unit vectors bounds |d ip| by 2^-8);
+    (each operand is a unit vector rounded to BF16, relative error <= 2^-9 per
+    component, so |d ip| <= 2^-8 and |d fid| <= 2 * 2^-8 * sqrt(fid) + 2^-16);
   * top-k: every oracle top-k window that beats the oracle's (k+1)-th score by
     more than the tolerance is present; reported scores match the oracle's
-    fidelity of the reported window.
+    fidelity of the reported window; the reported best window is the oracle's
+    best wherever the oracle's best beats its second by more than the
+    tolerance (the planted locus is then unique).
 """
 import numpy as np
 import pytest
@@ -40,6 +44,21 @@ def cfg1():
     op = oracle.Params(s=4, m=2, t=2, variant=1, N=150, stride=1)
     w9, s9 = oracle.score_topk(ref, rd.seqs, rd.offsets, op, k=9)
     return dict(ref=ref, rd=rd, op=op, ow=w9, os=s9)
+
+
+@pytest.fixture(scope="module")
+def cfg1_wide(lib):
+    """The same reference with 640 reads: three 256-read groups of the
+    tensor-core scan, the last one ragged (dense parity only)."""
+    ref = synth.uniform_ref(100_000, 1)
+    rd = synth.reads(ref, 640, seed=12)
+    op = oracle.Params(s=4, m=2, t=2, variant=1, N=150, stride=1)
+    p = gparams(op)
+    idx = lib.rope_encode_reference(p, dev(ref))
+    f32, bf16, norms = lib.rope_encode_reads(p, dev(rd.seqs), dev(rd.offsets))
+    lib.rope_sync_status()
+    yield dict(ref=ref, rd=rd, op=op), dict(idx=idx, f32=f32, bf16=bf16, norms=norms)
+    idx.free()
 
 
 @pytest.fixture(scope="module")
@@ -189,50 +208,103 @@ def test_dense_fp32_parity(lib, cfg1, cfg1_gpu, j0, cnt, nr):
     assert np.all(np.abs(got - want) <= f32_tol(want)), np.abs(got - want).max()
 
 
-@pytest.mark.parametrize("j0,cnt,nr", [(0, 2100, 256), (97_000, 2851, 37), (31, 1, 5), (1000, 17, 513)])
+def _bf16_error_summary(tag, got, want):
+    """Observed BF16 error next to its bound: largest relative error where
+    fid >= 0.16 (where the bound is the relative 2e-2) and largest absolute
+    error below (where the sqrt term of the bound is the looser one)."""
+    err = np.abs(got - want)
+    hi = want >= 0.16
+    rel_hi = (err[hi] / want[hi]).max() if hi.any() else float("nan")
+    abs_lo = err[~hi].max() if (~hi).any() else float("nan")
+    frac = (err / bf16_tol(want)).max()
+    print(f"BF16-ERR {tag}: n={err.size} fid>=0.16: {int(hi.sum())} max rel {rel_hi:.3e}; "
+          f"fid<0.16: max abs {abs_lo:.3e}; max err/bound {frac:.3f}")
+
+
+@pytest.mark.parametrize("j0,cnt,nr", [(0, 2100, 256), (97_000, 2851, 37), (31, 1, 5)])
 def test_dense_bf16_parity(lib, cfg1, cfg1_gpu, j0, cnt, nr):
-    if nr > 256:
-        pytest.skip("needs more reads than the fixture")
     got, want = _dense_case(lib, cfg1, cfg1_gpu, "bf16", j0, cnt, nr)
     assert not np.isnan(got).any()
+    _bf16_error_summary(f"dense j0={j0} cnt={cnt} reads={nr}", got, want)
     err = np.abs(got - want)
     assert np.all(err <= bf16_tol(want)), (err.max(), (err / np.maximum(want, 1e-9)).max())
 
 
+@pytest.mark.parametrize("precision", ["bf16", "fp32"])
+@pytest.mark.parametrize("j0,cnt,nr", [(1000, 17, 513), (50_000, 700, 640)])
+def test_dense_parity_several_read_groups(lib, cfg1_wide, precision, j0, cnt, nr):
+    """More than two 256-read groups of the tensor-core scan (the last ragged),
+    each compared element by element with the oracle."""
+    host, g = cfg1_wide
+    got, want = _dense_case(lib, host, g, precision, j0, cnt, nr)
+    assert not np.isnan(got).any()
+    err = np.abs(got - want)
+    if precision == "bf16":
+        _bf16_error_summary(f"dense j0={j0} cnt={cnt} reads={nr}", got, want)
+        assert np.all(err <= bf16_tol(want)), (err.max(), (err / np.maximum(want, 1e-9)).max())
+    else:
+        assert np.all(err <= f32_tol(want)), err.max()
+
+
 # ---------------------------------------------------------------- a5-a7: top-k
+
+def _check_top1(gw, ow, os_, tol_fn):
+    """The reported best window is the oracle's best wherever the oracle's best
+    beats its second by more than the tolerance (there it is unique); returns
+    the mask of those reads."""
+    clear = os_[:, 0] - os_[:, 1] > tol_fn(os_[:, 0])
+    bad = np.nonzero(clear & (gw[:, 0] != ow[:, 0]))[0]
+    assert bad.size == 0, (bad[:10], gw[bad[:10], 0], ow[bad[:10], 0])
+    return clear
+
 
 def test_topk_fp32_config1(lib, cfg1, cfg1_gpu):
     g = cfg1_gpu
     gw, gs = lib.rope_score_topk(g["idx"], g["f32"], None, g["norms"], k=8, precision="fp32")
     lib.rope_sync_status()
-    check_topk(cfg1["ref"], cfg1["rd"], cfg1["op"], gw.cpu().numpy(), gs.cpu().numpy().astype(np.float64),
-               cfg1["ow"], cfg1["os"], 8, f32_tol)
+    gw, gs = gw.cpu().numpy(), gs.cpu().numpy().astype(np.float64)
+    check_topk(cfg1["ref"], cfg1["rd"], cfg1["op"], gw, gs, cfg1["ow"], cfg1["os"], 8, f32_tol)
+    assert _check_top1(gw, cfg1["ow"], cfg1["os"], f32_tol).mean() > 0.9
 
 
 def test_topk_bf16_rescored_config1(lib, cfg1, cfg1_gpu):
     g = cfg1_gpu
     gw, gs = lib.rope_score_topk(g["idx"], g["f32"], g["bf16"], g["norms"], k=8, precision="bf16", rescore=1)
     lib.rope_sync_status()
-    check_topk(cfg1["ref"], cfg1["rd"], cfg1["op"], gw.cpu().numpy(), gs.cpu().numpy().astype(np.float64),
-               cfg1["ow"], cfg1["os"], 8, bf16_tol, f32_tol)
+    gw, gs = gw.cpu().numpy(), gs.cpu().numpy().astype(np.float64)
+    check_topk(cfg1["ref"], cfg1["rd"], cfg1["op"], gw, gs, cfg1["ow"], cfg1["os"], 8, bf16_tol, f32_tol)
+    # the BF16 scan only proposes candidates; once re-scored the top-1 is
+    # decided in FP32, so it must be exact wherever the FP32 tolerance clears it
+    assert _check_top1(gw, cfg1["ow"], cfg1["os"], f32_tol).mean() > 0.9
 
 
 def test_topk_bf16_raw_config1(lib, cfg1, cfg1_gpu):
     g = cfg1_gpu
     gw, gs = lib.rope_score_topk(g["idx"], g["f32"], g["bf16"], g["norms"], k=8, precision="bf16", rescore=0)
     lib.rope_sync_status()
-    check_topk(cfg1["ref"], cfg1["rd"], cfg1["op"], gw.cpu().numpy(), gs.cpu().numpy().astype(np.float64),
-               cfg1["ow"], cfg1["os"], 8, bf16_tol)
+    gw, gs = gw.cpu().numpy(), gs.cpu().numpy().astype(np.float64)
+    check_topk(cfg1["ref"], cfg1["rd"], cfg1["op"], gw, gs, cfg1["ow"], cfg1["os"], 8, bf16_tol)
+    # raw BF16 scores decide the order: exact only where the gap exceeds the
+    # BF16 tolerance (a minority here: a window one letter off the planted
+    # start typically scores within 1% of it)
+    _check_top1(gw, cfg1["ow"], cfg1["os"], bf16_tol)
 
 
 @pytest.mark.parametrize("precision", ["fp32", "bf16"])
 def test_topk_planted_accuracy(lib, cfg1, cfg1_gpu, precision):
+    """Planted loci: wherever the oracle's top-1 is clear of its second by the
+    tolerance, the GPU finds exactly the oracle's window, so it hits the
+    planted locus exactly when the oracle does; elsewhere (near ties) the two
+    may pick different windows of equal score."""
     g = cfg1_gpu
     gw, _ = lib.rope_score_topk(g["idx"], g["f32"], g["bf16"], g["norms"], k=1, precision=precision)
-    hit = np.abs(gw.cpu().numpy()[:, 0] - cfg1["rd"].true_pos) < 150
+    gw = gw.cpu().numpy()
+    hit = np.abs(gw[:, 0] - cfg1["rd"].true_pos) < 150
     ora = np.abs(cfg1["ow"][:, 0] - cfg1["rd"].true_pos) < 150
+    clear = _check_top1(gw, cfg1["ow"], cfg1["os"], f32_tol)  # BF16 results are re-scored in FP32
+    assert np.array_equal(hit[clear], ora[clear])
     assert hit.mean() >= 0.97
-    assert abs(hit.mean() - ora.mean()) <= 1.0 / 256 + 1e-12
+    assert abs(hit.mean() - ora.mean()) <= (~clear).sum() / 256 + 1e-12
 
 
 @pytest.mark.parametrize("precision", ["fp32", "bf16"])
