@@ -95,14 +95,16 @@ WORKLOADS = {
              "index scored by the BF16 tcgen05 GEMM, FP32 re-scoring, top-8",
         L=3_100_000_000, gc=0.41, tandem=0.0, segdup=0.0, inter=0.50, ref_seed=7,
         n_reads=96_000, read_len=20000, sub=0.05, indel=0.10, read_seed=10,
-        s=8, m=4, t=4, variant=1, N=20000, stride=1250, k=8, strands=True, batch=24_000),
+        s=8, m=4, t=4, variant=1, N=20000, stride=1250, k=8, strands=True, batch=24_000, cpu_reads=16,
+        cpu_windows=3000),
     "markov300M_20k": dict(
         desc="300 Mbp order-2 Markov reference (GC 41%, 2.5% tandem repeats, 2.5% segmental duplicates), 8192 planted "
              "20 kbp reads at 15% errors, both strands, s=8 m=4 t=4 (d=2048), N=20000, step 1250, top-8 (a one-batch "
              "case of the long-read configuration small enough for ncu captures)",
         L=300_000_000, gc=0.41, tandem=0.025, segdup=0.025, inter=0.0, ref_seed=3,
         n_reads=8192, read_len=20000, sub=0.05, indel=0.10, read_seed=11,
-        s=8, m=4, t=4, variant=1, N=20000, stride=1250, k=8, strands=True, batch=8192),
+        s=8, m=4, t=4, variant=1, N=20000, stride=1250, k=8, strands=True, batch=8192, cpu_reads=16,
+        cpu_windows=3000),
     "uniform100k": dict(
         desc="100 kbp uniform reference, 256 x 150 bp planted reads (1% sub, 0.5% indel), d=64, stride 1, top-8",
         L=100_000, gc=None, ref_seed=1, n_reads=256, read_len=150, sub=0.01, indel=0.005, read_seed=2,
@@ -261,8 +263,9 @@ def cpu_baseline(ref, rd, wl, n_reads, n_windows):
     t0 = time.perf_counter()
     oracle.score_topk(ref, sub.seqs, sub.offsets, op, k=wl["k"], j_begin=0, j_end=n_windows, n_threads=cores)
     dt = time.perf_counter() - t0
-    # the oracle's full-DP Levenshtein distance (reranker labels) on all cores
-    n_ld = 100_000
+    # the oracle's full-DP Levenshtein distance (reranker labels) on all cores,
+    # about 2e9 DP cells
+    n_ld = max(16, int(2.25e9 // (wl["N"] * wl["N"])))
     rng = np.random.default_rng(0)
     ri = rng.integers(0, rd.n, n_ld)
     ws = rng.integers(0, len(ref) - wl["N"], n_ld)
@@ -736,7 +739,7 @@ def main():
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu:
-        cpu = cpu_baseline(ref, rd, wl, args.cpu_reads, args.cpu_windows)
+        cpu = cpu_baseline(ref, rd, wl, wl.get("cpu_reads", args.cpu_reads), wl.get("cpu_windows", args.cpu_windows))
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,

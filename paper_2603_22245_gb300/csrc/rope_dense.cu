@@ -174,8 +174,9 @@ __global__ void __launch_bounds__(256) dense_windows_kernel(DevIndex ix, DenseTa
 
 cudaError_t launch_dense_index(const DevIndex& ix, const DenseTables& dt, float2* bsum, float* win_f32,
                                uint16_t* win_bf16, float* inv_norm, cudaStream_t st) {
-  {
-    const int wpb = 8;
+  if (dt.n_blocks > 0) {
+    int wpb = (int)((96 * 1024) / ((size_t)ix.D * sizeof(float2)));  // accumulators within 96 KB
+    wpb = wpb < 1 ? 1 : wpb > 8 ? 8 : wpb;
     const size_t smem = (size_t)wpb * ix.D * sizeof(float2);
     if (smem > 48 * 1024) {
       cudaError_t e = cudaFuncSetAttribute(block_sums_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
