@@ -105,6 +105,22 @@ WORKLOADS = {
         n_reads=8192, read_len=20000, sub=0.05, indel=0.10, read_seed=11,
         s=8, m=4, t=4, variant=1, N=20000, stride=1250, k=8, strands=True, batch=8192, cpu_reads=16,
         cpu_windows=3000),
+    "human30M_20k_thr": dict(
+        desc="threshold regime (multi-locus output) on a 30 Mbp human-shaped order-2 Markov genome (GC 41%, 50% "
+             "interspersed repeats), 2000 planted 20 kbp reads at 15% per-letter edits split evenly between "
+             "substitutions, insertions and deletions (the thresholds' own mutation model), s=8 m=4 t=4 (d=2048), "
+             "N=20000, step 1250; per-window thresholds from 8 mutated copies for rates 0.15, 0.20, 0.25; every "
+             "(read, window) pair reaching its window's threshold",
+        L=30_000_000, gc=0.41, tandem=0.0, segdup=0.0, inter=0.50, ref_seed=12,
+        n_reads=2000, read_len=20000, sub=0.05, indel=0.10, geom_p=1.0, read_seed=13,
+        s=8, m=4, t=4, variant=1, N=20000, stride=1250, k=8, threshold=dict(errs=[0.15, 0.20, 0.25], n_samples=8)),
+    "markov10M_d128_thr": dict(
+        desc="threshold regime on a 10 Mbp order-2 Markov reference (GC 41%, 2.5% tandem repeats, 2.5% segmental "
+             "duplicates), 2000 planted 150 bp reads at 15% per-letter edits split evenly (substitutions, insertions, "
+             "deletions), s=4 m=4 t=2 (d=128), N=150, stride 1; thresholds from 8 copies for rates 0.15, 0.20, 0.25",
+        L=10_000_000, gc=0.41, tandem=0.025, segdup=0.025, inter=0.0, ref_seed=5,
+        n_reads=2000, read_len=150, sub=0.05, indel=0.10, geom_p=1.0, read_seed=14,
+        s=4, m=4, t=2, variant=1, N=150, stride=1, k=8, threshold=dict(errs=[0.15, 0.20, 0.25], n_samples=8)),
     "uniform100k": dict(
         desc="100 kbp uniform reference, 256 x 150 bp planted reads (1% sub, 0.5% indel), d=64, stride 1, top-8",
         L=100_000, gc=None, ref_seed=1, n_reads=256, read_len=150, sub=0.01, indel=0.005, read_seed=2,
@@ -142,8 +158,9 @@ def make_inputs(wl, rank):
     else:
         ref = synth.markov_ref(wl["L"], wl["gc"], wl["ref_seed"], wl["tandem"], wl["segdup"], wl["inter"])
     rd = synth.reads(ref, wl["n_reads"], seed=wl["read_seed"] + 1000 * rank, length=wl["read_len"],
-                     sub_rate=wl["sub"], indel_rate=wl["indel"], lognormal_sigma=wl.get("sigma"),
-                     len_min=wl.get("len_min", 100), len_max=wl.get("len_max", 10000))
+                     sub_rate=wl["sub"], indel_rate=wl["indel"], geom_p=wl.get("geom_p", 0.7),
+                     lognormal_sigma=wl.get("sigma"), len_min=wl.get("len_min", 100),
+                     len_max=wl.get("len_max", 10000))
     if wl.get("strands"):
         rd = reverse_every_other(rd)
     return ref, rd
@@ -497,6 +514,75 @@ def run_ladder(args, wl):
         dist.destroy_process_group()
 
 
+def locus_stats(reads, wins, true_pos, n_reads, stride, N):
+    """§3.5 multi-locus output per read: loci = runs of output windows whose
+    starts lie within N of the previous one (overlapping windows of one
+    locus); unique = exactly one locus; missed = no output window within N of
+    the planted start."""
+    order = np.lexsort((wins, reads))
+    r, w = reads[order], wins[order] * stride
+    loci = np.zeros(n_reads, dtype=np.int64)
+    hit = np.zeros(n_reads, dtype=bool)
+    if len(r):
+        new = np.ones(len(r), dtype=bool)
+        new[1:] = (r[1:] != r[:-1]) | (w[1:] - w[:-1] > N)
+        np.add.at(loci, r[new], 1)
+        near = np.abs(w - true_pos[r]) < N
+        hit[np.unique(r[near])] = True
+    return {"loci_per_read": float(loci.mean()), "unique_fraction": float(np.mean(loci == 1)),
+            "missed_fraction": float(np.mean(~hit)), "pairs_per_read": len(reads) / n_reads,
+            "reads_without_output": float(np.mean(loci == 0))}
+
+
+def run_threshold(args, wl):
+    """Threshold regime: thresholds for every window, then every pair reaching
+    its window's threshold; the paper's §3.5 quantities per read."""
+    import torch
+
+    from paper_2603_22245_gb300 import rotormap as rm
+
+    rm.load()
+    ref, rd = make_inputs(wl, 0)
+    p = rm.Params(s=wl["s"], m=wl["m"], t=wl["t"], variant=wl["variant"], window_len=wl["N"], stride=wl["stride"])
+    idx = rm.rope_encode_reference(p, torch.from_numpy(ref).cuda())
+    W = idx.n_windows
+    th = wl["threshold"]
+    _, bf16, _ = rm.rope_encode_reads(p, torch.from_numpy(rd.seqs).cuda(), torch.from_numpy(rd.offsets).cuda(),
+                                      want_f32=False)
+    cap = 1 << 26
+    sweep = []
+    ms = None
+    for err in th["errs"]:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        thr = rm.rope_fragment_thresholds(idx, err, th["n_samples"], 12345)
+        torch.cuda.synchronize()
+        t_thr = time.perf_counter() - t0
+        rm.rope_score_threshold(idx, bf16, thr, cap=cap)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(args.steps):
+            r, w, s, total = rm.rope_score_threshold(idx, bf16, thr, cap=cap)
+        e1.record()
+        torch.cuda.synchronize()
+        rm.rope_sync_status()
+        ms = e0.elapsed_time(e1) / args.steps if ms is None else ms
+        stats = locus_stats(r.cpu().numpy(), w.cpu().numpy(), rd.true_pos, rd.n, wl["stride"], wl["N"])
+        thr_h = thr.cpu().numpy()
+        sweep.append(dict(stats, err=err, n_samples=th["n_samples"], pairs=int(total),
+                          pairs_dropped=int(max(0, total - cap)), threshold_s=t_thr,
+                          threshold_windows_per_s=W / t_thr, threshold_mean=float(thr_h.mean()),
+                          threshold_p10_p90=[float(np.percentile(thr_h, 10)), float(np.percentile(thr_h, 90))]))
+    line = {"metric": METRIC, "value": rd.n * W / (ms / 1000.0), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": 1, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "bf16", "data": "synthetic",
+            "config": {"workload": args.workload + ": " + wl["desc"], "reads": rd.n, "n_windows": W},
+            "threshold_regime": sweep, "gpu_launches": 2 * args.steps * len(sweep)}
+    print(json.dumps(line), flush=True)
+    idx.free()
+
+
 def main():
     args = parse()
     wl = WORKLOADS[args.workload]
@@ -505,6 +591,9 @@ def main():
         return
     if "ladder" in wl:
         run_ladder(args, wl)
+        return
+    if "threshold" in wl:
+        run_threshold(args, wl)
         return
 
     import torch

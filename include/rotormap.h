@@ -317,12 +317,33 @@ rope_status rope_map(const rope_index* idx, const uint8_t* seqs, const int64_t* 
  * *out_count (device); the first min(count, cap) of them, in no particular
  * order, to out_read / out_win (window number j; start j*stride) /
  * out_score (device). A count above cap means pairs were dropped: call
- * again with a larger cap. Score mode 0, d = 64 (tile variant 0) or 128. */
+ * again with a larger cap. Score mode 0, d = 64 (tile variant 0) or 128, or
+ * a materialised index of any dimension. */
 rope_status rope_fragment_thresholds(const rope_index* idx, double err, int32_t n_samples, uint64_t seed,
                                      int64_t j_begin, int64_t count, float* out, cudaStream_t stream);
+/* On a materialised index (rope_encode_reference_dense) both calls take any
+ * complex dimension: the copies are walked on the GPU, encoded by the read
+ * encoder and compared with the windows' stored FP32 rows (pool scratch of
+ * at most about 2 GB, a chunk of windows at a time), and the pairs come from
+ * the GEMM scan's threshold mode. */
 rope_status rope_score_threshold(const rope_index* idx, const uint16_t* emb_bf16, int64_t n_reads, const float* thr,
                                  int64_t j_begin, int64_t j_end, int64_t cap, int64_t* out_read, int64_t* out_win,
                                  float* out_score, unsigned long long* out_count, cudaStream_t stream);
+
+/* ---- scoring of correlations (§2.4) ---------------------------------------
+ * For each string i (seqs[offsets[i], offsets[i+1]) on the device, at least
+ * N = p->window_len letters of A,C,G,T): the fidelity (p's score mode) between
+ * the encoding of its first N letters and the encoding of its mutated copy at
+ * rate errs[i] (double, device). The copy is the first N letters of the walk
+ * of the threshold regime over the string (each letter mutated with
+ * probability errs[i]: deleted, preceded by a random inserted letter, or
+ * substituted, 1/3 each; A past the string's end), its draws the SplitMix64
+ * stream keyed by output i of the generator started at `seed`. These are the
+ * samples of the paper's fitting curve (mean fidelity per mutation rate,
+ * inverted to predict the rate). Any complex dimension; FP32 encodings and
+ * products. out_fid: n floats (device). Pool scratch: n*(N + 16*D + 8) bytes. */
+rope_status rope_pair_fidelities(const rope_params* p, const uint8_t* seqs, const int64_t* offsets, int64_t n,
+                                 const double* errs, uint64_t seed, float* out_fid, cudaStream_t stream);
 
 /* ---- refinement (§3.4, increasing the accuracy) -------------------------
  * Slides the window one letter at a time around coarse candidates and scores

@@ -752,6 +752,51 @@ extern "C" rope_status rope_encode_reads(const rope_params* p, const uint8_t* se
   return ROPE_OK;
 }
 
+// ---------------------------------------------------------------- §2.4 pair fidelities
+
+extern "C" rope_status rope_pair_fidelities(const rope_params* p, const uint8_t* seqs, const int64_t* offsets,
+                                            int64_t n, const double* errs, uint64_t seed, float* out_fid,
+                                            cudaStream_t stream) {
+  rope_status st = check_params(p);
+  if (st != ROPE_OK) return st;
+  if (n < 0) return fail(ROPE_ERR_INVALID_ARG, "n < 0");
+  if (n == 0) return ROPE_OK;
+  if (!seqs || !offsets || !errs || !out_fid) return fail(ROPE_ERR_INVALID_ARG, "NULL pointer");
+  DeviceCtx* c;
+  if ((st = get_ctx(&c)) != ROPE_OK) return st;
+  EncTables tb;
+  if ((st = get_enc_tables(*p, &tb)) != ROPE_OK) return st;
+  const int N = p->window_len, D = tb.D, m = tb.m;
+  auto al = [](size_t b) { return (b + 255) & ~size_t(255); };
+  const size_t b_copy = al((size_t)n * N), b_off = al((size_t)(n + 1) * sizeof(int64_t));
+  const size_t b_emb = al((size_t)2 * n * 2 * D * sizeof(float)), b_norm = al((size_t)2 * n * (1 + m) * sizeof(float));
+  uint8_t* scratch = nullptr;
+  if ((st = pool_alloc(c, (void**)&scratch, b_copy + b_off + b_emb + b_norm, stream)) != ROPE_OK) return st;
+  uint8_t* copies = scratch;
+  int64_t* coff = reinterpret_cast<int64_t*>(scratch + b_copy);
+  float* emb = reinterpret_cast<float*>(scratch + b_copy + b_off);
+  float* norms = reinterpret_cast<float*>(scratch + b_copy + b_off + b_emb);
+  MutArgs ma{};
+  ma.seqs = seqs;
+  ma.offsets = offsets;
+  ma.errs = errs;
+  ma.n = n;
+  ma.N = N;
+  ma.seed = seed;
+  ma.out = copies;
+  ma.status = c->status;
+  cudaError_t e = launch_mutate(ma, stream);
+  if (e == cudaSuccess) e = launch_iota_offsets(coff, n, N, stream);
+  if (e == cudaSuccess) e = launch_encode_reads(tb, seqs, offsets, n, emb, nullptr, norms, c->status, stream);
+  if (e == cudaSuccess)
+    e = launch_encode_reads(tb, copies, coff, n, emb + (size_t)n * 2 * D, nullptr, norms + (size_t)n * (1 + m),
+                            c->status, stream);
+  if (e == cudaSuccess) e = launch_pair_fidelity(emb, norms, n, D, m, tb.nb, p->score_mode, out_fid, stream);
+  cudaFreeAsync(scratch, stream);
+  if (e != cudaSuccess) return fail(ROPE_ERR_CUDA, "pair fidelities launch: %s", cudaGetErrorString(e));
+  return ROPE_OK;
+}
+
 // ---------------------------------------------------------------- scan
 
 namespace {
@@ -1024,7 +1069,8 @@ namespace {
 rope_status dense_scan(const rope_index* idx, const uint16_t* emb_bf16, const float* emb_f32, const float* norms,
                        int64_t n_reads, const rope_score_opts& o, int64_t jb, int64_t je, int64_t* out_win,
                        float* out_score, float* dense_out, cudaStream_t stream, int prof_slot,
-                       const int64_t* out_row) {
+                       const int64_t* out_row, const ThrOut* thr_out = nullptr) {
+  const int mode = thr_out ? 2 : dense_out ? 1 : 0;
   const DevIndex& ix = idx->ix;
   if (o.precision != ROPE_PREC_BF16)
     return fail(ROPE_ERR_UNSUPPORTED, "a materialised index is scored by the BF16 tensor-core GEMM (precision %d)",
@@ -1052,11 +1098,11 @@ rope_status dense_scan(const rope_index* idx, const uint16_t* emb_bf16, const fl
   if (n_ranges > n_wt) n_ranges = (int)std::max<int64_t>(1, n_wt);
   const int64_t tiles_per_range = n_wt > 0 ? (n_wt + n_ranges - 1) / n_ranges : 1;
   if (n_wt > 0) n_ranges = (int)((n_wt + tiles_per_range - 1) / tiles_per_range);
-  const int stages = gemm_tc_stages(dense_out ? 0 : o.cand_depth);
+  const int stages = gemm_tc_stages(mode == 0 ? o.cand_depth : 0);
   if (stages < 2) return fail(ROPE_ERR_UNSUPPORTED, "cand_depth=%d: the GEMM scan does not fit in shared memory", o.cand_depth);
   auto al = [](size_t b) { return (b + 255) & ~size_t(255); };
   const size_t a_bytes = al((size_t)2 * n_pad * 2 * ix.D * sizeof(uint16_t));
-  const size_t cand_bytes = dense_out ? 0 : (size_t)n_reads * n_ranges * o.cand_depth * sizeof(Candidate);
+  const size_t cand_bytes = mode != 0 ? 0 : (size_t)n_reads * n_ranges * o.cand_depth * sizeof(Candidate);
   uint8_t* scratch = nullptr;
   if ((st = pool_alloc(c, (void**)&scratch, a_bytes + cand_bytes, stream)) != ROPE_OK) return st;
   uint16_t* a_op = reinterpret_cast<uint16_t*>(scratch);
@@ -1082,20 +1128,21 @@ rope_status dense_scan(const rope_index* idx, const uint16_t* emb_bf16, const fl
     g.jb = jb;
     g.je = je;
     g.range_len = tiles_per_range * BN;
-    g.cand_depth = dense_out ? 1 : o.cand_depth;
+    g.cand_depth = mode == 0 ? o.cand_depth : 1;
     g.sep = o.sep;
     g.stride = ix.stride;
-    g.cand = dense_out ? nullptr : cand;
+    g.cand = mode == 0 ? cand : nullptr;
     g.dense = dense_out;
     g.status = c->status;
     g.wait_limit_ns = wait_limit_ns();
-    e = launch_gemm_tc(tmA, idx->tm_win, g, dense_out != nullptr, c->num_sms, stream);
+    if (thr_out) g.thr = *thr_out;
+    e = launch_gemm_tc(tmA, idx->tm_win, g, mode, c->num_sms, stream);
     if (e != cudaSuccess) return release(fail(ROPE_ERR_CUDA, "GEMM scan launch: %s", cudaGetErrorString(e)));
-  } else if (!dense_out) {
+  } else if (mode == 0) {
     e = cudaMemsetAsync(cand, 0xFF, cand_bytes, stream);  // every slot empty
     if (e != cudaSuccess) return release(fail(ROPE_ERR_CUDA, "cudaMemsetAsync: %s", cudaGetErrorString(e)));
   }
-  if (dense_out) return release(ROPE_OK);
+  if (mode != 0) return release(ROPE_OK);
   prof_mark(prof_slot, 2, stream);
   MergeArgs m{};
   m.cand = cand;
@@ -1311,6 +1358,15 @@ extern "C" rope_status rope_score_threshold(const rope_index* idx, const uint16_
   ROPE_CUDA(cudaMemsetAsync(out_count, 0, sizeof(unsigned long long), stream));
   if (n_reads == 0 || je <= jb) return ROPE_OK;
   if (!emb_bf16) return fail(ROPE_ERR_INVALID_ARG, "threshold scan needs emb_bf16");
+  if (idx->dense) {
+    rope_score_opts o{};
+    o.k = 1;
+    o.precision = ROPE_PREC_BF16;
+    o.cand_depth = 1;
+    const ThrOut to{thr, out_count, cap, out_read, out_win, out_score};
+    return dense_scan(idx, emb_bf16, nullptr, nullptr, n_reads, o, jb, je, nullptr, nullptr, nullptr, stream, -1,
+                      nullptr, &to);
+  }
   DeviceCtx* c;
   rope_status st = get_ctx(&c);
   if (st != ROPE_OK) return st;

@@ -62,6 +62,20 @@ __device__ __forceinline__ uint64_t globaltimer_ns() {
 
 constexpr uint64_t kWaitLimitNs = 2000000000ull;  // 2 s per wait
 
+// ---------------------------------------------------------------- SplitMix64
+
+// Output i (0-based) of the SplitMix64 generator started at `seed` (Steele,
+// Lea and Flood, 2014): the state advances by the golden-ratio increment and
+// each output is the state passed through the published 64-bit finaliser.
+__device__ __forceinline__ uint64_t sm64_out(uint64_t seed, uint64_t i) {
+  uint64_t z = seed + (i + 1) * 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+// the top 53 bits as a double in [0, 1)
+__device__ __forceinline__ double sm64_unit(uint64_t z) { return (double)(z >> 11) * (1.0 / 9007199254740992.0); }
+
 // ---------------------------------------------------------------- letters
 
 // A,C,G,T (either case) -> 0..3, else 4

@@ -277,10 +277,14 @@ __device__ __forceinline__ bool gemm_item(const GemmArgs& g, int64_t it, int& rt
   return rt < g.n_rt;
 }
 
-template <bool kDense>
+// kMode 0: per-read candidate lists (top-k); 1: every score into g.dense;
+// 2: every pair whose score reaches its window's threshold g.thr.thr[j],
+// appended at an atomically taken index of g.thr's bounded arrays.
+template <int kMode>
 __global__ void __launch_bounds__(GemmShape::NTHREADS, 1)
     gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, GemmArgs g) {
   using Sh = GemmShape;
+  constexpr bool kDense = kMode == 1, kThr = kMode == 2, kLists = kMode == 0;
   extern __shared__ __align__(1024) uint8_t gm_raw[];
   __shared__ __align__(8) uint64_t bar_full[Sh::MAX_STAGES], bar_empty[Sh::MAX_STAGES];
   __shared__ __align__(8) uint64_t bar_accfull[2], bar_accempty[2], bar_drain;
@@ -418,7 +422,7 @@ __global__ void __launch_bounds__(GemmShape::NTHREADS, 1)
       const bool have = r < g.n_reads;
       float thr = -INFINITY;
       int worst = 0;
-      if (!kDense) {
+      if (kLists) {
         for (int e = 0; e < g.cand_depth; ++e) {
           ls[e * Sh::BM] = -INFINITY;
           lw[e * Sh::BM] = kEmptyWin;
@@ -446,7 +450,32 @@ __global__ void __launch_bounds__(GemmShape::NTHREADS, 1)
 #pragma unroll
           for (int n = 0; n < 16; n += 2) abs2_pair(vr[n], vr[n + 1], vi[n], vi[n + 1], sc[n], sc[n + 1]);
           const int64_t jc = w0 + c0;
-          if constexpr (kDense) {
+          if constexpr (kThr) {
+            // lane l holds the threshold of window jc + (l & 15) (+inf outside
+            // the range); the chunk's smallest threshold decides whether any
+            // of its 16 scores needs a look
+            const float tl = (jc + (lane & 15) < w_hi) ? __ldg(g.thr.thr + jc + (lane & 15)) : INFINITY;
+            float mn = tl;
+#pragma unroll
+            for (int o = 8; o > 0; o >>= 1) mn = fminf(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+            float mx = sc[0];
+#pragma unroll
+            for (int n = 1; n < 16; ++n) mx = fmaxf(mx, sc[n]);
+            if (__any_sync(0xffffffffu, have && mx >= mn)) {
+#pragma unroll
+              for (int n = 0; n < 16; ++n) {
+                const float th = __shfl_sync(0xffffffffu, tl, n);
+                if (have && sc[n] >= th) {
+                  const unsigned long long slot = atomicAdd(g.thr.count, 1ull);
+                  if (slot < (unsigned long long)g.thr.cap) {
+                    g.thr.read[slot] = r;
+                    g.thr.win[slot] = jc + n;
+                    g.thr.score[slot] = sc[n];
+                  }
+                }
+              }
+            }
+          } else if constexpr (kDense) {
             if (have) {
 #pragma unroll
               for (int n = 0; n < 16; ++n)
@@ -474,7 +503,7 @@ __global__ void __launch_bounds__(GemmShape::NTHREADS, 1)
           }
         }
       }
-      if (!kDense && have) {
+      if (kLists && have) {
         Candidate* out = g.cand + ((size_t)r * g.n_ranges + rg) * g.cand_depth;
         for (int e = 0; e < g.cand_depth; ++e) out[e] = Candidate{ls[e * Sh::BM], lw[e * Sh::BM]};
       }
@@ -512,12 +541,12 @@ int gemm_tc_stages(int cand_depth) {
   return 0;
 }
 
-cudaError_t launch_gemm_tc(const CUtensorMap& tmA, const CUtensorMap& tmB, const GemmArgs& g, bool dense,
+cudaError_t launch_gemm_tc(const CUtensorMap& tmA, const CUtensorMap& tmB, const GemmArgs& g, int mode,
                            int num_sms, cudaStream_t st) {
   const int64_t n_items = (int64_t)((g.n_rt + g.grp - 1) / g.grp) * g.grp * g.n_ranges;
   const int grid = (int)(n_items < num_sms ? n_items : num_sms);
   if (grid < 1) return cudaSuccess;
-  const size_t smem = gemm_smem(g.stages, dense ? 0 : g.cand_depth);
+  const size_t smem = gemm_smem(g.stages, mode == 0 ? g.cand_depth : 0);
   auto go = [&](auto kern) -> cudaError_t {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) {
@@ -527,7 +556,7 @@ cudaError_t launch_gemm_tc(const CUtensorMap& tmA, const CUtensorMap& tmB, const
     kern<<<grid, GemmShape::NTHREADS, smem, st>>>(tmA, tmB, g);
     return cudaGetLastError();
   };
-  return dense ? go(gemm_tc_kernel<true>) : go(gemm_tc_kernel<false>);
+  return mode == 1 ? go(gemm_tc_kernel<1>) : mode == 2 ? go(gemm_tc_kernel<2>) : go(gemm_tc_kernel<0>);
 }
 
 }  // namespace rope

@@ -234,28 +234,40 @@ __global__ void encode_reads_kernel(EncTables tb, const uint8_t* __restrict__ se
   }
 }
 
-// Encodings wider than kMaxScanDim complex entries: the accumulator in shared
-// memory, updated by the lane of each band for one location at a time.
+// Encodings wider than kMaxScanDim complex entries, or heads whose phase table
+// exceeds what one block stages: one warp per read head, its D complex entries
+// in shared memory. Locations are taken 32 at a time, one per lane; lanes whose
+// locations fall in the same bin form a group (__match_any_sync), and the
+// group's lowest lane (its first location) sums the group's phases in
+// location order and adds that sum to the entry, so each entry receives one
+// update per 32 locations, in location order (deterministic FP32 sums of the
+// §2.1-§2.3 direct sum). The phases of kEncChunk locations are staged in
+// shared memory once per block for all of its warps.
+constexpr int kEncChunk = 1024;
+
 __global__ void encode_reads_wide_kernel(EncTables tb, const uint8_t* __restrict__ seqs,
                                     const int64_t* __restrict__ offsets, int64_t n, float* __restrict__ emb_f32,
                                     __nv_bfloat16* __restrict__ emb_bf16, float* __restrict__ norms, int* status,
                                     const int64_t* __restrict__ perm, bool rc) {
-  extern __shared__ float2 enc_acc[];
+  extern __shared__ float2 enc_sm[];
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
   const int wpb = blockDim.x >> 5;
-  float2* acc = enc_acc + (size_t)warp * tb.D;
   const int n_loc = tb.N - tb.s + 1;
-  for (int64_t r = (int64_t)blockIdx.x * wpb + warp; r < n; r += (int64_t)gridDim.x * wpb) {
-    const int64_t src = perm ? perm[r] : r;
-    const int64_t start = offsets[src];
-    const int64_t len = offsets[src + 1] - start;
+  float2* ph = enc_sm;                                              // [m][kEncChunk]
+  float2* acc = enc_sm + (size_t)tb.m * kEncChunk + (size_t)warp * tb.D;  // this warp's entries
+  for (int64_t r0 = (int64_t)blockIdx.x * wpb; r0 < n; r0 += (int64_t)gridDim.x * wpb) {
+    const int64_t r = r0 + warp;
+    const bool live = r < n;
+    const int64_t src = live ? (perm ? perm[r] : r) : 0;
+    const int64_t start = live ? offsets[src] : 0;
+    const int64_t len = live ? offsets[src + 1] - start : 0;
     const uint8_t* seq = seqs + start;
     for (int g = lane; g < tb.D; g += 32) acc[g] = make_float2(0.f, 0.f);
-    bool ok = len >= tb.N;
-    if (!ok) {
+    bool ok = live && len >= tb.N;
+    if (live && !ok) {
       if (lane == 0) set_status(status, kStatusShortRead);
-    } else {
+    } else if (ok) {
       int bad = 0;
       for (int i = lane; i < tb.N; i += 32) bad |= head_letter(seq, len, i, rc) > 3;
       if (__any_sync(0xffffffffu, bad)) {
@@ -263,54 +275,85 @@ __global__ void encode_reads_wide_kernel(EncTables tb, const uint8_t* __restrict
         if (lane == 0) set_status(status, kStatusBadBase);
       }
     }
-    __syncwarp();
-    if (ok) {
-      for (int loc0 = 0; loc0 < n_loc; loc0 += 32) {
-        const int loc = loc0 + lane;
-        uint32_t b = 0;
-        if (loc < n_loc) {
-          uint32_t code = 0;
-          for (int i = 0; i < tb.s; ++i) code = code * 4u + (head_letter(seq, len, loc + i, rc) & 3u);
-          b = tb.map[code];
+    for (int c0 = 0; c0 < n_loc; c0 += kEncChunk) {
+      const int c1 = min(c0 + kEncChunk, n_loc);
+      __syncthreads();  // every warp is done with the previous chunk's phases
+      for (int i = threadIdx.x; i < tb.m * kEncChunk; i += blockDim.x) {
+        const int k = i / kEncChunk, u = i - k * kEncChunk;
+        if (c0 + u < c1) ph[i] = tb.phase[(size_t)k * n_loc + c0 + u];
+      }
+      __syncthreads();
+      if (!ok) continue;
+      for (int l0 = c0; l0 < c1; l0 += 32) {
+        const int loc = l0 + lane;
+        const bool valid = loc < c1;
+        // s-mer code of this lane's location from the letters of lanes
+        // loc .. loc+s-1 (two 32-letter rows held across the warp)
+        // every letter of the head is loaded, also past the chunk's last
+        // location: the s-mers of the chunk's last locations read them
+        const uint32_t lo = loc < tb.N ? head_letter(seq, len, loc, rc) & 3u : 0u;
+        const uint32_t hi = (l0 + 32 + lane < tb.N) ? head_letter(seq, len, l0 + 32 + lane, rc) & 3u : 0u;
+        uint32_t code = 0;
+        for (int i = 0; i < tb.s; ++i) {
+          const int sl = lane + i;
+          const uint32_t a = __shfl_sync(0xffffffffu, lo, sl & 31);
+          const uint32_t b = __shfl_sync(0xffffffffu, hi, sl & 31);
+          code = code * 4u + (sl < 32 ? a : b);
         }
-        const int cnt = min(32, n_loc - loc0);
-        for (int jj = 0; jj < cnt; ++jj) {
-          const uint32_t bj = __shfl_sync(0xffffffffu, b, jj);
-          if (lane < tb.m) {
-            const float2 ph = tb.phase[lane * n_loc + loc0 + jj];
-            float2& a = acc[lane * tb.nb + bj];
-            a.x += ph.x;
-            a.y += ph.y;
+        const uint32_t bin = valid ? (uint32_t)__ldg(tb.map + code) : 0xFFFFFFFFu;
+        const uint32_t grp = __match_any_sync(0xffffffffu, bin);
+        const int size = __popc(grp);
+        const int gmax = (int)__reduce_max_sync(0xffffffffu, (unsigned)size);
+        const bool leader = valid && (__ffs(grp) - 1) == lane;
+        for (int k = 0; k < tb.m; ++k) {
+          const float2 p = valid ? ph[k * kEncChunk + (loc - c0)] : make_float2(0.f, 0.f);
+          float sx = 0.f, sy = 0.f;
+          uint32_t rest = grp;
+          for (int it = 0; it < gmax; ++it) {  // the group's members in location order
+            const int m_lane = rest ? __ffs(rest) - 1 : lane;
+            rest &= rest - 1u;
+            const float qx = __shfl_sync(0xffffffffu, p.x, m_lane);
+            const float qy = __shfl_sync(0xffffffffu, p.y, m_lane);
+            if (it < size) {
+              sx += qx;
+              sy += qy;
+            }
           }
-          __syncwarp();
+          if (leader) {
+            float2& e = acc[k * tb.nb + bin];
+            e.x += sx;
+            e.y += sy;
+          }
         }
       }
     }
     __syncwarp();
-    // per-band squared norms, then the total
-    float total = 0.f;
-    for (int k = 0; k < tb.m; ++k) {
-      float part = 0.f;
-      for (int b = lane; b < tb.nb; b += 32) {
-        const float2 a = acc[k * tb.nb + b];
-        part = fmaf(a.x, a.x, fmaf(a.y, a.y, part));
-      }
+    if (live) {
+      // per-band squared norms, then the total
+      float total = 0.f;
+      for (int k = 0; k < tb.m; ++k) {
+        float part = 0.f;
+        for (int b = lane; b < tb.nb; b += 32) {
+          const float2 a = acc[k * tb.nb + b];
+          part = fmaf(a.x, a.x, fmaf(a.y, a.y, part));
+        }
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
-      if (lane == 0) norms[r * (1 + tb.m) + 1 + k] = part;
-      total += part;
-    }
-    if (lane == 0) norms[r * (1 + tb.m)] = total;
-    const float inv = total > kZeroNorm2 ? rsqrtf(total) : 0.f;
-    for (int g = lane; g < tb.D; g += 32) {
-      const float2 a = acc[g];
-      if (emb_f32) {
-        emb_f32[r * 2 * tb.D + g] = a.x;
-        emb_f32[r * 2 * tb.D + tb.D + g] = a.y;
+        for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+        if (lane == 0) norms[r * (1 + tb.m) + 1 + k] = part;
+        total += part;
       }
-      if (emb_bf16) {
-        emb_bf16[r * 2 * tb.D + g] = __float2bfloat16_rn(a.x * inv);
-        emb_bf16[r * 2 * tb.D + tb.D + g] = __float2bfloat16_rn(a.y * inv);
+      if (lane == 0) norms[r * (1 + tb.m)] = total;
+      const float inv = total > kZeroNorm2 ? rsqrtf(total) : 0.f;
+      for (int g = lane; g < tb.D; g += 32) {
+        const float2 a = acc[g];
+        if (emb_f32) {
+          emb_f32[r * 2 * tb.D + g] = a.x;
+          emb_f32[r * 2 * tb.D + tb.D + g] = a.y;
+        }
+        if (emb_bf16) {
+          emb_bf16[r * 2 * tb.D + g] = __float2bfloat16_rn(a.x * inv);
+          emb_bf16[r * 2 * tb.D + tb.D + g] = __float2bfloat16_rn(a.y * inv);
+        }
       }
     }
     __syncwarp();
@@ -331,12 +374,25 @@ cudaError_t launch_encode_reads(const EncTables& tb, const uint8_t* seqs, const 
                                                                  status, perm, rc);
     return cudaGetLastError();
   }
-  int wpb = (int)(48 * 1024 / (tb.D * sizeof(float2)));
+  // phase chunk + one accumulator per warp, within 100 KB (two blocks per SM)
+  const size_t chunk_bytes = (size_t)tb.m * kEncChunk * sizeof(float2);
+  int wpb = (int)((100 * 1024 - chunk_bytes) / (tb.D * sizeof(float2)));
   if (wpb > 8) wpb = 8;
   if (wpb < 1) wpb = 1;
-  const size_t smem = (size_t)wpb * tb.D * sizeof(float2);
+  const size_t smem = chunk_bytes + (size_t)wpb * tb.D * sizeof(float2);
+  static int attr_set[64] = {};  // per device: bytes the attribute was last raised to
+  int dev = 0;
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64 || (int)smem > attr_set[dev]) {
+      e = cudaFuncSetAttribute(encode_reads_wide_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+      if (dev >= 0 && dev < 64) attr_set[dev] = (int)smem;
+    }
+  }
   int64_t blocks = (n + wpb - 1) / wpb;
-  if (blocks > 152 * 64) blocks = 152 * 64;
+  if (blocks > 152 * 16) blocks = 152 * 16;
   encode_reads_wide_kernel<<<(unsigned)blocks, wpb * 32, smem, st>>>(tb, seqs, offsets, n, emb_f32,
                                                                        reinterpret_cast<__nv_bfloat16*>(emb_bf16),
                                                                        norms, status, perm, rc);

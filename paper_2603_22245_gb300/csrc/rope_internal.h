@@ -164,11 +164,39 @@ struct GemmArgs {
   float* dense;          // [n_reads, je - jb] (dense mode)
   int* status;
   uint64_t wait_limit_ns;
+  ThrOut thr;            // threshold mode: every score >= thr.thr[j] appended
 };
+// rope_pairs.cu: mutated copies (the threshold regime's walk), §2.4 pair
+// fidelities, per-window thresholds of the materialised index
+struct MutArgs {
+  const uint8_t* seqs;      // strings mode: ASCII strings seqs[offsets[i], offsets[i+1]) (null: windows mode)
+  const int64_t* offsets;
+  const double* errs;       // strings mode: rate of copy i
+  const uint32_t* packed;   // windows mode: packed reference, windows j0 + i / n_samples
+  int64_t L, j0;
+  int32_t stride, n_samples;
+  double err;               // windows mode: rate
+  int64_t n;                // copies
+  int32_t N;                // letters per copy
+  uint64_t seed;
+  uint8_t* out;             // [n, N] ASCII
+  int* status;
+};
+cudaError_t launch_mutate(const MutArgs& a, cudaStream_t st);
+// out[i] = fidelity of rows i and n + i of emb [2n, 2D] (FP32 encodings, norms [2n, 1 + m])
+cudaError_t launch_pair_fidelity(const float* emb, const float* norms, int64_t n, int D, int m, int nb,
+                                 int score_mode, float* out, cudaStream_t st);
+// out[w] = mean over t of the fidelity between window j0 + w's stored FP32 row
+// and row w * n_samples + t of emb (materialised index)
+cudaError_t launch_window_thresholds(const DevIndex& ix, const float* emb, const float* norms, int64_t j0,
+                                     int64_t count, int n_samples, float* out, cudaStream_t st);
+cudaError_t launch_iota_offsets(int64_t* off, int64_t n, int64_t N, cudaStream_t st);
+
 int gemm_tc_group();       // reads per tile
 int gemm_tc_window_tile(); // windows per tile
 int gemm_tc_stages(int cand_depth);  // deepest pipeline that fits (0: none)
-cudaError_t launch_gemm_tc(const CUtensorMap& tmA, const CUtensorMap& tmB, const GemmArgs& g, bool dense,
+// mode 0: top-k lists, 1: every score (dense), 2: threshold pairs
+cudaError_t launch_gemm_tc(const CUtensorMap& tmA, const CUtensorMap& tmB, const GemmArgs& g, int mode,
                            int num_sms, cudaStream_t st);
 
 // rope_rerank.cu

@@ -125,28 +125,6 @@ __device__ __forceinline__ float fmax3(float a, float b, float c) {
   return d;
 }
 
-// largest |value| of a chunk's 16 Re and 16 Im accumulator columns (bit
-// patterns of FP32 values)
-__device__ __forceinline__ float max_abs32(const uint32_t (&vr)[16], const uint32_t (&vi)[16]) {
-  auto a = [](uint32_t u) { return fabsf(__uint_as_float(u)); };
-  float m[11];
-#pragma unroll
-  for (int g = 0; g < 5; ++g) {
-    m[g] = fmax3(a(vr[3 * g]), a(vr[3 * g + 1]), a(vr[3 * g + 2]));
-    m[5 + g] = fmax3(a(vi[3 * g]), a(vi[3 * g + 1]), a(vi[3 * g + 2]));
-  }
-  m[10] = fmaxf(a(vr[15]), a(vi[15]));
-  const float p = fmax3(m[0], m[1], m[2]), q = fmax3(m[3], m[4], m[5]), r = fmax3(m[6], m[7], m[8]);
-  return fmax3(fmax3(p, q, r), m[9], m[10]);
-}
-
-// Filter threshold on max(|Re|, |Im|) for a list whose worst kept score is
-// thr: |<x|c>|^2 = Re^2 + Im^2 <= 2 max(|Re|, |Im|)^2, so a chunk whose
-// largest |Re| or |Im| is below sqrt(thr / 2) holds no score >= thr. Taken
-// with the factor 0.49998 instead of 0.5, so that FP32 rounding of the score
-// (a few ulps) can never make the bound skip a passing window.
-__device__ __forceinline__ float filter_tau(float thr) { return thr > 0.f ? sqrtf(thr * 0.49998f) : -1.f; }
-
 // bin of position p from the super-tile's staged words (word index relative to word0)
 __device__ __forceinline__ uint32_t bin_staged(const uint32_t* words, int64_t word0, int64_t p, int s,
                                                const uint16_t* __restrict__ map_lsb) {
@@ -249,7 +227,6 @@ __global__ void __launch_bounds__(Sh::NTHREADS, 1) scan_tc_kernel(DevIndex ix, S
     int prev_grp = -1;     // read group of the list being kept
     int seg_rng = 0;       // range whose slot receives that list
     float thr = -INFINITY;  // worst kept score, kept in a register
-    float tau = -1.f;       // filter_tau(thr)
     int worst = 0;
     // writes the kept list of read r to the slot of range rng
     auto flush = [&](int64_t r, int rng) {
@@ -295,7 +272,6 @@ __global__ void __launch_bounds__(Sh::NTHREADS, 1) scan_tc_kernel(DevIndex ix, S
           fence_proxy_async_smem();
         }
         thr = -INFINITY;
-        tau = -1.f;
         worst = 0;
         if (kLists) {
           for (int e = 0; e < a.cand_depth; ++e) {
@@ -338,24 +314,14 @@ __global__ void __launch_bounds__(Sh::NTHREADS, 1) scan_tc_kernel(DevIndex ix, S
               thr_min[2 * u + 1] = __shfl_sync(0xffffffffu, mn, 16);
             }
           }
+// the 16-column chunk at column c0 of this warp's share, its Re and Im
+          // accumulator columns in vr / vi
+          auto chunk = [&](const int c0, const uint32_t (&vr)[16], const uint32_t (&vi)[16]) {
+            float sc[16];
 #pragma unroll
-          for (int c0 = h * Sh::WPH; c0 < (h + 1) * Sh::WPH; c0 += 16) {
-            const uint32_t taddr = tbase + lane_base + col + c0;
-            uint32_t vr[16], vi[16];
-            tmem_ld16(taddr, vr);
-            tmem_ld16(taddr + T, vi);
-            tc_wait_ld();
-            if (c0 + 16 == (h + 1) * Sh::WPH) {
-              // this warp's last chunk is in registers: hand the accumulator back
-              tc_fence_before();
-              __syncwarp();
-              if (lane == 0) mbar_arrive(&bar_aempty[s]);
-            }
+            for (int n = 0; n < 16; n += 2) abs2_pair(vr[n], vr[n + 1], vi[n], vi[n + 1], sc[n], sc[n + 1]);
             const uint32_t jc = jbase + (uint32_t)(c0 * A);
             if constexpr (kThr) {
-              float sc[16];
-#pragma unroll
-              for (int n = 0; n < 16; n += 2) abs2_pair(vr[n], vr[n + 1], vi[n], vi[n + 1], sc[n], sc[n + 1]);
               // the chunk's scores against their windows' thresholds
               const float m0 = fmax3(sc[0], sc[1], sc[2]), m1 = fmax3(sc[3], sc[4], sc[5]);
               const float m2 = fmax3(sc[6], sc[7], sc[8]), m3 = fmax3(sc[9], sc[10], sc[11]);
@@ -379,9 +345,6 @@ __global__ void __launch_bounds__(Sh::NTHREADS, 1) scan_tc_kernel(DevIndex ix, S
                 }
               }
             } else if (kDense) {
-              float sc[16];
-#pragma unroll
-              for (int n = 0; n < 16; n += 2) abs2_pair(vr[n], vr[n + 1], vi[n], vi[n + 1], sc[n], sc[n + 1]);
               if (have_read) {
 #pragma unroll
                 for (int n = 0; n < 16; ++n) {
@@ -389,11 +352,7 @@ __global__ void __launch_bounds__(Sh::NTHREADS, 1) scan_tc_kernel(DevIndex ix, S
                   if (j >= jlo && j < jhi) a.dense[r * (a.je - a.jb) + ((int64_t)j - a.jb)] = sc[n] * Sh::SCORE_SCALE;
                 }
               }
-            } else if (have_read && max_abs32(vr, vi) >= tau) {
-              // rare: some window of the chunk may reach the list; exact scores
-              float sc[16];
-#pragma unroll
-              for (int n = 0; n < 16; n += 2) abs2_pair(vr[n], vr[n + 1], vi[n], vi[n + 1], sc[n], sc[n + 1]);
+            } else {
               float mx;
               if (full) {
                 // depth-3 tree of 3-input maxima
@@ -409,7 +368,7 @@ __global__ void __launch_bounds__(Sh::NTHREADS, 1) scan_tc_kernel(DevIndex ix, S
                   if (j >= jlo && j < jhi) mx = fmaxf(mx, sc[n]);
                 }
               }
-              if (mx >= thr) {
+              if (have_read && mx >= thr) {
                 // rare: the windows of this chunk at or above the threshold, in
                 // column order, each offered to the out-of-line list update
                 uint32_t pass = 0;
@@ -431,8 +390,39 @@ __global__ void __launch_bounds__(Sh::NTHREADS, 1) scan_tc_kernel(DevIndex ix, S
                     worst = ns.worst;
                   }
                 }
-                tau = filter_tau(thr);
               }
+            }
+                    };
+          if constexpr (Sh::WPH == 32 && !kThr) {
+            // both chunks in registers before the accumulator is handed back,
+            // so the next MMAs into it wait only for the loads
+            const uint32_t taddr = tbase + lane_base + col + h * Sh::WPH;
+            uint32_t vr0[16], vi0[16], vr1[16], vi1[16];
+            tmem_ld16(taddr, vr0);
+            tmem_ld16(taddr + T, vi0);
+            tmem_ld16(taddr + 16, vr1);
+            tmem_ld16(taddr + 16 + T, vi1);
+            tc_wait_ld();
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&bar_aempty[s]);
+            chunk(h * Sh::WPH, vr0, vi0);
+            chunk(h * Sh::WPH + 16, vr1, vi1);
+          } else {
+#pragma unroll
+            for (int c0 = h * Sh::WPH; c0 < (h + 1) * Sh::WPH; c0 += 16) {
+              const uint32_t taddr = tbase + lane_base + col + c0;
+              uint32_t vr[16], vi[16];
+              tmem_ld16(taddr, vr);
+              tmem_ld16(taddr + T, vi);
+              tc_wait_ld();
+              if (c0 + 16 == (h + 1) * Sh::WPH) {
+                // this warp's last chunk is in registers: hand the accumulator back
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&bar_aempty[s]);
+              }
+              chunk(c0, vr, vi);
             }
           }
         }

@@ -35,14 +35,6 @@ struct ThrArgs {
   float* out;              // [count]
 };
 
-__device__ __forceinline__ uint64_t sm64_out(uint64_t seed, uint64_t i) {
-  uint64_t z = seed + (i + 1) * 0x9E3779B97F4A7C15ull;
-  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
-  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
-  return z ^ (z >> 31);
-}
-__device__ __forceinline__ double sm64_unit(uint64_t z) { return (double)(z >> 11) * (1.0 / 9007199254740992.0); }
-
 __device__ __forceinline__ uint32_t thr_letter(const uint32_t* __restrict__ packed, int64_t L, int64_t pos) {
   return pos < L ? (__ldg(packed + (pos >> 4)) >> ((pos & 15) * 2)) & 3u : 0u;
 }
@@ -172,6 +164,54 @@ extern "C" rope_status rope_fragment_thresholds(const rope_index* idx, double er
   if (j_begin < 0 || count < 0 || j_begin + count > idx->ix.W) return host_fail(ROPE_ERR_INVALID_ARG, "bad window range");
   if (count == 0) return ROPE_OK;
   if (!out) return host_fail(ROPE_ERR_INVALID_ARG, "NULL pointer");
+  if (idx->dense) {
+    // materialised index: the copies are walked, then encoded by the read
+    // encoder, and compared with the windows' stored FP32 rows, a chunk of
+    // windows at a time (scratch of about 2 GB at most)
+    DeviceCtx* c;
+    rope_status st = host_ctx(&c);
+    if (st != ROPE_OK) return st;
+    const DevIndex& ix = idx->ix;
+    const int N = ix.N, D = ix.D, m = ix.m;
+    const size_t per_copy = (size_t)N + 8 + (size_t)2 * D * sizeof(float) + (size_t)(1 + m) * sizeof(float);
+    int64_t chunk = (int64_t)(((size_t)2 << 30) / (per_copy * n_samples));
+    if (chunk < 1) chunk = 1;
+    if (chunk > count) chunk = count;
+    const int64_t n_copy = chunk * n_samples;
+    auto al = [](size_t b) { return (b + 255) & ~size_t(255); };
+    const size_t b_copy = al((size_t)n_copy * N), b_off = al((size_t)(n_copy + 1) * sizeof(int64_t));
+    const size_t b_emb = al((size_t)n_copy * 2 * D * sizeof(float));
+    const size_t b_norm = al((size_t)n_copy * (1 + m) * sizeof(float));
+    uint8_t* scratch = nullptr;
+    if ((st = host_pool_alloc(c, (void**)&scratch, b_copy + b_off + b_emb + b_norm, stream)) != ROPE_OK) return st;
+    uint8_t* copies = scratch;
+    int64_t* coff = reinterpret_cast<int64_t*>(scratch + b_copy);
+    float* emb = reinterpret_cast<float*>(scratch + b_copy + b_off);
+    float* norms = reinterpret_cast<float*>(scratch + b_copy + b_off + b_emb);
+    cudaError_t e = launch_iota_offsets(coff, n_copy, N, stream);
+    for (int64_t w0 = 0; w0 < count && e == cudaSuccess; w0 += chunk) {
+      const int64_t cw = count - w0 < chunk ? count - w0 : chunk;
+      MutArgs ma{};
+      ma.packed = ix.packed;
+      ma.L = ix.L;
+      ma.j0 = j_begin + w0;
+      ma.stride = ix.stride;
+      ma.n_samples = n_samples;
+      ma.err = err;
+      ma.n = cw * n_samples;
+      ma.N = N;
+      ma.seed = seed;
+      ma.out = copies;
+      ma.status = c->status;
+      e = launch_mutate(ma, stream);
+      if (e == cudaSuccess)
+        e = launch_encode_reads(idx->enc, copies, coff, cw * n_samples, emb, nullptr, norms, c->status, stream);
+      if (e == cudaSuccess) e = launch_window_thresholds(ix, emb, norms, j_begin + w0, cw, n_samples, out + w0, stream);
+    }
+    cudaFreeAsync(scratch, stream);
+    if (e != cudaSuccess) return host_fail(ROPE_ERR_CUDA, "thresholds launch: %s", cudaGetErrorString(e));
+    return ROPE_OK;
+  }
   if (idx->ix.D > 64) return host_fail(ROPE_ERR_UNSUPPORTED, "thresholds take complex dimension <= 64");
   ThrArgs a{};
   a.tb = idx->enc;

@@ -68,6 +68,7 @@ EXPORTS = {
     "rope_score_dense": ([_P, _P, _P, _P, _I64, _I32, _I64, _I64, _P, _P], ctypes.c_int),
     "rope_map": ([_P, _P, _P, _I64, _P, _P, _P, _P], ctypes.c_int),
     "rope_map_strands": ([_P, _P, _P, _I64, _P, _P, _P, _P, _P], ctypes.c_int),
+    "rope_pair_fidelities": ([_P, _P, _P, _I64, _P, ctypes.c_uint64, _P, _P], ctypes.c_int),
     "rope_refine": ([_P, _P, _P, _P, _I64, _P, _I32, _I32, _P, _P, _P], ctypes.c_int),
     "rope_fragment_thresholds": ([_P, ctypes.c_double, _I32, ctypes.c_uint64, _I64, _I64, _P, _P], ctypes.c_int),
     "rope_score_threshold": ([_P, _P, _I64, _P, _I64, _I64, _I64, _P, _P, _P, _P, _P], ctypes.c_int),
@@ -351,6 +352,18 @@ def rope_map_strands(idx: Index, seqs: torch.Tensor, offsets: torch.Tensor, k: i
     o = _opts(k, sep, precision, rescore, cand_depth, rescore_depth, n_ranges, 0, 0)
     _check(load().rope_map_strands(idx.handle, _ptr(seqs), _ptr(offsets), n, ctypes.byref(o), _ptr(out[0]),
                                    _ptr(out[1]), _ptr(out[2]), _stream(stream)))
+    return out
+
+
+def rope_pair_fidelities(p: Params, seqs: torch.Tensor, offsets: torch.Tensor, errs: torch.Tensor, seed: int = 0,
+                         stream=None) -> torch.Tensor:
+    """§2.4: fidelity of each string's first N letters against its mutated copy at rate errs[i] (float32 [n])."""
+    n = offsets.numel() - 1
+    out = torch.empty((n,), dtype=torch.float32, device=seqs.device)
+    e = errs.to(device=seqs.device, dtype=torch.float64).contiguous()
+    pc = p.c()
+    _check(load().rope_pair_fidelities(ctypes.byref(pc), _ptr(seqs), _ptr(offsets), n, _ptr(e), seed, _ptr(out),
+                                       _stream(stream)))
     return out
 
 
