@@ -314,9 +314,19 @@ __global__ void __launch_bounds__(Sh::NTHREADS, 1) scan_tc_kernel(DevIndex ix, S
               thr_min[2 * u + 1] = __shfl_sync(0xffffffffu, mn, 16);
             }
           }
-// the 16-column chunk at column c0 of this warp's share, its Re and Im
-          // accumulator columns in vr / vi
-          auto chunk = [&](const int c0, const uint32_t (&vr)[16], const uint32_t (&vi)[16]) {
+#pragma unroll
+          for (int c0 = h * Sh::WPH; c0 < (h + 1) * Sh::WPH; c0 += 16) {
+            const uint32_t taddr = tbase + lane_base + col + c0;
+            uint32_t vr[16], vi[16];
+            tmem_ld16(taddr, vr);
+            tmem_ld16(taddr + T, vi);
+            tc_wait_ld();
+            if (c0 + 16 == (h + 1) * Sh::WPH) {
+              // this warp's last chunk is in registers: hand the accumulator back
+              tc_fence_before();
+              __syncwarp();
+              if (lane == 0) mbar_arrive(&bar_aempty[s]);
+            }
             float sc[16];
 #pragma unroll
             for (int n = 0; n < 16; n += 2) abs2_pair(vr[n], vr[n + 1], vi[n], vi[n + 1], sc[n], sc[n + 1]);
@@ -391,38 +401,6 @@ __global__ void __launch_bounds__(Sh::NTHREADS, 1) scan_tc_kernel(DevIndex ix, S
                   }
                 }
               }
-            }
-                    };
-          if constexpr (Sh::WPH == 32 && !kThr) {
-            // both chunks in registers before the accumulator is handed back,
-            // so the next MMAs into it wait only for the loads
-            const uint32_t taddr = tbase + lane_base + col + h * Sh::WPH;
-            uint32_t vr0[16], vi0[16], vr1[16], vi1[16];
-            tmem_ld16(taddr, vr0);
-            tmem_ld16(taddr + T, vi0);
-            tmem_ld16(taddr + 16, vr1);
-            tmem_ld16(taddr + 16 + T, vi1);
-            tc_wait_ld();
-            tc_fence_before();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&bar_aempty[s]);
-            chunk(h * Sh::WPH, vr0, vi0);
-            chunk(h * Sh::WPH + 16, vr1, vi1);
-          } else {
-#pragma unroll
-            for (int c0 = h * Sh::WPH; c0 < (h + 1) * Sh::WPH; c0 += 16) {
-              const uint32_t taddr = tbase + lane_base + col + c0;
-              uint32_t vr[16], vi[16];
-              tmem_ld16(taddr, vr);
-              tmem_ld16(taddr + T, vi);
-              tc_wait_ld();
-              if (c0 + 16 == (h + 1) * Sh::WPH) {
-                // this warp's last chunk is in registers: hand the accumulator back
-                tc_fence_before();
-                __syncwarp();
-                if (lane == 0) mbar_arrive(&bar_aempty[s]);
-              }
-              chunk(c0, vr, vi);
             }
           }
         }
