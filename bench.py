@@ -141,7 +141,7 @@ def parse():
     ap.add_argument("--refine-radius", type=int, default=8)
     ap.add_argument("--scan-variant", type=int, default=-1,
                     help="pin the scan's tile variant (and 16 items per SM) instead of the library's choice")
-    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--e2e-steps", type=int, default=-1, help="end-to-end steps (-1: as many as --steps)")
     ap.add_argument("--cpu-reads", type=int, default=32)
     ap.add_argument("--cpu-windows", type=int, default=1_000_000)
     ap.add_argument("--no-cpu", action="store_true")
@@ -786,25 +786,33 @@ def main():
         except Exception as exc:  # a failure here must not cost the bench line
             refine = {"error": str(exc)}
 
-    # end to end through host buffers: H2D reads, rope_map, D2H top-k, every step
+    # end to end through host buffers, every step a different batch: H2D of
+    # the batch's reads from pinned host memory, rope_map, D2H of the top-k
     e2e = None
-    if args.e2e_steps > 0:
-        b0 = 0
-        o_h = rd.offsets[b0 * B:(b0 + 1) * B + 1]
-        s_h = rd.seqs[o_h[0]:o_h[-1]]
-        seq_pin = torch.from_numpy(np.ascontiguousarray(s_h)).pin_memory()
-        off_pin = torch.from_numpy(np.ascontiguousarray(o_h - o_h[0])).pin_memory()
+    n_e2e = args.e2e_steps if args.e2e_steps >= 0 else args.steps
+    if n_e2e > 0:
+        lim = rd.offsets[min(n_batches, n_e2e + 1) * B]  # letters of the batches used
+        seq_pin = torch.from_numpy(np.ascontiguousarray(rd.seqs[:lim])).pin_memory()
+        nb_e2e = min(n_batches, n_e2e + 1)
+        # per batch, its offsets relative to its first letter (host side, pinned)
+        off_pin = torch.from_numpy(np.stack([rd.offsets[b * B:(b + 1) * B + 1] - rd.offsets[b * B]
+                                             for b in range(nb_e2e)])).pin_memory()
         w_pin = torch.empty((B, k), dtype=torch.int64).pin_memory()
         s_pin = torch.empty((B, k), dtype=torch.float32).pin_memory()
         t_pin = torch.empty((B, k), dtype=torch.int8).pin_memory()
-        dseq = torch.empty(seq_pin.shape, dtype=torch.uint8, device="cuda")
-        doff = torch.empty(off_pin.shape, dtype=torch.int64, device="cuda")
-        for it in range(2 + args.e2e_steps):
-            if it == 2:
+        max_letters = int(max(rd.offsets[(b + 1) * B] - rd.offsets[b * B] for b in range(min(n_batches, n_e2e + 1))))
+        dseq = torch.empty((max_letters,), dtype=torch.uint8, device="cuda")
+        doff = torch.empty((B + 1,), dtype=torch.int64, device="cuda")
+        h2d = d2h = 0
+        for it in range(1 + n_e2e):
+            if it == 1:
                 torch.cuda.synchronize()
                 t0 = time.perf_counter()
-            dseq.copy_(seq_pin, non_blocking=True)
-            doff.copy_(off_pin, non_blocking=True)
+                h2d = d2h = 0
+            b = it % min(n_batches, n_e2e + 1)
+            a0, a1 = int(rd.offsets[b * B]), int(rd.offsets[(b + 1) * B])
+            dseq[:a1 - a0].copy_(seq_pin[a0:a1], non_blocking=True)
+            doff.copy_(off_pin[b], non_blocking=True)
             if strands:
                 w_, s_, t_ = rm.rope_map_strands(idx, dseq, doff, k=k, precision="bf16", out=outs)
                 t_pin.copy_(t_, non_blocking=True)
@@ -813,14 +821,16 @@ def main():
             w_pin.copy_(w_, non_blocking=True)
             s_pin.copy_(s_, non_blocking=True)
             torch.cuda.synchronize()
-        te = (time.perf_counter() - t0) / args.e2e_steps
+            h2d += (a1 - a0) + (B + 1) * 8
+            d2h += w_pin.numel() * 8 + s_pin.numel() * 4 + (t_pin.numel() if strands else 0)
+        te = (time.perf_counter() - t0) / n_e2e
         if dist:
             t = torch.tensor([te], device="cuda")
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
             te = float(t.item())
-        e2e = {"value": ws * scores_step / te, "unit": UNIT, "reads_per_s": ws * B / te,
-               "h2d_bytes_per_step": int(seq_pin.numel() + off_pin.numel() * 8),
-               "d2h_bytes_per_step": int(w_pin.numel() * 8 + s_pin.numel() * 4 + (t_pin.numel() if strands else 0))}
+        e2e = {"value": ws * scores_step / te, "unit": UNIT, "reads_per_s": ws * B / te, "steps": n_e2e,
+               "batches": f"{min(n_batches, n_e2e + 1)} distinct batches of {B} reads, one per step",
+               "h2d_bytes_per_step": int(h2d // n_e2e), "d2h_bytes_per_step": int(d2h // n_e2e)}
 
     reranker = None
     if args.rerank_train_reads > 0 and not dense_index:
@@ -843,7 +853,10 @@ def main():
         "reads_per_s": reads_s, "top1_acc": acc_bf16, "fp32_plain": fp32, "fp8_option": fp8, "refine": refine,
         "encode_pass": encode_pass,
         "speedup_vs_fp32_plain": value / ws / fp32["value"] if fp32 else None,
-        "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "reranker": reranker, "gpu_launches": 3 * args.steps, "clocks": clocks,
+        "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "reranker": reranker,
+        # per step: encode, scan, merge; with both strands two encodes and the
+        # strand merge; on a materialised index also the A-operand build
+        "gpu_launches": (3 + (2 if strands else 0) + (1 if dense_index else 0)) * args.steps, "clocks": clocks,
     }
     if rank == 0:
         print(json.dumps(line), flush=True)
