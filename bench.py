@@ -96,7 +96,7 @@ WORKLOADS = {
         L=3_100_000_000, gc=0.41, tandem=0.0, segdup=0.0, inter=0.50, ref_seed=7,
         n_reads=96_000, read_len=20000, sub=0.05, indel=0.10, read_seed=10,
         s=8, m=4, t=4, variant=1, N=20000, stride=1250, k=8, strands=True, batch=24_000, cpu_reads=16,
-        cpu_windows=3000),
+        cpu_windows=3000, fp32_reads=512),
     "markov300M_20k": dict(
         desc="300 Mbp order-2 Markov reference (GC 41%, 2.5% tandem repeats, 2.5% segmental duplicates), 8192 planted "
              "20 kbp reads at 15% errors, both strands, s=8 m=4 t=4 (d=2048), N=20000, step 1250, top-8 (a one-batch "
@@ -104,7 +104,7 @@ WORKLOADS = {
         L=300_000_000, gc=0.41, tandem=0.025, segdup=0.025, inter=0.0, ref_seed=3,
         n_reads=8192, read_len=20000, sub=0.05, indel=0.10, read_seed=11,
         s=8, m=4, t=4, variant=1, N=20000, stride=1250, k=8, strands=True, batch=8192, cpu_reads=16,
-        cpu_windows=3000),
+        cpu_windows=3000, fp32_reads=512),
     "human30M_20k_thr": dict(
         desc="threshold regime (multi-locus output) on a 30 Mbp human-shaped order-2 Markov genome (GC 41%, 50% "
              "interspersed repeats), 2000 planted 20 kbp reads at 15% per-letter edits split evenly between "
@@ -706,28 +706,38 @@ def main():
 
     # FP32 plain path and BF16 on the same read subset (equal-accuracy check)
     fp32 = None
-    F = min(args.fp32_reads, B) if not dense_index else 0
+    F = min(wl.get("fp32_reads", args.fp32_reads), B)
     if F > 0:
-        fo = (torch.empty((F, k), dtype=torch.int64, device="cuda"), torch.empty((F, k), dtype=torch.float32,
-                                                                                 device="cuda"))
         osub = offs[:F + 1]
-        rm.rope_map(idx, seqs, osub, k=k, precision="fp32", out=fo)
+
+        def map_sub(precision):
+            if strands:
+                return rm.rope_map_strands(idx, seqs, osub, k=k, precision=precision)
+            return rm.rope_map(idx, seqs, osub, k=k, precision=precision)
+
+        def hits_sub(res):
+            h = np.abs(res[0][:, 0].cpu().numpy() - true_pos[:F]) < wl["N"]
+            return h & (res[2][:, 0].cpu().numpy() == true_strand[:F]) if strands else h
+
+        map_sub("fp32")
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
         n32 = 2
         for _ in range(n32):
-            rm.rope_map(idx, seqs, osub, k=k, precision="fp32", out=fo)
+            fo = map_sub("fp32")
         e1.record()
         torch.cuda.synchronize()
         t32 = e0.elapsed_time(e1) / 1000.0 / n32
-        acc32 = float(np.mean(np.abs(fo[0][:, 0].cpu().numpy() - true_pos[:F]) < wl["N"]))
-        bo = rm.rope_map(idx, seqs, osub, k=k, precision="bf16")
-        acc16_sub = float(np.mean(np.abs(bo[0][:, 0].cpu().numpy() - true_pos[:F]) < wl["N"]))
+        acc32 = float(np.mean(hits_sub(fo)))
+        bo = map_sub("bf16")
+        acc16_sub = float(np.mean(hits_sub(bo)))
         agree = float(torch.mean((bo[0][:, 0] == fo[0][:, 0]).float()).item())
         rm.rope_sync_status()
-        fp32 = {"value": F * W / t32, "unit": UNIT, "reads_per_s": F / t32, "reads": F, "top1_acc": acc32,
-                "bf16_top1_acc_same_reads": acc16_sub, "top1_window_agreement": agree}
+        fp32 = {"value": rows * F * W / t32, "unit": UNIT, "reads_per_s": F / t32, "reads": F, "top1_acc": acc32,
+                "bf16_top1_acc_same_reads": acc16_sub, "top1_window_agreement": agree,
+                "path": "FP32 CUDA-core scan over the stored FP32 rows" if dense_index else
+                "FP32 CUDA-core scan with on-chip windows"}
 
     # E4M3 option: the same steps with the FP8 tensor-core scan (same batches,
     # same rescoring), its top-1 accuracy on the same planted reads

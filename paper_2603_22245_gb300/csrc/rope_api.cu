@@ -1072,14 +1072,16 @@ rope_status dense_scan(const rope_index* idx, const uint16_t* emb_bf16, const fl
                        const int64_t* out_row, const ThrOut* thr_out = nullptr) {
   const int mode = thr_out ? 2 : dense_out ? 1 : 0;
   const DevIndex& ix = idx->ix;
-  if (o.precision != ROPE_PREC_BF16)
-    return fail(ROPE_ERR_UNSUPPORTED, "a materialised index is scored by the BF16 tensor-core GEMM (precision %d)",
-                o.precision);
-  if (!emb_bf16) return fail(ROPE_ERR_INVALID_ARG, "the tensor-core scan needs emb_bf16");
+  // FP32: the plain CUDA-core scan over the stored FP32 rows (top-k only)
+  const bool fp32 = o.precision == ROPE_PREC_FP32 && mode == 0;
+  if (!fp32 && o.precision != ROPE_PREC_BF16)
+    return fail(ROPE_ERR_UNSUPPORTED, "a materialised index is scored by the BF16 tensor-core GEMM or, for its top-k, "
+                "the FP32 plain scan (precision %d)", o.precision);
+  if (!fp32 && !emb_bf16) return fail(ROPE_ERR_INVALID_ARG, "the tensor-core scan needs emb_bf16");
   DeviceCtx* c;
   rope_status st = get_ctx(&c);
   if (st != ROPE_OK) return st;
-  const int BM = gemm_tc_group(), BN = gemm_tc_window_tile();
+  const int BM = fp32 ? dense_fp32_group() : gemm_tc_group(), BN = fp32 ? dense_fp32_group() : gemm_tc_window_tile();
   const int64_t n_pad = (n_reads + BM - 1) / BM * BM;
   if (2 * n_pad > 0x7FFFFFFF) return fail(ROPE_ERR_UNSUPPORTED, "more than 2^30 reads in one call");
   const int n_rt = (int)(n_pad / BM);
@@ -1087,21 +1089,22 @@ rope_status dense_scan(const rope_index* idx, const uint16_t* emb_bf16, const fl
   // waves of grp read tiles x n_ranges window ranges (one block each): the
   // grp read tiles' operands stay in L2 while each range's window tiles stream
   // past its grp blocks
+  const int slots = fp32 ? 2 * c->num_sms : c->num_sms;  // blocks resident at once
   int grp, n_ranges;
-  if ((int64_t)n_rt * 4 >= c->num_sms) {
+  if ((int64_t)n_rt * 4 >= slots) {
     n_ranges = 4;
-    grp = std::max(1, c->num_sms / 4);
+    grp = std::max(1, slots / 4);
   } else {
     grp = n_rt;
-    n_ranges = std::max(1, c->num_sms / n_rt);
+    n_ranges = std::max(1, slots / n_rt);
   }
   if (n_ranges > n_wt) n_ranges = (int)std::max<int64_t>(1, n_wt);
   const int64_t tiles_per_range = n_wt > 0 ? (n_wt + n_ranges - 1) / n_ranges : 1;
   if (n_wt > 0) n_ranges = (int)((n_wt + tiles_per_range - 1) / tiles_per_range);
-  const int stages = gemm_tc_stages(mode == 0 ? o.cand_depth : 0);
+  const int stages = fp32 ? 2 : gemm_tc_stages(mode == 0 ? o.cand_depth : 0);
   if (stages < 2) return fail(ROPE_ERR_UNSUPPORTED, "cand_depth=%d: the GEMM scan does not fit in shared memory", o.cand_depth);
   auto al = [](size_t b) { return (b + 255) & ~size_t(255); };
-  const size_t a_bytes = al((size_t)2 * n_pad * 2 * ix.D * sizeof(uint16_t));
+  const size_t a_bytes = fp32 ? 0 : al((size_t)2 * n_pad * 2 * ix.D * sizeof(uint16_t));
   const size_t cand_bytes = mode != 0 ? 0 : (size_t)n_reads * n_ranges * o.cand_depth * sizeof(Candidate);
   uint8_t* scratch = nullptr;
   if ((st = pool_alloc(c, (void**)&scratch, a_bytes + cand_bytes, stream)) != ROPE_OK) return st;
@@ -1112,7 +1115,23 @@ rope_status dense_scan(const rope_index* idx, const uint16_t* emb_bf16, const fl
     return r;
   };
   cudaError_t e = cudaSuccess;
-  if (n_wt > 0) {
+  if (n_wt > 0 && fp32) {
+    GemmArgs g{};
+    g.n_reads = n_reads;
+    g.n_rt = n_rt;
+    g.grp = grp;
+    g.n_ranges = n_ranges;
+    g.jb = jb;
+    g.je = je;
+    g.range_len = tiles_per_range * BN;
+    g.cand_depth = o.cand_depth;
+    g.sep = o.sep;
+    g.stride = ix.stride;
+    g.cand = cand;
+    g.status = c->status;
+    e = launch_dense_fp32(ix, g, emb_f32, norms, c->num_sms, stream);
+    if (e != cudaSuccess) return release(fail(ROPE_ERR_CUDA, "FP32 scan launch: %s", cudaGetErrorString(e)));
+  } else if (n_wt > 0) {
     CUtensorMap tmA;
     e = launch_gemm_a(emb_bf16, n_reads, n_pad, ix.D, a_op, stream);
     if (e != cudaSuccess) return release(fail(ROPE_ERR_CUDA, "A operand launch: %s", cudaGetErrorString(e)));

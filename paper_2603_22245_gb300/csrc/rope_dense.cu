@@ -520,6 +520,128 @@ __global__ void __launch_bounds__(GemmShape::NTHREADS, 1)
   }
 }
 
+// ---------------------------------------------------------------- FP32 plain scan
+
+// The plain path of the materialised index: FP32 inner products of the reads'
+// unnormalised FP32 encodings with the stored FP32 window rows on the CUDA
+// cores. A block of 256 threads computes a 64-read x 64-window tile, each
+// thread a 4 x 4 sub-tile of (Re, Im) accumulators, over K in chunks of 32
+// complex entries staged in shared memory; the tile's fidelities
+// |ip|^2 / (|x|^2 |c|^2) go to shared memory and one thread per read offers
+// them, in window order, to its read's candidate list. Work items are
+// (read tile, window range) as in the GEMM scan.
+constexpr int kF32Tile = 64;
+constexpr int kF32Kc = 32;  // complex entries per K chunk
+
+__global__ void __launch_bounds__(256) dense_fp32_kernel(DevIndex ix, GemmArgs g, const float* __restrict__ emb,
+                                                         const float* __restrict__ norms) {
+  __shared__ float2 xs[kF32Kc][kF32Tile + 1];   // [k][read]: (xr, xi); the score tile after the K loop
+  __shared__ float2 cs[kF32Kc][kF32Tile + 1];   // [k][window]: (cr, ci)
+  static_assert(sizeof(xs) >= sizeof(float) * kF32Tile * (kF32Tile + 1), "score tile overlays xs");
+  float (*tile_s)[kF32Tile + 1] = reinterpret_cast<float (*)[kF32Tile + 1]>(&xs[0][0]);
+  extern __shared__ float f32_lists[];          // [cand_depth][64] scores, then windows
+  float* ls_all = f32_lists;
+  uint32_t* lw_all = reinterpret_cast<uint32_t*>(f32_lists + (size_t)g.cand_depth * kF32Tile);
+  const int tid = threadIdx.x;
+  const int tr = tid / 16, tc = tid % 16;  // sub-tile: reads 4tr..4tr+3, windows 4tc..4tc+3
+  const int D = ix.D, m = ix.m;
+  const int64_t n_items = (int64_t)((g.n_rt + g.grp - 1) / g.grp) * g.grp * g.n_ranges;
+  for (int64_t it = blockIdx.x; it < n_items; it += gridDim.x) {
+    int rt, rg;
+    int64_t w_lo, w_hi;
+    if (!gemm_item(g, it, rt, rg, w_lo, w_hi)) continue;
+    const int64_t r0 = (int64_t)rt * kF32Tile;
+    float thr = -INFINITY;
+    int worst = 0;
+    float* ls = ls_all + (tid < kF32Tile ? tid : 0);
+    uint32_t* lw = lw_all + (tid < kF32Tile ? tid : 0);
+    if (tid < kF32Tile)
+      for (int e = 0; e < g.cand_depth; ++e) {
+        ls[e * kF32Tile] = -INFINITY;
+        lw[e * kF32Tile] = kEmptyWin;
+      }
+    for (int64_t w0 = w_lo; w0 < w_hi; w0 += kF32Tile) {
+      float re[4][4], im[4][4];
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) re[a][b] = im[a][b] = 0.f;
+      for (int k0 = 0; k0 < D; k0 += kF32Kc) {
+        __syncthreads();  // the previous chunk (or tile) is consumed
+        for (int q = tid; q < kF32Kc * kF32Tile; q += 256) {
+          const int k = q % kF32Kc, i = q / kF32Kc;
+          const int64_t r = r0 + i, j = w0 + i;
+          const float* xrow = emb + (size_t)r * 2 * D;
+          const float* crow = ix.win_f32 + (size_t)j * 2 * D;
+          xs[k][i] = r < g.n_reads ? make_float2(xrow[k0 + k], xrow[D + k0 + k]) : make_float2(0.f, 0.f);
+          cs[k][i] = j < w_hi ? make_float2(crow[k0 + k], crow[D + k0 + k]) : make_float2(0.f, 0.f);
+        }
+        __syncthreads();
+#pragma unroll 4
+        for (int k = 0; k < kF32Kc; ++k) {
+          float2 x[4], c[4];
+#pragma unroll
+          for (int a = 0; a < 4; ++a) x[a] = xs[k][4 * tr + a];
+#pragma unroll
+          for (int b = 0; b < 4; ++b) c[b] = cs[k][4 * tc + b];
+#pragma unroll
+          for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int b = 0; b < 4; ++b) {
+              // Re += xr cr + xi ci, Im += xr ci - xi cr (conj(x) . c, §4)
+              re[a][b] = fmaf(x[a].x, c[b].x, fmaf(x[a].y, c[b].y, re[a][b]));
+              im[a][b] = fmaf(x[a].x, c[b].y, fmaf(-x[a].y, c[b].x, im[a][b]));
+            }
+        }
+      }
+      // fidelities of the tile (over the staged x chunk: every thread is past it)
+      __syncthreads();
+#pragma unroll
+      for (int a = 0; a < 4; ++a) {
+        const int64_t r = r0 + 4 * tr + a;
+        const float X = r < g.n_reads ? norms[r * (1 + m)] : 0.f;
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+          const int64_t j = w0 + 4 * tc + b;
+          const float inv = j < w_hi ? __ldg(ix.inv_norm + j) : 0.f;  // 1/|c|, 0 for a zero vector
+          const float num = fmaf(re[a][b], re[a][b], im[a][b] * im[a][b]);
+          tile_s[4 * tr + a][4 * tc + b] = (X > kZeroNorm2 && inv > 0.f) ? num / X * (inv * inv) : 0.f;
+        }
+      }
+      __syncthreads();
+      if (tid < kF32Tile && r0 + tid < g.n_reads) {
+        const int n_w = (int)(w_hi - w0 < kF32Tile ? w_hi - w0 : kF32Tile);
+        for (int n = 0; n < n_w; ++n) {
+          const float v = tile_s[tid][n];
+          if (v >= thr) {
+            const ListState ns = list_insert(ls, lw, kF32Tile, g.cand_depth, worst, v, (uint32_t)(w0 + n), g.sep,
+                                             g.stride);
+            thr = ns.thr;
+            worst = ns.worst;
+          }
+        }
+      }
+    }
+    if (tid < kF32Tile && r0 + tid < g.n_reads) {
+      Candidate* out = g.cand + ((size_t)(r0 + tid) * g.n_ranges + rg) * g.cand_depth;
+      for (int e = 0; e < g.cand_depth; ++e) out[e] = Candidate{ls[e * kF32Tile], lw[e * kF32Tile]};
+    }
+    __syncthreads();  // the lists are reused by the next item
+  }
+}
+
+int dense_fp32_group() { return kF32Tile; }
+
+cudaError_t launch_dense_fp32(const DevIndex& ix, const GemmArgs& g, const float* emb, const float* norms, int num_sms,
+                              cudaStream_t st) {
+  const int64_t n_items = (int64_t)((g.n_rt + g.grp - 1) / g.grp) * g.grp * g.n_ranges;
+  int64_t grid = n_items < (int64_t)num_sms * 2 ? n_items : (int64_t)num_sms * 2;
+  if (grid < 1) return cudaSuccess;
+  const size_t smem = (size_t)g.cand_depth * kF32Tile * 8;
+  dense_fp32_kernel<<<(unsigned)grid, 256, smem, st>>>(ix, g, emb, norms);
+  return cudaGetLastError();
+}
+
 int gemm_tc_group() { return GemmShape::BM; }
 int gemm_tc_window_tile() { return GemmShape::BN; }
 

@@ -192,6 +192,11 @@ cudaError_t launch_window_thresholds(const DevIndex& ix, const float* emb, const
                                      int64_t count, int n_samples, float* out, cudaStream_t st);
 cudaError_t launch_iota_offsets(int64_t* off, int64_t n, int64_t N, cudaStream_t st);
 
+// FP32 plain scan of a materialised index (reads' FP32 encodings against the
+// stored FP32 rows, CUDA cores): per-read lists into g.cand, items as the GEMM's
+int dense_fp32_group();    // reads per tile (64)
+cudaError_t launch_dense_fp32(const DevIndex& ix, const GemmArgs& g, const float* emb, const float* norms, int num_sms,
+                              cudaStream_t st);
 int gemm_tc_group();       // reads per tile
 int gemm_tc_window_tile(); // windows per tile
 int gemm_tc_stages(int cand_depth);  // deepest pipeline that fits (0: none)

@@ -175,10 +175,32 @@ def test_dense_small_dimension_matches_on_the_fly(lib):
     b.free()
 
 
+def test_dense_topk_fp32_plain(lib, long_reads):
+    """The plain FP32 scan of the materialised index (CUDA cores, the stored
+    FP32 rows): the oracle's top-k at the FP32 tolerance, top-1 exact where
+    clear."""
+    c = long_reads
+    gw, gs = lib.rope_score_topk(c["idx"], c["f32"], None, c["norms"], k=8, precision="fp32")
+    lib.rope_sync_status()
+    gw, gs = gw.cpu().numpy(), gs.cpu().numpy().astype(np.float64)
+    check_topk(c["ref"], c["rd"], c["op"], gw, gs, c["ow"], c["os"], 8, f32_tol)
+    clear = c["os"][:, 0] - c["os"][:, 1] > f32_tol(c["os"][:, 0])
+    assert np.array_equal(gw[clear, 0], c["ow"][clear, 0])
+    # a window sub-range with buckets, three read tiles of 64 (the last ragged)
+    k, sep = 4, 5000
+    gw, gs = lib.rope_score_topk(c["idx"], c["f32"][:150], None, c["norms"][:150], k=k, sep=sep, precision="fp32",
+                                 j_begin=50, j_end=700)
+    lib.rope_sync_status()
+    sub = c["rd"].subset(np.arange(150))
+    ow, os_ = oracle.score_topk(c["ref"], sub.seqs, sub.offsets, c["op"], k=k + 1, sep=sep, j_begin=50, j_end=700)
+    check_topk(c["ref"], sub, c["op"], gw.cpu().numpy(), gs.cpu().numpy().astype(np.float64), ow, os_, k, f32_tol,
+               sep=sep)
+
+
 def test_dense_refusals(lib, long_reads):
     c = long_reads
-    with pytest.raises(lib.RopeError) as e:
-        lib.rope_score_topk(c["idx"], c["f32"], None, c["norms"], k=4, precision="fp32")
+    with pytest.raises(lib.RopeError) as e:  # every score: the BF16 GEMM only
+        lib.rope_score_dense(c["idx"], c["f32"], None, c["norms"], 0, 10, precision="fp32")
     assert e.value.status == 6
     out = (torch.empty((300, 4), dtype=torch.int64, device="cuda"), torch.empty((300, 4), dtype=torch.float32,
                                                                                device="cuda"))
