@@ -171,17 +171,19 @@ rope_status rope_encode_reference(const rope_params* p, const uint8_t* ref, int6
 
 /* Materialised index (§3.1's "database of vectors", sized in §3.2 for 20 kbp
  * reads: window 20,000, step 1,250, 1024 complex dimensions). Stores every
- * window's encoding twice on the device -- FP32 [W, 2D] unnormalised
- * (re block, im block; for re-scoring) and BF16 [W, 2D] divided by its norm
- * (the tensor-core operand) -- plus 1/|c_j| in FP32: W * 2D * 6 bytes (30 GB
- * for a 3.1 Gbp genome at those settings), and 8 * D bytes per window of
- * scratch during the build. Each window is summed exactly from per-block sums
- * over blocks of `stride` s-mer starts (no recurrence, no drift; FP32).
- * Any stride (1..65536); D = m*4^t a multiple of 32, at most 4096; score_mode
- * 0; W < 2^31. rope_score_topk / rope_map / rope_map_strands / rope_score_dense
- * on it run the BF16 tensor-core GEMM (precision ROPE_PREC_BF16 only) with
- * the top-k fused into its epilogue, and re-score in FP32 from the stored
- * rows; the other scans refuse it (ROPE_ERR_UNSUPPORTED). Synchronous. */
+ * window's encoding on the device -- FP32 [W, 2D] unnormalised (re block, im
+ * block; for re-scoring and the FP32 scan) and, divided by its norm, the two
+ * BF16 [W, 2D] tensor-core operands [cr | ci] and [ci | -cr] -- plus 1/|c_j|
+ * in FP32: W * 2D * 8 bytes (41 GB for a 3.1 Gbp genome at those settings),
+ * and 8 * D bytes per window of scratch during the build. Each window is
+ * summed exactly from per-block sums over blocks of `stride` s-mer starts (no
+ * recurrence, no drift; FP32). Any stride (1..65536); D = m*4^t a multiple of
+ * 32, at most 4096; score_mode 0; W < 2^31. rope_score_topk / rope_map /
+ * rope_map_strands / rope_score_dense / rope_score_threshold on it run the
+ * BF16 tensor-core GEMM (ROPE_PREC_BF16) with the top-k fused into its
+ * epilogue and re-score in FP32 from the stored rows; the top-k calls also
+ * take ROPE_PREC_FP32 (a plain CUDA-core scan over the FP32 rows). Other
+ * precisions and the other scans refuse it (ROPE_ERR_UNSUPPORTED). Synchronous. */
 rope_status rope_encode_reference_dense(const rope_params* p, const uint8_t* ref, int64_t len, rope_index** out,
                                         cudaStream_t stream);
 

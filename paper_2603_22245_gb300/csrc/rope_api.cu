@@ -548,12 +548,13 @@ rope_status rope::encode_reference_dense_impl(const rope_params* p, const uint8_
   const int64_t n_blocks = n_blk > 0 ? W + n_blk - 1 : 0;
   uint32_t* packed = nullptr;
   float *inv_norm = nullptr, *win_f32 = nullptr;
-  uint16_t *win_bf16 = nullptr, *map_lsb = nullptr, *map = nullptr;
+  uint16_t *win_bf16 = nullptr, *win_bf16_im = nullptr, *map_lsb = nullptr, *map = nullptr;
   float2 *phase = nullptr, *d_bph = nullptr, *d_rotu = nullptr, *d_tph = nullptr;
   if ((st = upload(idx->owned, std::vector<uint32_t>(), &packed, (size_t)(n_words + pad_words))) != ROPE_OK ||
       (st = upload(idx->owned, std::vector<float>(), &inv_norm, (size_t)W + 256)) != ROPE_OK ||
       (st = upload(idx->owned, std::vector<float>(), &win_f32, (size_t)W * 2 * D)) != ROPE_OK ||
       (st = upload(idx->owned, std::vector<uint16_t>(), &win_bf16, (size_t)W * 2 * D)) != ROPE_OK ||
+      (st = upload(idx->owned, std::vector<uint16_t>(), &win_bf16_im, (size_t)W * 2 * D)) != ROPE_OK ||
       (st = upload(idx->owned, h.map_lsb, &map_lsb)) != ROPE_OK || (st = upload(idx->owned, h.map, &map)) != ROPE_OK ||
       (st = upload(idx->owned, to_f32(h.phase), &phase)) != ROPE_OK ||
       (st = upload(idx->owned, bph, &d_bph)) != ROPE_OK || (st = upload(idx->owned, rotu, &d_rotu)) != ROPE_OK ||
@@ -587,12 +588,14 @@ rope_status rope::encode_reference_dense_impl(const rope_params* p, const uint8_
   if (e == cudaSuccess && n_blocks > 0) e = cudaMalloc(&bsum, (size_t)n_blocks * D * sizeof(float2));
   if (e == cudaErrorMemoryAllocation) return cleanup(fail(ROPE_ERR_OOM, "block sums: %s", cudaGetErrorString(e)));
   if (e == cudaSuccess) e = launch_pack(ref, len, packed, c->status, stream);
-  if (e == cudaSuccess) e = launch_dense_index(ix, dt, bsum, win_f32, win_bf16, inv_norm, stream);
+  if (e == cudaSuccess) e = launch_dense_index(ix, dt, bsum, win_f32, win_bf16, win_bf16_im, inv_norm, stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
   if (bsum) cudaFree(bsum);
   if (e != cudaSuccess) return cleanup(fail(ROPE_ERR_CUDA, "materialised index build: %s", cudaGetErrorString(e)));
   if ((st = rope_sync_status(stream)) != ROPE_OK) return cleanup(st);
-  if ((st = tensor_map_rows(&idx->tm_win, win_bf16, W, 2 * D)) != ROPE_OK) return cleanup(st);
+  if ((st = tensor_map_rows(&idx->tm_win, win_bf16, W, 2 * D)) != ROPE_OK ||
+      (st = tensor_map_rows(&idx->tm_win_im, win_bf16_im, W, 2 * D)) != ROPE_OK)
+    return cleanup(st);
   *out = idx;
   return ROPE_OK;
 }
@@ -1104,7 +1107,7 @@ rope_status dense_scan(const rope_index* idx, const uint16_t* emb_bf16, const fl
   const int stages = fp32 ? 2 : gemm_tc_stages(mode == 0 ? o.cand_depth : 0);
   if (stages < 2) return fail(ROPE_ERR_UNSUPPORTED, "cand_depth=%d: the GEMM scan does not fit in shared memory", o.cand_depth);
   auto al = [](size_t b) { return (b + 255) & ~size_t(255); };
-  const size_t a_bytes = fp32 ? 0 : al((size_t)2 * n_pad * 2 * ix.D * sizeof(uint16_t));
+  const size_t a_bytes = fp32 ? 0 : al((size_t)n_pad * 2 * ix.D * sizeof(uint16_t));
   const size_t cand_bytes = mode != 0 ? 0 : (size_t)n_reads * n_ranges * o.cand_depth * sizeof(Candidate);
   uint8_t* scratch = nullptr;
   if ((st = pool_alloc(c, (void**)&scratch, a_bytes + cand_bytes, stream)) != ROPE_OK) return st;
@@ -1135,14 +1138,13 @@ rope_status dense_scan(const rope_index* idx, const uint16_t* emb_bf16, const fl
     CUtensorMap tmA;
     e = launch_gemm_a(emb_bf16, n_reads, n_pad, ix.D, a_op, stream);
     if (e != cudaSuccess) return release(fail(ROPE_ERR_CUDA, "A operand launch: %s", cudaGetErrorString(e)));
-    if ((st = tensor_map_rows(&tmA, a_op, 2 * n_pad, 2 * ix.D)) != ROPE_OK) return release(st);
+    if ((st = tensor_map_rows(&tmA, a_op, n_pad, 2 * ix.D)) != ROPE_OK) return release(st);
     GemmArgs g{};
     g.n_reads = n_reads;
     g.n_rt = n_rt;
     g.grp = grp;
     g.n_ranges = n_ranges;
     g.k_blocks = 2 * ix.D / 64;
-    g.a_im_row0 = (int32_t)n_pad;
     g.stages = stages;
     g.jb = jb;
     g.je = je;
@@ -1155,7 +1157,7 @@ rope_status dense_scan(const rope_index* idx, const uint16_t* emb_bf16, const fl
     g.status = c->status;
     g.wait_limit_ns = wait_limit_ns();
     if (thr_out) g.thr = *thr_out;
-    e = launch_gemm_tc(tmA, idx->tm_win, g, mode, c->num_sms, stream);
+    e = launch_gemm_tc(tmA, idx->tm_win, idx->tm_win_im, g, mode, c->num_sms, stream);
     if (e != cudaSuccess) return release(fail(ROPE_ERR_CUDA, "GEMM scan launch: %s", cudaGetErrorString(e)));
   } else if (mode == 0) {
     e = cudaMemsetAsync(cand, 0xFF, cand_bytes, stream);  // every slot empty

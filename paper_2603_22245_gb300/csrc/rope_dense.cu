@@ -20,11 +20,14 @@
 //
 // Scan: C[read][window] = <x|c> as a real GEMM on tcgen05 (BF16 in, FP32 in
 // tensor memory). Per tile 128 reads x 128 windows and per 64-wide K block, TMA
-// brings three 128-row boxes into shared memory: the reads' [xr | xi] rows
-// (A_re), their [-xi | xr] rows (A_im) and the windows' [cr | ci] rows (B), so
-// that D_re = A_re B^T = Re<x|c> and D_im = A_im B^T = Im<x|c> land in the same
-// tensor-memory lane (the read) and column (the window): the epilogue thread of
-// a read forms |.|^2 with no data exchange (§4's real identity).
+// brings three 128-row boxes into shared memory: the reads' [xr | xi] rows (A)
+// and, back to back as one 256-row B operand, the windows' [cr | ci] rows and
+// their [ci | -cr] rows (both stored by the index). One MMA of N = 256 per K
+// step then writes Re<x|c> = xr.cr + xi.ci to columns [0, 128) and
+// Im<x|c> = xr.ci - xi.cr to columns [128, 256) of the read's tensor-memory
+// lane: the epilogue thread of a read forms |.|^2 with no data exchange (§4's
+// real identity). Against two N = 128 MMAs (a [-xi | xr] A tile for Im) this
+// reads 12 KB of shared memory per 128 tensor cycles instead of 16 KB.
 #include <cuda.h>
 #include <cuda_bf16.h>
 
@@ -73,13 +76,14 @@ __global__ void block_sums_kernel(DevIndex ix, DenseTables dt, float2* __restric
 // One block of 256 threads per run of consecutive windows; thread t holds
 // entries t, t+256, ... (EPT of them). Per window: the tail sums (one warp, in
 // start order, into shared memory), the block combination, the squared norm
-// (fixed-order block reduction), then the FP32 row, the normalised BF16 row
-// and 1/|c|.
+// (fixed-order block reduction), then the FP32 row, the normalised BF16 rows
+// [cr | ci] and [ci | -cr] (the scan's two B operands) and 1/|c|.
 template <int EPT>
 __global__ void __launch_bounds__(256) dense_windows_kernel(DevIndex ix, DenseTables dt,
                                                             const float2* __restrict__ bsum,
                                                             float* __restrict__ out_f32,
                                                             __nv_bfloat16* __restrict__ out_bf16,
+                                                            __nv_bfloat16* __restrict__ out_bf16_im,
                                                             float* __restrict__ inv_norm, int64_t run) {
   extern __shared__ float2 dw_tail[];  // [D]
   __shared__ float red[8];
@@ -157,14 +161,18 @@ __global__ void __launch_bounds__(256) dense_windows_kernel(DevIndex ix, DenseTa
     const float inv = tot > kZeroNorm2 ? (float)(1.0 / sqrt((double)tot)) : 0.f;
     float* of = out_f32 + (size_t)j * 2 * D;
     __nv_bfloat16* ob = out_bf16 + (size_t)j * 2 * D;
+    __nv_bfloat16* obi = out_bf16_im + (size_t)j * 2 * D;
 #pragma unroll
     for (int i = 0; i < EPT; ++i) {
       const int e = tid + 256 * i;
       if (e < D) {
         of[e] = cr[i];
         of[D + e] = ci[i];
-        ob[e] = __float2bfloat16_rn(cr[i] * inv);
-        ob[D + e] = __float2bfloat16_rn(ci[i] * inv);
+        const __nv_bfloat16 br = __float2bfloat16_rn(cr[i] * inv), bi = __float2bfloat16_rn(ci[i] * inv);
+        ob[e] = br;
+        ob[D + e] = bi;
+        obi[e] = bi;
+        obi[D + e] = __hneg(br);  // exact: the sign bit
       }
     }
     if (tid == 0) inv_norm[j] = inv;
@@ -173,7 +181,7 @@ __global__ void __launch_bounds__(256) dense_windows_kernel(DevIndex ix, DenseTa
 }
 
 cudaError_t launch_dense_index(const DevIndex& ix, const DenseTables& dt, float2* bsum, float* win_f32,
-                               uint16_t* win_bf16, float* inv_norm, cudaStream_t st) {
+                               uint16_t* win_bf16, uint16_t* win_bf16_im, float* inv_norm, cudaStream_t st) {
   if (dt.n_blocks > 0) {
     int wpb = (int)((96 * 1024) / ((size_t)ix.D * sizeof(float2)));  // accumulators within 96 KB
     wpb = wpb < 1 ? 1 : wpb > 8 ? 8 : wpb;
@@ -197,7 +205,7 @@ cudaError_t launch_dense_index(const DevIndex& ix, const DenseTables& dt, float2
       if (e != cudaSuccess) return e;
     }
     kern<<<(unsigned)grid, 256, smem, st>>>(ix, dt, bsum, win_f32, reinterpret_cast<__nv_bfloat16*>(win_bf16),
-                                            inv_norm, run);
+                                            reinterpret_cast<__nv_bfloat16*>(win_bf16_im), inv_norm, run);
     return cudaGetLastError();
   };
   const int ept = (ix.D + 255) / 256;
@@ -212,31 +220,27 @@ cudaError_t launch_dense_index(const DevIndex& ix, const DenseTables& dt, float2
 // ---------------------------------------------------------------- scan operands
 
 // A operand of the scan: rows [0, n_pad) are the reads' normalised [xr | xi]
-// (zero past n), rows [n_pad, 2 n_pad) are [-xi | xr]. Four BF16 entries per
-// thread (D is a multiple of 32).
+// rows, zero past n (an aligned, padded copy the tensor map can address).
+// Eight BF16 entries per thread (2D is a multiple of 64).
 __global__ void gemm_a_kernel(const uint16_t* __restrict__ emb, int64_t n, int64_t n_pad, int D,
                               uint16_t* __restrict__ a) {
-  const int q4 = D / 4;
-  const int64_t total = n_pad * q4;
+  const int q8 = 2 * D / 8;
+  const int64_t total = n_pad * q8;
   for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
        idx += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t r = idx / q4;
-    const int g = (int)(idx % q4) * 4;
-    uint2 xr = make_uint2(0, 0), xi = make_uint2(0, 0);
+    const int64_t r = idx / q8;
+    const int g = (int)(idx % q8) * 8;
+    uint2 lo = make_uint2(0, 0), hi = make_uint2(0, 0);
     if (r < n) {
-      xr = *reinterpret_cast<const uint2*>(emb + r * 2 * D + g);
-      xi = *reinterpret_cast<const uint2*>(emb + r * 2 * D + D + g);
+      lo = *reinterpret_cast<const uint2*>(emb + r * 2 * D + g);
+      hi = *reinterpret_cast<const uint2*>(emb + r * 2 * D + g + 4);
     }
-    const uint2 nxi = make_uint2(xi.x ^ 0x80008000u, xi.y ^ 0x80008000u);
-    *reinterpret_cast<uint2*>(a + r * 2 * D + g) = xr;
-    *reinterpret_cast<uint2*>(a + r * 2 * D + D + g) = xi;
-    *reinterpret_cast<uint2*>(a + (n_pad + r) * 2 * D + g) = nxi;
-    *reinterpret_cast<uint2*>(a + (n_pad + r) * 2 * D + D + g) = xr;
+    *reinterpret_cast<uint4*>(a + r * 2 * D + g) = make_uint4(lo.x, lo.y, hi.x, hi.y);
   }
 }
 
 cudaError_t launch_gemm_a(const uint16_t* emb, int64_t n, int64_t n_pad, int D, uint16_t* a, cudaStream_t st) {
-  const int64_t total = n_pad * (D / 4);
+  const int64_t total = n_pad * (2 * D / 8);
   int64_t blocks = (total + 255) / 256;
   if (blocks > 152 * 64) blocks = 152 * 64;
   if (blocks < 1) return cudaSuccess;
@@ -248,17 +252,18 @@ cudaError_t launch_gemm_a(const uint16_t* emb, int64_t n, int64_t n_pad, int D, 
 
 struct GemmShape {
   static constexpr int BM = 128;                 // reads per tile (tensor-memory lanes)
-  static constexpr int BN = 128;                 // windows per tile (MMA N)
+  static constexpr int BN = 128;                 // windows per tile (MMA N = 2 BN: Re and Im rows)
   static constexpr int BK = 64;                  // K per stage: one 128-byte swizzled BF16 row
   static constexpr int MAX_STAGES = 4;
   static constexpr int BOX_BYTES = 128 * BK * 2;           // one 128-row box: 16 KB
-  static constexpr int STAGE_BYTES = 3 * BOX_BYTES;        // A_re, A_im, B
+  static constexpr int STAGE_BYTES = 3 * BOX_BYTES;        // A, B_re, B_im
   static constexpr int ACC_COLS = 2 * BN;                  // Re and Im accumulators of a tile
   static constexpr int TMEM_COLS = 512;                    // two accumulator buffers
   static constexpr int EPI_WARPS = 4;
   static constexpr int NTHREADS = 32 * (2 + EPI_WARPS);    // producer, MMA, epilogue
-  static constexpr uint32_t IDESC = idesc_bf16_f32(BM, BN);
+  static constexpr uint32_t IDESC = idesc_bf16_f32(BM, 2 * BN);
   static_assert(2 * ACC_COLS <= TMEM_COLS, "tensor memory");
+  static_assert(2 * BN <= 256 && BOX_BYTES % 1024 == 0, "B_re and B_im form one swizzled 256-row operand");
 };
 
 // (read tile, window range) of item `it`; false for the padding items of the
@@ -282,7 +287,8 @@ __device__ __forceinline__ bool gemm_item(const GemmArgs& g, int64_t it, int& rt
 // appended at an atomically taken index of g.thr's bounded arrays.
 template <int kMode>
 __global__ void __launch_bounds__(GemmShape::NTHREADS, 1)
-    gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, GemmArgs g) {
+    gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                   const __grid_constant__ CUtensorMap tmBi, GemmArgs g) {
   using Sh = GemmShape;
   constexpr bool kDense = kMode == 1, kThr = kMode == 2, kLists = kMode == 0;
   extern __shared__ __align__(1024) uint8_t gm_raw[];
@@ -313,6 +319,7 @@ __global__ void __launch_bounds__(GemmShape::NTHREADS, 1)
     fence_barrier_init();
     prefetch_tensor_map(&tmA);
     prefetch_tensor_map(&tmB);
+    prefetch_tensor_map(&tmBi);
   }
   if (warp == 1) {
     tmem_alloc(&tmem_base_s, Sh::TMEM_COLS);
@@ -343,8 +350,8 @@ __global__ void __launch_bounds__(GemmShape::NTHREADS, 1)
             uint8_t* st = stages + (size_t)stage * Sh::STAGE_BYTES;
             mbar_expect_tx(&bar_full[stage], Sh::STAGE_BYTES);
             tma_load_2d(st, &tmA, kb * Sh::BK, rt * Sh::BM, &bar_full[stage]);
-            tma_load_2d(st + Sh::BOX_BYTES, &tmA, kb * Sh::BK, g.a_im_row0 + rt * Sh::BM, &bar_full[stage]);
-            tma_load_2d(st + 2 * Sh::BOX_BYTES, &tmB, kb * Sh::BK, (int32_t)w0, &bar_full[stage]);
+            tma_load_2d(st + Sh::BOX_BYTES, &tmB, kb * Sh::BK, (int32_t)w0, &bar_full[stage]);
+            tma_load_2d(st + 2 * Sh::BOX_BYTES, &tmBi, kb * Sh::BK, (int32_t)w0, &bar_full[stage]);
             ++issued;
             if (++stage == (uint32_t)ns) {
               stage = 0;
@@ -374,7 +381,7 @@ __global__ void __launch_bounds__(GemmShape::NTHREADS, 1)
             break;
           }
           tc_fence_after();
-          const uint32_t d_re = tbase + buf * Sh::ACC_COLS, d_im = d_re + Sh::BN;
+          const uint32_t d = tbase + buf * Sh::ACC_COLS;  // Re: columns [0, BN), Im: [BN, 2 BN)
           for (int kb = 0; kb < g.k_blocks; ++kb) {
             if (!mbar_wait(&bar_full[stage], phase, abort_flag, g.status, wlim)) {
               ok = false;
@@ -382,14 +389,13 @@ __global__ void __launch_bounds__(GemmShape::NTHREADS, 1)
             }
             tc_fence_after();
             const uint32_t base = smem_u32(stages + (size_t)stage * Sh::STAGE_BYTES);
-            const uint64_t a_re = smem_desc_sw128(base), a_im = smem_desc_sw128(base + Sh::BOX_BYTES);
-            const uint64_t b = smem_desc_sw128(base + 2 * Sh::BOX_BYTES);
+            const uint64_t a = smem_desc_sw128(base);
+            const uint64_t b = smem_desc_sw128(base + Sh::BOX_BYTES);  // 256 rows: B_re then B_im
 #pragma unroll
             for (int kk = 0; kk < Sh::BK / 16; ++kk) {
               const uint32_t acc = (kb > 0 || kk > 0) ? 1u : 0u;
               // K step kk: 32 bytes further along the 128-byte rows (16-byte units)
-              tc_mma_ss(d_re, a_re + 2 * kk, b + 2 * kk, Sh::IDESC, acc);
-              tc_mma_ss(d_im, a_im + 2 * kk, b + 2 * kk, Sh::IDESC, acc);
+              tc_mma_ss(d, a + 2 * kk, b + 2 * kk, Sh::IDESC, acc);
             }
             tc_commit(&bar_empty[stage]);
             if (++stage == (uint32_t)ns) {
@@ -638,6 +644,11 @@ cudaError_t launch_dense_fp32(const DevIndex& ix, const GemmArgs& g, const float
   int64_t grid = n_items < (int64_t)num_sms * 2 ? n_items : (int64_t)num_sms * 2;
   if (grid < 1) return cudaSuccess;
   const size_t smem = (size_t)g.cand_depth * kF32Tile * 8;
+  // lists of up to 32 entries (16 KB) beside 33 KB of static tiles: past the
+  // default 48 KB per block
+  const cudaError_t attr =
+      cudaFuncSetAttribute(dense_fp32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (attr != cudaSuccess) return attr;
   dense_fp32_kernel<<<(unsigned)grid, 256, smem, st>>>(ix, g, emb, norms);
   return cudaGetLastError();
 }
@@ -663,8 +674,8 @@ int gemm_tc_stages(int cand_depth) {
   return 0;
 }
 
-cudaError_t launch_gemm_tc(const CUtensorMap& tmA, const CUtensorMap& tmB, const GemmArgs& g, int mode,
-                           int num_sms, cudaStream_t st) {
+cudaError_t launch_gemm_tc(const CUtensorMap& tmA, const CUtensorMap& tmB, const CUtensorMap& tmBi,
+                           const GemmArgs& g, int mode, int num_sms, cudaStream_t st) {
   const int64_t n_items = (int64_t)((g.n_rt + g.grp - 1) / g.grp) * g.grp * g.n_ranges;
   const int grid = (int)(n_items < num_sms ? n_items : num_sms);
   if (grid < 1) return cudaSuccess;
@@ -675,7 +686,7 @@ cudaError_t launch_gemm_tc(const CUtensorMap& tmA, const CUtensorMap& tmB, const
       cudaGetLastError();
       return e;
     }
-    kern<<<grid, GemmShape::NTHREADS, smem, st>>>(tmA, tmB, g);
+    kern<<<grid, GemmShape::NTHREADS, smem, st>>>(tmA, tmB, tmBi, g);
     return cudaGetLastError();
   };
   return mode == 1 ? go(gemm_tc_kernel<1>) : mode == 2 ? go(gemm_tc_kernel<2>) : go(gemm_tc_kernel<0>);

@@ -73,7 +73,8 @@ struct rope_index {
   rope::EncTables enc{};
   std::vector<void*> owned;
   // materialised index (rope_encode_reference_dense, or any encoding wider
-  // than the on-the-fly scans take): the window matrix's TMA descriptor
+  // than the on-the-fly scans take): TMA descriptors of the window matrices
+  // [cr | ci] and [ci | -cr]
   bool dense = false;
-  CUtensorMap tm_win{};
+  CUtensorMap tm_win{}, tm_win_im{};
 };

@@ -144,10 +144,11 @@ struct DenseTables {
   const float2* tph;     // [m * n_t] +-exp(2 pi i f_k (t0 + i) / N)
 };
 // block sums into bsum [n_blocks, D] (scratch), then every window's FP32 row
-// [W, 2D], normalised BF16 row [W, 2D] and 1/|c| [W]
+// [W, 2D], normalised BF16 rows [cr | ci] and [ci | -cr] ([W, 2D] each) and
+// 1/|c| [W]
 cudaError_t launch_dense_index(const DevIndex& ix, const DenseTables& dt, float2* bsum, float* win_f32,
-                               uint16_t* win_bf16, float* inv_norm, cudaStream_t st);
-// the scan's A operand [2 n_pad, 2D]: [xr | xi] rows then [-xi | xr] rows
+                               uint16_t* win_bf16, uint16_t* win_bf16_im, float* inv_norm, cudaStream_t st);
+// the scan's A operand [n_pad, 2D]: the reads' [xr | xi] rows, zero past n
 cudaError_t launch_gemm_a(const uint16_t* emb, int64_t n, int64_t n_pad, int D, uint16_t* a, cudaStream_t st);
 struct GemmArgs {
   int64_t n_reads;
@@ -155,7 +156,6 @@ struct GemmArgs {
   int32_t grp;           // read tiles per wave
   int32_t n_ranges;      // window ranges (candidate lists per read)
   int32_t k_blocks;      // 2D / 64
-  int32_t a_im_row0;     // first [-xi | xr] row of the A operand (n_pad)
   int32_t stages;        // shared-memory pipeline depth
   int64_t jb, je;        // scanned windows [jb, je)
   int64_t range_len;     // windows per range (multiple of 128)
@@ -201,8 +201,8 @@ int gemm_tc_group();       // reads per tile
 int gemm_tc_window_tile(); // windows per tile
 int gemm_tc_stages(int cand_depth);  // deepest pipeline that fits (0: none)
 // mode 0: top-k lists, 1: every score (dense), 2: threshold pairs
-cudaError_t launch_gemm_tc(const CUtensorMap& tmA, const CUtensorMap& tmB, const GemmArgs& g, int mode,
-                           int num_sms, cudaStream_t st);
+cudaError_t launch_gemm_tc(const CUtensorMap& tmA, const CUtensorMap& tmB, const CUtensorMap& tmBi,
+                           const GemmArgs& g, int mode, int num_sms, cudaStream_t st);
 
 // rope_rerank.cu
 constexpr int kMaxFeatures = 32;

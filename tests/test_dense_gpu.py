@@ -186,10 +186,11 @@ def test_dense_topk_fp32_plain(lib, long_reads):
     check_topk(c["ref"], c["rd"], c["op"], gw, gs, c["ow"], c["os"], 8, f32_tol)
     clear = c["os"][:, 0] - c["os"][:, 1] > f32_tol(c["os"][:, 0])
     assert np.array_equal(gw[clear, 0], c["ow"][clear, 0])
-    # a window sub-range with buckets, three read tiles of 64 (the last ragged)
+    # a window sub-range with buckets, three read tiles of 64 (the last ragged),
+    # the deepest candidate lists (32 entries: 16 KB of lists per block)
     k, sep = 4, 5000
     gw, gs = lib.rope_score_topk(c["idx"], c["f32"][:150], None, c["norms"][:150], k=k, sep=sep, precision="fp32",
-                                 j_begin=50, j_end=700)
+                                 j_begin=50, j_end=700, cand_depth=32)
     lib.rope_sync_status()
     sub = c["rd"].subset(np.arange(150))
     ow, os_ = oracle.score_topk(c["ref"], sub.seqs, sub.offsets, c["op"], k=k + 1, sep=sep, j_begin=50, j_end=700)
