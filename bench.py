@@ -850,12 +850,15 @@ def main():
     if rank == 0 and ws == 1 and not args.no_cpu:
         cpu = cpu_baseline(ref, rd, wl, wl.get("cpu_reads", args.cpu_reads), wl.get("cpu_windows", args.cpu_windows))
 
+    # bytes one scan pass streams: the packed reference and 8 B of anchors and
+    # norms per window, or the materialised index's two BF16 window matrices
+    index_gb = (W * 2 * p.dim * 2 if dense_index else wl['L'] / 4 + 8 * W) / 1e9
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1000.0 * elapsed / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
         "config": {"workload": args.workload + ": " + wl["desc"], "reads_per_step_per_gpu": B, "n_windows": W,
-                   "scores_per_step_per_gpu": scores_step, "l2": f"inputs larger than L2 ({(wl['L'] / 4 + 8 * W) / 1e9:.1f} GB index "
+                   "scores_per_step_per_gpu": scores_step, "l2": f"inputs larger than L2 ({index_gb:.1f} GB index "
                    f"streamed per scan pass; reads {B * wl['read_len'] / 1e6:.0f} MB/step)", "index_build_s": index_s, "parallelism": f"replicated index, "
                    f"reads sharded over {ws} GPU(s)",
                    "scan_tiles": None if tuned is None else {"variant": tuned[0], "items_per_sm": tuned[1],

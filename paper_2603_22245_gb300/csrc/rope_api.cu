@@ -1095,8 +1095,30 @@ rope_status dense_scan(const rope_index* idx, const uint16_t* emb_bf16, const fl
   const int slots = fp32 ? 2 * c->num_sms : c->num_sms;  // blocks resident at once
   int grp, n_ranges;
   if ((int64_t)n_rt * 4 >= slots) {
+    // 4..8 ranges: the split whose busiest block scans the fewest window
+    // tiles (items go to blocks round-robin; padding items cost nothing), so
+    // that the last wave leaves few blocks idle; ties to fewer ranges
+    int64_t best = -1;
     n_ranges = 4;
     grp = std::max(1, slots / 4);
+    for (int nr = 4; nr <= 8; ++nr) {
+      const int gp = std::max(1, slots / nr);
+      const int64_t per_wave = (int64_t)gp * nr, waves = (n_rt + gp - 1) / gp;
+      const int64_t n_items = waves * per_wave, grid = std::min<int64_t>(n_items, slots);
+      int64_t busiest = 0;
+      for (int64_t b = 0; b < grid; ++b) {
+        int64_t cnt = 0;
+        for (int64_t it = b; it < n_items; it += grid)
+          cnt += (it / per_wave) * gp + (it % per_wave) % gp < n_rt;
+        busiest = std::max(busiest, cnt);
+      }
+      const int64_t cost = busiest * ((n_wt + nr - 1) / nr);
+      if (best < 0 || cost < best) {
+        best = cost;
+        n_ranges = nr;
+        grp = gp;
+      }
+    }
   } else {
     grp = n_rt;
     n_ranges = std::max(1, slots / n_rt);

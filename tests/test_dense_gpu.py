@@ -211,3 +211,29 @@ def test_dense_refusals(lib, long_reads):
     with pytest.raises(lib.RopeError) as e:  # 4^1 x 1 = 4 complex dimensions: not a multiple of 32
         lib.rope_encode_reference_dense(lib.Params(s=1, m=1, t=1, window_len=50), dev(synth.uniform_ref(1000, 1)))
     assert e.value.status == 6
+
+
+@pytest.mark.parametrize("precision,tol", [("bf16", f32_tol), ("fp32", f32_tol)])
+def test_dense_topk_many_read_tiles(lib, precision, tol):
+    """Enough reads that the work split runs in waves: 5000 reads (40 tiles of
+    128 for the GEMM, 79 of 64 for the FP32 scan, the last ragged) against a
+    materialised index of 8550 windows (67 tiles); the split takes between 4
+    and 8 window ranges per read and waves whose items need not fill the grid
+    exactly. Re-scored top-k against the oracle's, top-1 exact where clear."""
+    op = oracle.Params(s=4, m=2, t=2, variant=1, N=150, stride=7)
+    ref = synth.markov_ref(60_000, 0.41, 241, 0.05, 0.05)
+    rd = synth.reads(ref, 5000, seed=242, length=150)
+    p = gparams(lib, 4, 2, 2, 150, 7)
+    idx = lib.rope_encode_reference_dense(p, dev(ref))
+    f32, bf16, norms = lib.rope_encode_reads(p, dev(rd.seqs), dev(rd.offsets))
+    k = 4
+    gw, gs = lib.rope_score_topk(idx, f32, bf16 if precision == "bf16" else None, norms, k=k, precision=precision,
+                                 rescore=1 if precision == "bf16" else None)
+    lib.rope_sync_status()
+    gw, gs = gw.cpu().numpy(), gs.cpu().numpy().astype(np.float64)
+    ow, os_ = oracle.score_topk(ref, rd.seqs, rd.offsets, op, k=k + 1)
+    check_topk(ref, rd, op, gw, gs, ow, os_, k, tol)
+    clear = os_[:, 0] - os_[:, 1] > tol(os_[:, 0])
+    assert clear.sum() > 1000
+    assert np.array_equal(gw[clear, 0], ow[clear, 0])
+    idx.free()
