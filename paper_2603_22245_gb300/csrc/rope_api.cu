@@ -1095,30 +1095,8 @@ rope_status dense_scan(const rope_index* idx, const uint16_t* emb_bf16, const fl
   const int slots = fp32 ? 2 * c->num_sms : c->num_sms;  // blocks resident at once
   int grp, n_ranges;
   if ((int64_t)n_rt * 4 >= slots) {
-    // 4..8 ranges: the split whose busiest block scans the fewest window
-    // tiles (items go to blocks round-robin; padding items cost nothing), so
-    // that the last wave leaves few blocks idle; ties to fewer ranges
-    int64_t best = -1;
     n_ranges = 4;
     grp = std::max(1, slots / 4);
-    for (int nr = 4; nr <= 8; ++nr) {
-      const int gp = std::max(1, slots / nr);
-      const int64_t per_wave = (int64_t)gp * nr, waves = (n_rt + gp - 1) / gp;
-      const int64_t n_items = waves * per_wave, grid = std::min<int64_t>(n_items, slots);
-      int64_t busiest = 0;
-      for (int64_t b = 0; b < grid; ++b) {
-        int64_t cnt = 0;
-        for (int64_t it = b; it < n_items; it += grid)
-          cnt += (it / per_wave) * gp + (it % per_wave) % gp < n_rt;
-        busiest = std::max(busiest, cnt);
-      }
-      const int64_t cost = busiest * ((n_wt + nr - 1) / nr);
-      if (best < 0 || cost < best) {
-        best = cost;
-        n_ranges = nr;
-        grp = gp;
-      }
-    }
   } else {
     grp = n_rt;
     n_ranges = std::max(1, slots / n_rt);
@@ -1126,11 +1104,13 @@ rope_status dense_scan(const rope_index* idx, const uint16_t* emb_bf16, const fl
   if (n_ranges > n_wt) n_ranges = (int)std::max<int64_t>(1, n_wt);
   const int64_t tiles_per_range = n_wt > 0 ? (n_wt + n_ranges - 1) / n_ranges : 1;
   if (n_wt > 0) n_ranges = (int)((n_wt + tiles_per_range - 1) / tiles_per_range);
-  const int stages = fp32 ? 2 : gemm_tc_stages(mode == 0 ? o.cand_depth : 0);
+  const int k_blocks = 2 * ix.D / 64;
+  const int stages = fp32 ? 2 : gemm_tc_stages(mode == 0 ? o.cand_depth : 0, k_blocks);
+  const int lists = fp32 ? 1 : gemm_tc_lists(k_blocks);  // candidate lists per (read, range)
   if (stages < 2) return fail(ROPE_ERR_UNSUPPORTED, "cand_depth=%d: the GEMM scan does not fit in shared memory", o.cand_depth);
   auto al = [](size_t b) { return (b + 255) & ~size_t(255); };
   const size_t a_bytes = fp32 ? 0 : al((size_t)n_pad * 2 * ix.D * sizeof(uint16_t));
-  const size_t cand_bytes = mode != 0 ? 0 : (size_t)n_reads * n_ranges * o.cand_depth * sizeof(Candidate);
+  const size_t cand_bytes = mode != 0 ? 0 : (size_t)n_reads * n_ranges * lists * o.cand_depth * sizeof(Candidate);
   uint8_t* scratch = nullptr;
   if ((st = pool_alloc(c, (void**)&scratch, a_bytes + cand_bytes, stream)) != ROPE_OK) return st;
   uint16_t* a_op = reinterpret_cast<uint16_t*>(scratch);
@@ -1166,7 +1146,7 @@ rope_status dense_scan(const rope_index* idx, const uint16_t* emb_bf16, const fl
     g.n_rt = n_rt;
     g.grp = grp;
     g.n_ranges = n_ranges;
-    g.k_blocks = 2 * ix.D / 64;
+    g.k_blocks = k_blocks;
     g.stages = stages;
     g.jb = jb;
     g.je = je;
@@ -1190,7 +1170,7 @@ rope_status dense_scan(const rope_index* idx, const uint16_t* emb_bf16, const fl
   MergeArgs m{};
   m.cand = cand;
   m.n_reads = n_reads;
-  m.n_ranges = n_ranges;
+  m.n_ranges = n_ranges * lists;
   m.cand_depth = o.cand_depth;
   m.k = o.k;
   m.sep = o.sep;

@@ -250,20 +250,38 @@ cudaError_t launch_gemm_a(const uint16_t* emb, int64_t n, int64_t n_pad, int D, 
 
 // ---------------------------------------------------------------- tensor-core scan
 
+// Two shapes of the same scan. Long K (2D > 128, e.g. the long-read 2D = 2048):
+// every stage brings one K block of A, B_re and B_im; one epilogue warp per
+// tensor-memory lane quarter. Short K (2D <= 128: the d = 64 and d = 128
+// encodings): the read tile's A (at most two K blocks) stays resident in shared
+// memory for the whole work item, stages carry only the window boxes, and two
+// epilogue warps share each lane quarter (half of the tile's columns and their
+// own candidate list each): with so few MMAs per tile, the epilogue, not the
+// tensor pipe, would otherwise set the pace.
+template <bool kShort>
 struct GemmShape {
   static constexpr int BM = 128;                 // reads per tile (tensor-memory lanes)
   static constexpr int BN = 128;                 // windows per tile (MMA N = 2 BN: Re and Im rows)
   static constexpr int BK = 64;                  // K per stage: one 128-byte swizzled BF16 row
-  static constexpr int MAX_STAGES = 4;
   static constexpr int BOX_BYTES = 128 * BK * 2;           // one 128-row box: 16 KB
-  static constexpr int STAGE_BYTES = 3 * BOX_BYTES;        // A, B_re, B_im
+  static constexpr int STAGE_BYTES = (kShort ? 2 : 3) * BOX_BYTES;  // [A,] B_re, B_im
+  static constexpr int MAX_STAGES = kShort ? 5 : 4;
+  static constexpr int MAX_RES_KB = 2;           // short K: resident A of at most 2 K blocks
+  static constexpr int EQ = kShort ? 2 : 1;      // epilogue warps per lane quarter
+  static constexpr int WCOLS = BN / EQ;          // windows per epilogue warp per tile
   static constexpr int ACC_COLS = 2 * BN;                  // Re and Im accumulators of a tile
   static constexpr int TMEM_COLS = 512;                    // two accumulator buffers
-  static constexpr int EPI_WARPS = 4;
+  static constexpr int EPI_WARPS = 4 * EQ;
   static constexpr int NTHREADS = 32 * (2 + EPI_WARPS);    // producer, MMA, epilogue
   static constexpr uint32_t IDESC = idesc_bf16_f32(BM, 2 * BN);
   static_assert(2 * ACC_COLS <= TMEM_COLS, "tensor memory");
   static_assert(2 * BN <= 256 && BOX_BYTES % 1024 == 0, "B_re and B_im form one swizzled 256-row operand");
+  static_assert(WCOLS % 16 == 0, "the epilogue loads 16-column chunks");
+  // dynamic shared memory: [resident A][stages][lists], 1024-aligned
+  static size_t smem_bytes(int stages, int cand_depth, int k_blocks) {
+    return 1024 + (kShort ? (size_t)k_blocks * BOX_BYTES : 0) + (size_t)stages * STAGE_BYTES +
+           (size_t)cand_depth * BM * EQ * 8;
+  }
 };
 
 // (read tile, window range) of item `it`; false for the padding items of the
@@ -285,21 +303,23 @@ __device__ __forceinline__ bool gemm_item(const GemmArgs& g, int64_t it, int& rt
 // kMode 0: per-read candidate lists (top-k); 1: every score into g.dense;
 // 2: every pair whose score reaches its window's threshold g.thr.thr[j],
 // appended at an atomically taken index of g.thr's bounded arrays.
-template <int kMode>
-__global__ void __launch_bounds__(GemmShape::NTHREADS, 1)
+template <int kMode, bool kShort>
+__global__ void __launch_bounds__(GemmShape<kShort>::NTHREADS, 1)
     gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                    const __grid_constant__ CUtensorMap tmBi, GemmArgs g) {
-  using Sh = GemmShape;
+  using Sh = GemmShape<kShort>;
   constexpr bool kDense = kMode == 1, kThr = kMode == 2, kLists = kMode == 0;
   extern __shared__ __align__(1024) uint8_t gm_raw[];
   __shared__ __align__(8) uint64_t bar_full[Sh::MAX_STAGES], bar_empty[Sh::MAX_STAGES];
-  __shared__ __align__(8) uint64_t bar_accfull[2], bar_accempty[2], bar_drain;
+  __shared__ __align__(8) uint64_t bar_accfull[2], bar_accempty[2], bar_drain, bar_afull, bar_aempty;
   __shared__ uint32_t tmem_base_s;
   __shared__ int abort_s;
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(gm_raw) + 1023) & ~uintptr_t(1023));
-  uint8_t* stages = smem;
-  float* list_s = reinterpret_cast<float*>(smem + (size_t)g.stages * Sh::STAGE_BYTES);
-  uint32_t* list_w = reinterpret_cast<uint32_t*>(list_s + (size_t)g.cand_depth * Sh::BM);
+  const int kbl = g.k_blocks;
+  uint8_t* a_res = smem;  // short K: the item's A tile, kbl K blocks
+  uint8_t* stages = smem + (kShort ? (size_t)kbl * Sh::BOX_BYTES : 0);
+  float* list_s = reinterpret_cast<float*>(stages + (size_t)g.stages * Sh::STAGE_BYTES);
+  uint32_t* list_w = reinterpret_cast<uint32_t*>(list_s + (size_t)g.cand_depth * Sh::BM * Sh::EQ);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const uint64_t wlim = g.wait_limit_ns;
   volatile int* abort_flag = &abort_s;
@@ -315,6 +335,8 @@ __global__ void __launch_bounds__(GemmShape::NTHREADS, 1)
       mbar_init(&bar_accempty[i], Sh::EPI_WARPS);
     }
     mbar_init(&bar_drain, 1);
+    mbar_init(&bar_afull, 1);
+    mbar_init(&bar_aempty, 1);
     abort_s = 0;
     fence_barrier_init();
     prefetch_tensor_map(&tmA);
@@ -334,24 +356,36 @@ __global__ void __launch_bounds__(GemmShape::NTHREADS, 1)
   if (warp == 0) {
     // ================================================================ TMA producer
     if (lane == 0) {
-      uint32_t stage = 0, phase = 0;
-      int64_t issued = 0;
+      uint32_t stage = 0, phase = 0, a_par = 0;
+      int64_t issued = 0, a_issued = 0;
       for (int64_t it = blockIdx.x; it < n_items; it += gridDim.x) {
         int rt, rg;
         int64_t w_lo, w_hi;
         if (!gemm_item(g, it, rt, rg, w_lo, w_hi)) continue;
         bool ok = true;
+        if constexpr (kShort) {
+          // the resident A tile: free once the previous item's MMAs completed
+          if (!mbar_wait(&bar_aempty, a_par ^ 1u, abort_flag, g.status, wlim)) break;
+          mbar_expect_tx(&bar_afull, (uint32_t)(kbl * Sh::BOX_BYTES));
+          for (int kb = 0; kb < kbl; ++kb)
+            tma_load_2d(a_res + (size_t)kb * Sh::BOX_BYTES, &tmA, kb * Sh::BK, rt * Sh::BM, &bar_afull);
+          a_par ^= 1u;
+          ++a_issued;
+        }
         for (int64_t w0 = w_lo; w0 < w_hi && ok; w0 += Sh::BN) {
-          for (int kb = 0; kb < g.k_blocks; ++kb) {
+          for (int kb = 0; kb < kbl; ++kb) {
             if (!mbar_wait(&bar_empty[stage], phase ^ 1u, abort_flag, g.status, wlim)) {
               ok = false;
               break;
             }
             uint8_t* st = stages + (size_t)stage * Sh::STAGE_BYTES;
             mbar_expect_tx(&bar_full[stage], Sh::STAGE_BYTES);
-            tma_load_2d(st, &tmA, kb * Sh::BK, rt * Sh::BM, &bar_full[stage]);
-            tma_load_2d(st + Sh::BOX_BYTES, &tmB, kb * Sh::BK, (int32_t)w0, &bar_full[stage]);
-            tma_load_2d(st + 2 * Sh::BOX_BYTES, &tmBi, kb * Sh::BK, (int32_t)w0, &bar_full[stage]);
+            if constexpr (!kShort) {
+              tma_load_2d(st, &tmA, kb * Sh::BK, rt * Sh::BM, &bar_full[stage]);
+              st += Sh::BOX_BYTES;
+            }
+            tma_load_2d(st, &tmB, kb * Sh::BK, (int32_t)w0, &bar_full[stage]);
+            tma_load_2d(st + Sh::BOX_BYTES, &tmBi, kb * Sh::BK, (int32_t)w0, &bar_full[stage]);
             ++issued;
             if (++stage == (uint32_t)ns) {
               stage = 0;
@@ -361,19 +395,26 @@ __global__ void __launch_bounds__(GemmShape::NTHREADS, 1)
         }
         if (!ok) break;
       }
-      // the latest copy into each stage may still be in flight (after an abort)
+      // the latest copy into each stage (and into the A tile) may still be in
+      // flight (after an abort)
       for (int64_t i = issued > ns ? issued - ns : 0; i < issued; ++i)
         mbar_drain_wait(&bar_full[i % ns], (uint32_t)((i / ns) & 1), g.status, wlim);
+      if (kShort && a_issued > 0) mbar_drain_wait(&bar_afull, (uint32_t)((a_issued - 1) & 1), g.status, wlim);
     }
   } else if (warp == 1) {
     // ================================================================ MMA issue
     if (lane == 0) {
-      uint32_t stage = 0, phase = 0, t = 0;
+      uint32_t stage = 0, phase = 0, t = 0, a_par = 0;
       bool ok = true;
       for (int64_t it = blockIdx.x; it < n_items && ok; it += gridDim.x) {
         int rt, rg;
         int64_t w_lo, w_hi;
         if (!gemm_item(g, it, rt, rg, w_lo, w_hi)) continue;
+        if constexpr (kShort) {
+          if (!mbar_wait(&bar_afull, a_par, abort_flag, g.status, wlim)) break;
+          a_par ^= 1u;
+          tc_fence_after();
+        }
         for (int64_t w0 = w_lo; w0 < w_hi && ok; w0 += Sh::BN, ++t) {
           const uint32_t buf = t & 1u;
           if (!mbar_wait(&bar_accempty[buf], ((t >> 1) & 1u) ^ 1u, abort_flag, g.status, wlim)) {
@@ -382,15 +423,17 @@ __global__ void __launch_bounds__(GemmShape::NTHREADS, 1)
           }
           tc_fence_after();
           const uint32_t d = tbase + buf * Sh::ACC_COLS;  // Re: columns [0, BN), Im: [BN, 2 BN)
-          for (int kb = 0; kb < g.k_blocks; ++kb) {
+          for (int kb = 0; kb < kbl; ++kb) {
             if (!mbar_wait(&bar_full[stage], phase, abort_flag, g.status, wlim)) {
               ok = false;
               break;
             }
             tc_fence_after();
             const uint32_t base = smem_u32(stages + (size_t)stage * Sh::STAGE_BYTES);
-            const uint64_t a = smem_desc_sw128(base);
-            const uint64_t b = smem_desc_sw128(base + Sh::BOX_BYTES);  // 256 rows: B_re then B_im
+            const uint64_t a = kShort ? smem_desc_sw128(smem_u32(a_res) + (uint32_t)kb * Sh::BOX_BYTES)
+                                      : smem_desc_sw128(base);
+            // 256 rows: B_re then B_im
+            const uint64_t b = smem_desc_sw128(base + (kShort ? 0u : (uint32_t)Sh::BOX_BYTES));
 #pragma unroll
             for (int kk = 0; kk < Sh::BK / 16; ++kk) {
               const uint32_t acc = (kb > 0 || kk > 0) ? 1u : 0u;
@@ -405,6 +448,8 @@ __global__ void __launch_bounds__(GemmShape::NTHREADS, 1)
           }
           if (ok) tc_commit(&bar_accfull[buf]);
         }
+        // the resident A tile is free once this item's MMAs have completed
+        if (kShort) tc_commit(&bar_aempty);
       }
       // every MMA issued by this thread has completed (also after an abort)
       tc_commit(&bar_drain);
@@ -412,12 +457,16 @@ __global__ void __launch_bounds__(GemmShape::NTHREADS, 1)
     }
   } else {
     // ================================================================ epilogue
-    // thread = one read (tensor-memory lane 32q + lane of its warp's quarter)
+    // thread = one read (tensor-memory lane 32q + lane of its warp's quarter);
+    // with EQ warps per quarter, warp h of a quarter takes the tile's columns
+    // [h WCOLS, (h + 1) WCOLS) and keeps its own list for them
     const int q = warp & 3;
+    const int h = (warp - 2) >> 2;
     const int row = 32 * q + lane;
     const uint32_t lane_base = (uint32_t)(32 * q) << 16;
-    float* ls = list_s + row;
-    uint32_t* lw = list_w + row;
+    constexpr int LSTR = Sh::BM * Sh::EQ;  // list entry stride
+    float* ls = list_s + h * Sh::BM + row;
+    uint32_t* lw = list_w + h * Sh::BM + row;
     uint32_t t = 0;
     const int64_t n_dense = g.je - g.jb;
     for (int64_t it = blockIdx.x; it < n_items; it += gridDim.x) {
@@ -430,32 +479,23 @@ __global__ void __launch_bounds__(GemmShape::NTHREADS, 1)
       int worst = 0;
       if (kLists) {
         for (int e = 0; e < g.cand_depth; ++e) {
-          ls[e * Sh::BM] = -INFINITY;
-          lw[e * Sh::BM] = kEmptyWin;
+          ls[e * LSTR] = -INFINITY;
+          lw[e * LSTR] = kEmptyWin;
         }
       }
       for (int64_t w0 = w_lo; w0 < w_hi; w0 += Sh::BN, ++t) {
         const uint32_t buf = t & 1u;
         if (!mbar_wait_warp(&bar_accfull[buf], (t >> 1) & 1u, abort_flag, g.status, wlim)) goto epi_done;
         tc_fence_after();
-        const bool full = w0 + Sh::BN <= w_hi;
-#pragma unroll 1
-        for (int c0 = 0; c0 < Sh::BN; c0 += 16) {
-          const uint32_t taddr = tbase + lane_base + buf * Sh::ACC_COLS + (uint32_t)c0;
-          uint32_t vr[16], vi[16];
-          tmem_ld16(taddr, vr);
-          tmem_ld16(taddr + Sh::BN, vi);
-          tc_wait_ld();
-          if (c0 + 16 == Sh::BN) {
-            // the tile's last columns are in registers: hand the buffer back
-            tc_fence_before();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&bar_accempty[buf]);
-          }
+        const int64_t wc = w0 + h * Sh::WCOLS;  // this warp's first window
+        const bool full = wc + Sh::WCOLS <= w_hi;
+        const uint32_t tcol = tbase + lane_base + buf * Sh::ACC_COLS + (uint32_t)(h * Sh::WCOLS);
+        // the 16 windows from column c0 of this warp's share: Re in vr, Im in vi
+        auto chunk = [&](const uint32_t* vr, const uint32_t* vi, int c0) {
           float sc[16];
 #pragma unroll
           for (int n = 0; n < 16; n += 2) abs2_pair(vr[n], vr[n + 1], vi[n], vi[n + 1], sc[n], sc[n + 1]);
-          const int64_t jc = w0 + c0;
+          const int64_t jc = wc + c0;
           if constexpr (kThr) {
             // lane l holds the threshold of window jc + (l & 15) (+inf outside
             // the range); the chunk's smallest threshold decides whether any
@@ -500,18 +540,54 @@ __global__ void __launch_bounds__(GemmShape::NTHREADS, 1)
             if (have && mx >= thr) {
               for (int n = 0; n < 16; ++n) {
                 if (jc + n >= w_hi || !(sc[n] >= thr)) continue;
-                const ListState nsl = list_insert(ls, lw, Sh::BM, g.cand_depth, worst, sc[n], (uint32_t)(jc + n),
+                const ListState nsl = list_insert(ls, lw, LSTR, g.cand_depth, worst, sc[n], (uint32_t)(jc + n),
                                                   g.sep, g.stride);
                 thr = nsl.thr;
                 worst = nsl.worst;
               }
             }
           }
+        };
+        if constexpr (kShort) {
+          // every column of this warp's share in registers at once: one exposed
+          // tensor-memory load latency per tile instead of one per chunk
+          uint32_t vr[Sh::WCOLS], vi[Sh::WCOLS];
+#pragma unroll
+          for (int u = 0; u < Sh::WCOLS; u += 16) {
+            tmem_ld16(tcol + u, *reinterpret_cast<uint32_t(*)[16]>(&vr[u]));
+            tmem_ld16(tcol + Sh::BN + u, *reinterpret_cast<uint32_t(*)[16]>(&vi[u]));
+          }
+          tc_wait_ld();
+          reg_fence(vr);
+          reg_fence(vi);
+          // all of this warp's columns are in registers: hand the buffer back
+          tc_fence_before();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&bar_accempty[buf]);
+#pragma unroll
+          for (int c0 = 0; c0 < Sh::WCOLS; c0 += 16) chunk(vr + c0, vi + c0, c0);
+        } else {
+#pragma unroll 1
+          for (int c0 = 0; c0 < Sh::WCOLS; c0 += 16) {
+            uint32_t vr[16], vi[16];
+            tmem_ld16(tcol + c0, vr);
+            tmem_ld16(tcol + Sh::BN + c0, vi);
+            tc_wait_ld();
+            reg_fence(vr);
+            reg_fence(vi);
+            if (c0 + 16 == Sh::WCOLS) {
+              // this warp's last columns are in registers: hand the buffer back
+              tc_fence_before();
+              __syncwarp();
+              if (lane == 0) mbar_arrive(&bar_accempty[buf]);
+            }
+            chunk(vr, vi, c0);
+          }
         }
       }
       if (kLists && have) {
-        Candidate* out = g.cand + ((size_t)r * g.n_ranges + rg) * g.cand_depth;
-        for (int e = 0; e < g.cand_depth; ++e) out[e] = Candidate{ls[e * Sh::BM], lw[e * Sh::BM]};
+        Candidate* out = g.cand + (((size_t)r * g.n_ranges + rg) * Sh::EQ + h) * g.cand_depth;
+        for (int e = 0; e < g.cand_depth; ++e) out[e] = Candidate{ls[e * LSTR], lw[e * LSTR]};
       }
     }
   epi_done:;
@@ -653,15 +729,13 @@ cudaError_t launch_dense_fp32(const DevIndex& ix, const GemmArgs& g, const float
   return cudaGetLastError();
 }
 
-int gemm_tc_group() { return GemmShape::BM; }
-int gemm_tc_window_tile() { return GemmShape::BN; }
+int gemm_tc_group() { return GemmShape<false>::BM; }
+int gemm_tc_window_tile() { return GemmShape<false>::BN; }
+int gemm_tc_lists(int k_blocks) { return k_blocks <= GemmShape<true>::MAX_RES_KB ? GemmShape<true>::EQ : 1; }
 
-// Shared memory of a launch with `stages` stages and lists of cand_depth.
-static size_t gemm_smem(int stages, int cand_depth) {
-  return 1024 + (size_t)stages * GemmShape::STAGE_BYTES + (size_t)cand_depth * GemmShape::BM * 8;
-}
-
-int gemm_tc_stages(int cand_depth) {
+// Deepest pipeline of the shape for k_blocks whose shared memory fits with
+// lists of cand_depth (0: none fits).
+int gemm_tc_stages(int cand_depth, int k_blocks) {
   int optin = 0, dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess ||
       cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) {
@@ -669,9 +743,13 @@ int gemm_tc_stages(int cand_depth) {
     return 0;
   }
   const size_t avail = (size_t)optin > 2048 ? (size_t)optin - 2048 : 0;  // static shared memory
-  for (int s = GemmShape::MAX_STAGES; s >= 2; --s)
-    if (gemm_smem(s, cand_depth) <= avail) return s;
-  return 0;
+  auto deepest = [&](auto shape) {
+    using Sh = decltype(shape);
+    for (int s = Sh::MAX_STAGES; s >= 2; --s)
+      if (Sh::smem_bytes(s, cand_depth, k_blocks) <= avail) return s;
+    return 0;
+  };
+  return k_blocks <= GemmShape<true>::MAX_RES_KB ? deepest(GemmShape<true>{}) : deepest(GemmShape<false>{});
 }
 
 cudaError_t launch_gemm_tc(const CUtensorMap& tmA, const CUtensorMap& tmB, const CUtensorMap& tmBi,
@@ -679,17 +757,26 @@ cudaError_t launch_gemm_tc(const CUtensorMap& tmA, const CUtensorMap& tmB, const
   const int64_t n_items = (int64_t)((g.n_rt + g.grp - 1) / g.grp) * g.grp * g.n_ranges;
   const int grid = (int)(n_items < num_sms ? n_items : num_sms);
   if (grid < 1) return cudaSuccess;
-  const size_t smem = gemm_smem(g.stages, mode == 0 ? g.cand_depth : 0);
-  auto go = [&](auto kern) -> cudaError_t {
+  const bool short_k = g.k_blocks <= GemmShape<true>::MAX_RES_KB;
+  const size_t smem = short_k ? GemmShape<true>::smem_bytes(g.stages, mode == 0 ? g.cand_depth : 0, g.k_blocks)
+                              : GemmShape<false>::smem_bytes(g.stages, mode == 0 ? g.cand_depth : 0, g.k_blocks);
+  auto go = [&](auto kern, int threads) -> cudaError_t {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) {
       cudaGetLastError();
       return e;
     }
-    kern<<<grid, GemmShape::NTHREADS, smem, st>>>(tmA, tmB, tmBi, g);
+    kern<<<grid, threads, smem, st>>>(tmA, tmB, tmBi, g);
     return cudaGetLastError();
   };
-  return mode == 1 ? go(gemm_tc_kernel<1>) : mode == 2 ? go(gemm_tc_kernel<2>) : go(gemm_tc_kernel<0>);
+  if (short_k) {
+    constexpr int T = GemmShape<true>::NTHREADS;
+    return mode == 1 ? go(gemm_tc_kernel<1, true>, T) : mode == 2 ? go(gemm_tc_kernel<2, true>, T)
+                                                                 : go(gemm_tc_kernel<0, true>, T);
+  }
+  constexpr int T = GemmShape<false>::NTHREADS;
+  return mode == 1 ? go(gemm_tc_kernel<1, false>, T) : mode == 2 ? go(gemm_tc_kernel<2, false>, T)
+                                                                : go(gemm_tc_kernel<0, false>, T);
 }
 
 }  // namespace rope

@@ -199,7 +199,8 @@ cudaError_t launch_dense_fp32(const DevIndex& ix, const GemmArgs& g, const float
                               cudaStream_t st);
 int gemm_tc_group();       // reads per tile
 int gemm_tc_window_tile(); // windows per tile
-int gemm_tc_stages(int cand_depth);  // deepest pipeline that fits (0: none)
+int gemm_tc_stages(int cand_depth, int k_blocks);  // deepest pipeline that fits (0: none)
+int gemm_tc_lists(int k_blocks);     // candidate lists per (read, window range)
 // mode 0: top-k lists, 1: every score (dense), 2: threshold pairs
 cudaError_t launch_gemm_tc(const CUtensorMap& tmA, const CUtensorMap& tmB, const CUtensorMap& tmBi,
                            const GemmArgs& g, int mode, int num_sms, cudaStream_t st);

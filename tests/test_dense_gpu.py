@@ -213,13 +213,15 @@ def test_dense_refusals(lib, long_reads):
     assert e.value.status == 6
 
 
-@pytest.mark.parametrize("precision,tol", [("bf16", f32_tol), ("fp32", f32_tol)])
+@pytest.mark.parametrize("precision,tol", [("bf16", bf16_tol), ("fp32", f32_tol)])
 def test_dense_topk_many_read_tiles(lib, precision, tol):
     """Enough reads that the work split runs in waves: 5000 reads (40 tiles of
     128 for the GEMM, 79 of 64 for the FP32 scan, the last ragged) against a
-    materialised index of 8550 windows (67 tiles); the split takes between 4
-    and 8 window ranges per read and waves whose items need not fill the grid
-    exactly. Re-scored top-k against the oracle's, top-1 exact where clear."""
+    materialised index of 8551 windows (67 tiles of 128); 4 window ranges per
+    read, waves of 38 (GEMM) or 76 (FP32) read tiles, the second wave partial.
+    At d = 64 the GEMM runs its short-K shape (resident read tile, two lists
+    per read and range). Re-scored top-k against the oracle's, top-1 exact
+    where clear."""
     op = oracle.Params(s=4, m=2, t=2, variant=1, N=150, stride=7)
     ref = synth.markov_ref(60_000, 0.41, 241, 0.05, 0.05)
     rd = synth.reads(ref, 5000, seed=242, length=150)
@@ -232,7 +234,10 @@ def test_dense_topk_many_read_tiles(lib, precision, tol):
     lib.rope_sync_status()
     gw, gs = gw.cpu().numpy(), gs.cpu().numpy().astype(np.float64)
     ow, os_ = oracle.score_topk(ref, rd.seqs, rd.offsets, op, k=k + 1)
-    check_topk(ref, rd, op, gw, gs, ow, os_, k, tol)
+    # the BF16 scan proposes candidates by BF16 scores (an oracle top-k window
+    # within the BF16 tolerance of the (k+1)-th may lose its place); every
+    # reported score is the FP32 re-score
+    check_topk(ref, rd, op, gw, gs, ow, os_, k, tol, f32_tol)
     clear = os_[:, 0] - os_[:, 1] > tol(os_[:, 0])
     assert clear.sum() > 1000
     assert np.array_equal(gw[clear, 0], ow[clear, 0])
