@@ -852,7 +852,8 @@ def main():
 
     # bytes one scan pass streams: the packed reference and 8 B of anchors and
     # norms per window, or the materialised index's two BF16 window matrices
-    index_gb = (W * 2 * p.dim * 2 if dense_index else wl['L'] / 4 + 8 * W) / 1e9
+    # ([W, 2D] each)
+    index_gb = (2 * W * 2 * p.dim * 2 if dense_index else wl['L'] / 4 + 8 * W) / 1e9
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1000.0 * elapsed / args.steps, "higher_is_better": True, "scaling": "weak",
