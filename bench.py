@@ -386,7 +386,8 @@ def encode_roofline(rm, p, dref, ref, rd, n_reads):
             "pack": {"bytes": b_pack, "ms": t_pack * 1e3, "achieved": b_pack / t_pack / 1e9,
                      "frac": b_pack / t_pack / 1e9 / peak, "letters": L},
             "encode_reads": {"bytes": b_enc, "ms": t_enc * 1e3, "achieved": b_enc / t_enc / 1e9,
-                             "frac": b_enc / t_enc / 1e9 / peak, "reads": n_reads}}
+                             "frac": b_enc / t_enc / 1e9 / peak, "reads": n_reads,
+                             "reads_timed": 10 * n_reads, "s_per_million_reads": t_enc / n_reads * 1e6}}
 
 
 def run_reference(args, wl):

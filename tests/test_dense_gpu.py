@@ -242,3 +242,51 @@ def test_dense_topk_many_read_tiles(lib, precision, tol):
     assert clear.sum() > 1000
     assert np.array_equal(gw[clear, 0], ow[clear, 0])
     idx.free()
+
+
+@pytest.mark.parametrize("s,m,t,N,stride", [(4, 2, 2, 150, 7), (4, 4, 2, 150, 10)])
+def test_dense_short_k_shape(lib, s, m, t, N, stride):
+    """The GEMM's short-K shape (2D = 64: one K block of the read tile kept in
+    shared memory; 2D = 128: two) on every output mode: every score of a
+    window sub-range with ragged tiles at the raw BF16 tolerance, the top-k
+    with buckets against the oracle's, and the threshold pairs against the
+    oracle's exhaustive set except pairs within the BF16 tolerance of their
+    window's threshold."""
+    op = oracle.Params(s=s, m=m, t=t, variant=1, N=N, stride=stride)
+    ref = synth.markov_ref(40_000, 0.41, 251, 0.05, 0.05)
+    rd = synth.reads(ref, 300, seed=252, length=N)
+    p = gparams(lib, s, m, t, N, stride)
+    idx = lib.rope_encode_reference_dense(p, dev(ref))
+    W = idx.n_windows
+    f32, bf16, norms = lib.rope_encode_reads(p, dev(rd.seqs), dev(rd.offsets))
+    # dense scores over [37, 37 + 333): three window tiles, the last ragged
+    j0, cnt, nr = 37, 333, 300
+    got = lib.rope_score_dense(idx, f32, bf16, norms, j0, cnt, precision="bf16").cpu().numpy().astype(np.float64)
+    lib.rope_sync_status()
+    wins = oracle.windows_direct(ref, op, j0, cnt)
+    X = np.stack([oracle.embed(rd.read(i), op) for i in range(nr)])
+    want = np.abs(X.conj() @ wins.T) ** 2 / (np.sum(np.abs(X) ** 2, axis=1)[:, None] *
+                                              np.sum(np.abs(wins) ** 2, axis=1)[None, :])
+    assert np.all(np.abs(got - want) <= bf16_tol(want)), np.abs(got - want).max()
+    # top-k with buckets of 500 letters, re-scored
+    k, sep = 4, 500
+    gw, gs = lib.rope_score_topk(idx, f32, bf16, norms, k=k, sep=sep, precision="bf16", rescore=1)
+    lib.rope_sync_status()
+    ow, os_ = oracle.score_topk(ref, rd.seqs, rd.offsets, op, k=k + 1, sep=sep)
+    check_topk(ref, rd, op, gw.cpu().numpy(), gs.cpu().numpy().astype(np.float64), ow, os_, k, bf16_tol, f32_tol,
+               sep=sep)
+    # threshold pairs for a 10% rate
+    thr = lib.rope_fragment_thresholds(idx, 0.10, 4, 5)
+    r, w, sc, total = lib.rope_score_threshold(idx, bf16, thr)
+    lib.rope_sync_status()
+    r, w = r.cpu().numpy(), w.cpu().numpy()
+    assert total == len(r) and total > 0
+    thr_h = thr.cpu().numpy().astype(np.float64)
+    orr, ow2, _ = oracle.threshold_pairs(ref, rd.seqs, rd.offsets, op, thr_h)
+    got_set, want_set = set(zip(r.tolist(), w.tolist())), set(zip(orr.tolist(), ow2.tolist()))
+    assert len(got_set) == len(r)
+    for (i, j) in got_set ^ want_set:
+        f = oracle.score_pairs(ref, rd.seqs, rd.offsets, np.array([i]), np.array([j * stride]), op)[0]
+        assert abs(f - thr_h[j]) <= bf16_tol(f), (i, j, f, thr_h[j])
+    assert W == oracle.n_windows(len(ref), N, stride)
+    idx.free()
