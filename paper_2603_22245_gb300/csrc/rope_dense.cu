@@ -265,7 +265,7 @@ struct GemmShape {
   static constexpr int BK = 64;                  // K per stage: one 128-byte swizzled BF16 row
   static constexpr int BOX_BYTES = 128 * BK * 2;           // one 128-row box: 16 KB
   static constexpr int STAGE_BYTES = (kShort ? 2 : 3) * BOX_BYTES;  // [A,] B_re, B_im
-  static constexpr int MAX_STAGES = kShort ? 5 : 4;
+  static constexpr int MAX_STAGES = kShort ? 6 : 4;
   static constexpr int MAX_RES_KB = 2;           // short K: resident A of at most 2 K blocks
   static constexpr int EQ = kShort ? 2 : 1;      // epilogue warps per lane quarter
   static constexpr int WCOLS = BN / EQ;          // windows per epilogue warp per tile
@@ -283,6 +283,19 @@ struct GemmShape {
            (size_t)cand_depth * BM * EQ * 8;
   }
 };
+
+// largest of 16 scores: a depth-3 tree of 3-input maxima (short dependency
+// chains for the latency-bound epilogue)
+__device__ __forceinline__ float max3f(float a, float b, float c) {
+  float d;
+  asm("max.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
+  return d;
+}
+__device__ __forceinline__ float max16(const float (&v)[16]) {
+  const float m0 = max3f(v[0], v[1], v[2]), m1 = max3f(v[3], v[4], v[5]), m2 = max3f(v[6], v[7], v[8]);
+  const float m3 = max3f(v[9], v[10], v[11]), m4 = max3f(v[12], v[13], v[14]);
+  return fmaxf(max3f(m0, m1, m2), max3f(m3, m4, v[15]));
+}
 
 // (read tile, window range) of item `it`; false for the padding items of the
 // last wave. Items come in waves of grp read tiles x n_ranges ranges, range
@@ -504,9 +517,7 @@ __global__ void __launch_bounds__(GemmShape<kShort>::NTHREADS, 1)
             float mn = tl;
 #pragma unroll
             for (int o = 8; o > 0; o >>= 1) mn = fminf(mn, __shfl_xor_sync(0xffffffffu, mn, o));
-            float mx = sc[0];
-#pragma unroll
-            for (int n = 1; n < 16; ++n) mx = fmaxf(mx, sc[n]);
+            const float mx = max16(sc);
             if (__any_sync(0xffffffffu, have && mx >= mn)) {
 #pragma unroll
               for (int n = 0; n < 16; ++n) {
@@ -530,8 +541,7 @@ __global__ void __launch_bounds__(GemmShape<kShort>::NTHREADS, 1)
           } else {
             float mx = -INFINITY;
             if (full) {
-#pragma unroll
-              for (int n = 0; n < 16; ++n) mx = fmaxf(mx, sc[n]);
+              mx = max16(sc);
             } else {
 #pragma unroll
               for (int n = 0; n < 16; ++n)
