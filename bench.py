@@ -702,6 +702,7 @@ def main():
                 "kernel": "gemm_tc_kernel (BF16 tcgen05 GEMM over the materialised index, A operand build included)"
                 if dense_index else "scan_tc_kernel (BF16 tcgen05)", "peak_source": f"{peak_src} bf16_tflops_sustained",
                 "flops_per_launch": flops, "ms_per_launch": scan_s * 1000.0,
+                "ms_per_launch_median": float(np.median(stage_ms[:, 1])),
                 "stage_ms": {"encode": float(np.mean(stage_ms[:, 0])), "scan": float(np.mean(stage_ms[:, 1])),
                              "merge_rescore": float(np.mean(stage_ms[:, 2]))}}
 

@@ -290,3 +290,34 @@ def test_dense_short_k_shape(lib, s, m, t, N, stride):
         assert abs(f - thr_h[j]) <= bf16_tol(f), (i, j, f, thr_h[j])
     assert W == oracle.n_windows(len(ref), N, stride)
     idx.free()
+
+
+@pytest.mark.parametrize("precision", ["fp32", "bf16"])
+@pytest.mark.parametrize("s,m,t,N,stride", [(4, 2, 2, 150, 7), (8, 4, 4, 2000, 125)])
+def test_dense_topk_subrange_and_fill(lib, precision, s, m, t, N, stride):
+    """Edge cases of the materialised index's scans (short and long K): a
+    range of 5 windows with k = 8 (three (-1, -inf) fills, the 5 windows in
+    the oracle's order), an empty range (every slot (-1, -inf)), and no
+    reads at all."""
+    op = oracle.Params(s=s, m=m, t=t, variant=1, N=N, stride=stride)
+    ref = synth.uniform_ref(30_000, 261)
+    rd = synth.reads(ref, 9, seed=262, length=N)
+    p = gparams(lib, s, m, t, N, stride)
+    idx = lib.rope_encode_reference_dense(p, dev(ref))
+    f32, bf16, norms = lib.rope_encode_reads(p, dev(rd.seqs), dev(rd.offsets))
+    b = bf16 if precision == "bf16" else None
+    gw, gs = lib.rope_score_topk(idx, f32, b, norms, k=8, precision=precision, rescore=1 if b is not None else None,
+                                 j_begin=40, j_end=45)
+    lib.rope_sync_status()
+    gw, gs = gw.cpu().numpy(), gs.cpu().numpy().astype(np.float64)
+    ow, os_ = oracle.score_topk(ref, rd.seqs, rd.offsets, op, k=8, j_begin=40, j_end=45)
+    assert np.all(gw[:, 5:] == -1) and np.all(np.isneginf(gs[:, 5:]))
+    assert np.array_equal(np.sort(gw[:, :5], axis=1), np.sort(ow[:, :5], axis=1))
+    assert np.all(np.abs(np.sort(gs[:, :5], axis=1) - np.sort(os_[:, :5], axis=1)) <= f32_tol(np.sort(os_[:, :5], axis=1)))
+    gw, gs = lib.rope_score_topk(idx, f32, b, norms, k=4, precision=precision, j_begin=10, j_end=10)
+    lib.rope_sync_status()
+    assert np.all(gw.cpu().numpy() == -1) and np.all(np.isneginf(gs.cpu().numpy()))
+    gw, gs = lib.rope_score_topk(idx, f32[:0], b[:0] if b is not None else None, norms[:0], k=4, precision=precision)
+    lib.rope_sync_status()
+    assert gw.shape == (0, 4)
+    idx.free()
