@@ -94,7 +94,8 @@ enum { ROPE_PREC_FP32 = 0, ROPE_PREC_BF16 = 1, ROPE_PREC_FP8 = 2 };
  *              (tensor cores)
  *   rescore    1: re-score the kept candidates by direct FP32 summation before
  *              the final ranking; 0: report the scan's own scores
- *   cand_depth candidates kept per read per window range (0 = 16); k..32
+ *   cand_depth candidates kept per read per window range and list (0 = 8,
+ *              raised to k); k..32
  *   rescore_depth candidates re-scored per read (0 = 2*k, capped at 32)
  *   j_begin, j_end  window-number range [j_begin, j_end) scanned; j_end <= 0
  *              means all windows

@@ -861,7 +861,9 @@ rope_status check_opts(const rope_score_opts* o, rope_score_opts* v) {
   *v = *o;
   if (v->k < 1 || v->k > 32) return fail(ROPE_ERR_INVALID_ARG, "k=%d outside [1,32]", v->k);
   if (v->sep < 0) return fail(ROPE_ERR_INVALID_ARG, "sep < 0");
-  if (v->cand_depth == 0) v->cand_depth = 16;
+  // default: 8 candidates per list (k when k > 8); the union of a read's
+  // lists (two halves x several window ranges) feeds the re-scoring
+  if (v->cand_depth == 0) v->cand_depth = 8;
   if (v->cand_depth < v->k) v->cand_depth = v->k;
   if (v->cand_depth > 32) return fail(ROPE_ERR_INVALID_ARG, "cand_depth > 32");
   if (v->rescore_depth == 0) v->rescore_depth = v->k * 2 < 32 ? v->k * 2 : 32;

@@ -118,9 +118,9 @@ def test_noalloc_bf16_automatic_split(lib):
     scores and FP32 re-scoring the result is still rope_score_topk's."""
     n, k = 4096, 8
     idx, f32, bf16, norms = _inputs(lib, n, ref_len=1_000_000)
-    want = lib.rope_score_topk(idx, f32, bf16, norms, k=k, precision="bf16", rescore=1)
+    want = lib.rope_score_topk(idx, f32, bf16, norms, k=k, precision="bf16", rescore=1, cand_depth=16)
     got = _out(n, k)
-    lib.rope_score_topk_noalloc(idx, f32, bf16, norms, got, k=k, precision="bf16", rescore=1)
+    lib.rope_score_topk_noalloc(idx, f32, bf16, norms, got, k=k, precision="bf16", rescore=1, cand_depth=16)
     lib.rope_sync_status()
     lib.rope_noalloc_sync_status()
     assert torch.equal(got[0], want[0])
