@@ -637,8 +637,9 @@ __global__ void __launch_bounds__(Sh::NTHREADS, 1) scan_tc_kernel(DevIndex ix, S
 
 // d = 64:  256 reads x 64 windows per stage, MMA N = 128; 16 epilogue warps (two
 //          per accumulator quarter), 8 generator warps (chains of 4 lanes x 8
-//          entries), the MMA warp alone with epilogue warps on its scheduler.
-using TcShape32 = TcShape<32, 2, 64, 2, 4, 4, 2, true>;
+//          entries), the MMA warp alone with epilogue warps on its scheduler;
+//          up to 6 window slots between the generators and the MMA warp.
+using TcShape32 = TcShape<32, 2, 64, 2, 6, 4, 2, true>;
 // d = 64, second tile variant: one epilogue warp per accumulator quarter and
 //          tile (8 warps, each reading all 64 windows of a stage; one candidate
 //          list per read), more registers per thread. Faster at large strides.
