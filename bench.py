@@ -80,13 +80,13 @@ WORKLOADS = {
              "reads (1% sub, 0.5% indel geom p=0.7), d=64 (s=4 m=2 t=2 fine-tuned), N=150, stride 1, exhaustive, top-8",
         L=3_100_000_000, gc=0.41, tandem=0.0, segdup=0.0, inter=0.50, ref_seed=7,
         n_reads=100_000, read_len=150, sub=0.01, indel=0.005, read_seed=8,
-        s=4, m=2, t=2, variant=1, N=150, stride=1, k=8),
+        s=4, m=2, t=2, variant=1, N=150, stride=1, k=8, batch=16_384, fp32_reads=128),
     "maize2300M": dict(
         desc="2.3 Gbp maize-shaped order-2 Markov genome (GC 47%, 85% interspersed repeats), 100k x 150 bp planted "
              "reads (1% sub, 0.5% indel geom p=0.7), d=64 (s=4 m=2 t=2 fine-tuned), N=150, stride 1, exhaustive, top-8",
         L=2_300_000_000, gc=0.47, tandem=0.0, segdup=0.0, inter=0.85, ref_seed=8,
         n_reads=100_000, read_len=150, sub=0.01, indel=0.005, read_seed=9,
-        s=4, m=2, t=2, variant=1, N=150, stride=1, k=8),
+        s=4, m=2, t=2, variant=1, N=150, stride=1, k=8, batch=16_384, fp32_reads=128),
     "human3G_20k": dict(
         desc="3.1 Gbp human-shaped order-2 Markov genome (GC 41%, 50% interspersed repeats), 96k planted 20 kbp reads "
              "at 15% errors (5% substitutions, 10% indel events of geometric length p=0.7), every other read "
